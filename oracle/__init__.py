@@ -1,0 +1,14 @@
+"""FP64 CPU oracle of the DMSGM block-grid step (arXiv:1702.05156, Sec. 2.2-2.4).
+
+TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
+baseline leg use it to check and time the CUDA library.  The product package
+never imports it.
+"""
+from .oracle import (  # noqa: F401
+    DIAG,
+    OracleState,
+    build_oracle,
+    oracle_run,
+    oracle_step,
+    state_from_arrays,
+)

@@ -1,0 +1,146 @@
+"""ctypes shim around ``dmsgm_oracle.c`` -- the FP64 CPU oracle.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, the smoke check and the
+benchmark's CPU-baseline leg may import this module.  It shares no code with
+the CUDA library and never imports the product package.
+
+Everything the method computes lives in ``dmsgm_oracle.c`` (one plain loop
+nest per equation of arXiv:1702.05156 Sec. 2.2-2.4); this file only moves
+NumPy arrays in and out.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dmsgm_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Column indices of the per-block diagnostics (mirrors the enum in the C file).
+DIAG = dict(M=0, NOSRC=1, WSUM=2, MU_A=3, VAR_A=4, XAGE_A=5, MU_C=6, VAR_C=7,
+            XAGE_C=8, BRANCH=9, SWAP=10, MIN=11, MAX=12)
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (no -ffast-math, no FP contraction)."""
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build_oracle()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            lib.oracle_step.restype = ctypes.c_int
+            lib.oracle_step.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
+                ctypes.c_int, ctypes.c_int] + [P] * 16
+            lib.oracle_run.restype = ctypes.c_int
+            lib.oracle_run.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
+                ctypes.c_int, ctypes.c_int] + [P] * 15
+            lib.oracle_diag_stride.restype = ctypes.c_int
+            assert lib.oracle_diag_stride() == len(DIAG)
+            _lib = lib
+    return _lib
+
+
+@dataclass
+class OracleState:
+    """Block-grid state in FP64 / int32, each array of shape (Gy, Gx)."""
+    muA: np.ndarray
+    varA: np.ndarray
+    ageA: np.ndarray
+    muC: np.ndarray
+    varC: np.ndarray
+    ageC: np.ndarray
+
+    @staticmethod
+    def empty(gy: int, gx: int) -> "OracleState":
+        z = lambda dt: np.zeros((gy, gx), dtype=dt)  # noqa: E731
+        return OracleState(z(np.float64), z(np.float64), z(np.int32),
+                           z(np.float64), z(np.float64), z(np.int32))
+
+
+def state_from_arrays(muA, varA, ageA, muC, varC, ageC) -> OracleState:
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+    i = lambda a: np.ascontiguousarray(a, dtype=np.int32)  # noqa: E731
+    return OracleState(f(muA), f(varA), i(ageA), f(muC), f(varC), i(ageC))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def oracle_step(frame: np.ndarray, H: np.ndarray, prev: OracleState | None, *,
+                block: int, theta_s: float = 2.0, theta_d: float = 4.0,
+                age_max: int = 30, diag: bool = False):
+    """One frame.  ``prev=None`` means the first frame of a stream.
+
+    Returns ``(state, mask)`` or ``(state, mask, diag)``; ``mask`` is uint8
+    (H, W) with 1 = foreground.
+    """
+    lib = _load()
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    h, w = frame.shape
+    if w % block or h % block:
+        raise ValueError("frame size must be a multiple of the block size")
+    gy, gx = h // block, w // block
+    Hm = np.ascontiguousarray(H, dtype=np.float64).reshape(9)
+    first = prev is None
+    if first:
+        prev = OracleState.empty(gy, gx)
+    nxt = OracleState.empty(gy, gx)
+    mask = np.zeros((h, w), dtype=np.uint8)
+    dg = np.zeros((gy, gx, len(DIAG)), dtype=np.float64) if diag else None
+    rc = lib.oracle_step(
+        w, h, block, float(theta_s), float(theta_d), int(age_max), int(first),
+        _ptr(frame), _ptr(Hm),
+        _ptr(prev.muA), _ptr(prev.varA), _ptr(prev.ageA),
+        _ptr(prev.muC), _ptr(prev.varC), _ptr(prev.ageC),
+        _ptr(nxt.muA), _ptr(nxt.varA), _ptr(nxt.ageA),
+        _ptr(nxt.muC), _ptr(nxt.varC), _ptr(nxt.ageC),
+        _ptr(mask), _ptr(dg) if diag else None)
+    if rc:
+        raise ValueError(f"oracle_step failed ({rc})")
+    return (nxt, mask, dg) if diag else (nxt, mask)
+
+
+def oracle_run(frames: np.ndarray, Hs: np.ndarray, *, block: int,
+               theta_s: float = 2.0, theta_d: float = 4.0, age_max: int = 30):
+    """T frames free-running from an empty state; returns (state, masks[T,H,W])."""
+    lib = _load()
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, h, w = frames.shape
+    gy, gx = h // block, w // block
+    Hs = np.ascontiguousarray(Hs, dtype=np.float64).reshape(T, 9)
+    st = OracleState.empty(gy, gx)
+    tmp = OracleState.empty(gy, gx)
+    masks = np.zeros((T, h, w), dtype=np.uint8)
+    rc = lib.oracle_run(
+        w, h, block, float(theta_s), float(theta_d), int(age_max), T,
+        _ptr(frames), _ptr(Hs),
+        _ptr(st.muA), _ptr(st.varA), _ptr(st.ageA),
+        _ptr(st.muC), _ptr(st.varC), _ptr(st.ageC),
+        _ptr(tmp.muA), _ptr(tmp.varA), _ptr(tmp.ageA),
+        _ptr(tmp.muC), _ptr(tmp.varC), _ptr(tmp.ageC),
+        _ptr(masks))
+    if rc:
+        raise ValueError(f"oracle_run failed ({rc})")
+    return st, masks

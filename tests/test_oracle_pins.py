@@ -1,0 +1,395 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each test fixes one part of arXiv:1702.05156 Sec. 2.2-2.4 by a closed form,
+an exact symmetry, a hand-computed fixture or brute-force counting, so that a
+dropped term, a wrong sign, a swapped index or a transposed operand in the
+oracle fails at least one of them.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import DIAG, oracle_step, state_from_arrays
+from paper_1702_05156_gb300.synth import random_state, translation
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _q(s):
+    """'a' or 'a/b' with decimal a and b, evaluated exactly."""
+    if not isinstance(s, str):
+        return float(s)
+    num, _, den = s.partition("/")
+    return float(Fraction(num) / Fraction(den or "1"))
+
+
+# ---------------------------------------------------------------- hand fixture
+def test_hand_computed_8x8_sequence():
+    """Three frames computed by hand (tests/golden/hand_8x8.json): pins the
+    mean/variance/age equations (Sec. 2.2), V with the UPDATED mean, the
+    match -> candidate -> reset -> swap order (Sec. 2.3) and the mask taken
+    after the swap."""
+    with open(os.path.join(GOLDEN, "hand_8x8.json")) as f:
+        g = json.load(f)
+    st = None
+    for fr in g["frames"]:
+        img = np.array(fr["pixels"], dtype=np.uint8)
+        st, mask = oracle_step(img, np.eye(3), st, block=g["block"], theta_s=g["theta_s"],
+                               theta_d=g["theta_d"], age_max=g["age_max"])
+        e = fr["expect"]
+        for name in ("muA", "varA", "muC", "varC"):
+            exp = np.array([_q(v) for v in e[name]]).reshape(2, 2)
+            np.testing.assert_allclose(getattr(st, name), exp, rtol=1e-13, atol=0, err_msg=name)
+        for name in ("ageA", "ageC"):
+            np.testing.assert_array_equal(getattr(st, name), np.array(e[name]).reshape(2, 2), name)
+        np.testing.assert_array_equal(mask, np.array(e["mask"], dtype=np.uint8))
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("block", [1, 4, 8])
+@pytest.mark.parametrize("c", [0, 37, 255])
+def test_constant_frame_identity_closed_form(block, c):
+    """Identity H and a constant frame c: mu == c, var_n = 255/n while the
+    age n <= 30, then var_n = (255/30) * (30/31)^(n-30) at the cap; ages
+    1, 2, ..., 30, 30, ...; the candidate stays (c, 255, 1); the mask is
+    empty on every frame (Sec. 2.2 equations with V = 0)."""
+    W, H = 16, 8
+    img = np.full((H, W), c, dtype=np.uint8)
+    st = None
+    for n in range(1, 46):
+        st, mask = oracle_step(img, np.eye(3), st, block=block)
+        np.testing.assert_allclose(st.muA, c, rtol=0, atol=1e-12)
+        exp_var = 255.0 / n if n <= 30 else (255.0 / 30) * (30.0 / 31.0) ** (n - 30)
+        np.testing.assert_allclose(st.varA, exp_var, rtol=1e-12)
+        assert (st.ageA == min(n, 30)).all()
+        assert (st.muC == c).all() and (st.varC == 255).all() and (st.ageC == 1).all()
+        assert mask.sum() == 0
+
+
+def test_swap_script_and_age_cap_quirk():
+    """Background 50 for 10 frames, then 200: the candidate is reset at frame
+    11, grows one year per frame and wins at frame 21 when its age 11 exceeds
+    the apparent age 10 (Sec. 2.3, strict '>').  Before the swap every pixel
+    is foreground against A = 50, right after it none is.  If the apparent
+    model has reached the cap (age 30), a candidate capped at 30 can never
+    exceed it and no swap ever happens."""
+    W = H = 8
+    bg = np.full((H, W), 50, np.uint8)
+    fg = np.full((H, W), 200, np.uint8)
+    st = None
+    for t in range(1, 11):
+        st, _ = oracle_step(bg, np.eye(3), st, block=4)
+    assert (st.ageA == 10).all()
+    for t in range(11, 22):
+        st, mask, dg = oracle_step(fg, np.eye(3), st, block=4, diag=True)
+        k = t - 10  # frames of the new background so far
+        if t < 21:
+            assert (st.muA == 50).all() and (st.ageA == 10).all()
+            assert (st.ageC == k).all()
+            np.testing.assert_allclose(st.muC, 200, rtol=1e-14)
+            np.testing.assert_allclose(st.varC, 255.0 / k, rtol=1e-12)
+            assert mask.all()
+            assert (dg[..., DIAG["BRANCH"]] == (2 if t == 11 else 1)).all()
+        else:
+            assert (dg[..., DIAG["SWAP"]] == 1).all()
+            np.testing.assert_allclose(st.muA, 200, rtol=1e-14)
+            assert (st.ageA == 11).all()
+            np.testing.assert_allclose(st.varA, 255.0 / 11, rtol=1e-12)
+            assert (st.muC == 200).all() and (st.varC == 255).all() and (st.ageC == 1).all()
+            assert mask.sum() == 0
+
+    st = None
+    for t in range(40):
+        st, _ = oracle_step(bg, np.eye(3), st, block=4)
+    for t in range(60):
+        st, mask = oracle_step(fg, np.eye(3), st, block=4)
+    np.testing.assert_allclose(st.muA, 50, rtol=1e-14)
+    np.testing.assert_allclose(st.muC, 200, rtol=1e-14)
+    assert (st.ageA == 30).all() and (st.ageC == 30).all()
+    assert mask.all()
+
+
+# ---------------------------------------------------------------- compensation
+def _shift_blocks(a, k, l, fill):
+    out = np.full_like(a, fill)
+    gy, gx = a.shape
+    ys = slice(max(l, 0), gy + min(l, 0))
+    xs = slice(max(k, 0), gx + min(k, 0))
+    ys0 = slice(max(-l, 0), gy + min(-l, 0))
+    xs0 = slice(max(-k, 0), gx + min(-k, 0))
+    out[ys, xs] = a[ys0, xs0]
+    return out
+
+
+@pytest.mark.parametrize("block", [1, 4, 8])
+@pytest.mark.parametrize("k,l", [(1, 0), (0, 1), (-2, 3), (3, -1), (0, 0)])
+def test_whole_block_translation_is_an_exact_shift(block, k, l):
+    """Content moving by (k*B, l*B) px: the compensated state of block
+    (bx, by) is EXACTLY the previous state of block (bx-k, by-l) (all weight
+    on one block); blocks whose source is off the grid have no source and
+    restart both models at (M, 255, 1)."""
+    gx, gy = 11, 7
+    W, H = gx * block, gy * block
+    prev = state_from_arrays(*random_state(gy, gx, 30, seed=5))
+    rng = np.random.default_rng(1)
+    img = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    Hm = translation(k * block, l * block)
+    st, mask, dg = oracle_step(img, Hm, prev, block=block, diag=True)
+    nos = _shift_blocks(np.zeros((gy, gx)), k, l, 1.0) > 0
+    assert (dg[..., DIAG["NOSRC"]].astype(bool) == nos).all()
+    for name, col in (("muA", "MU_A"), ("varA", "VAR_A"), ("muC", "MU_C"), ("varC", "VAR_C"),
+                      ("ageA", "XAGE_A"), ("ageC", "XAGE_C")):
+        exp = _shift_blocks(getattr(prev, name).astype(np.float64), k, l, np.nan)
+        got = dg[..., DIAG[col]]
+        assert np.array_equal(got[~nos], exp[~nos]), name
+    # the whole step equals an identity step on the shifted state
+    shifted = state_from_arrays(*[_shift_blocks(getattr(prev, n), k, l, 1)
+                                  for n in ("muA", "varA", "ageA", "muC", "varC", "ageC")])
+    st2, mask2 = oracle_step(img, np.eye(3), shifted, block=block)
+    M = img.reshape(gy, block, gx, block).mean(axis=(1, 3))
+    for n in ("muA", "varA", "ageA", "muC", "varC", "ageC"):
+        a, b = getattr(st, n), getattr(st2, n)
+        assert np.array_equal(a[~nos], b[~nos]), n
+    assert np.array_equal(st.muA[nos], M[nos]) and (st.varA[nos] == 255).all()
+    assert (st.ageA[nos] == 1).all() and (st.ageC[nos] == 1).all()
+    pix_nos = np.kron(nos, np.ones((block, block), bool))
+    assert np.array_equal(mask[~pix_nos], mask2[~pix_nos])
+
+
+def test_fractional_shifts_hand_weights():
+    """Sub-block shifts with hand-derived weights (B = 4, block centres at
+    4*b + 2).  Content moving right by 2 px: the back-projected square starts
+    at u = bx - 1/2, so blocks bx-1 and bx get 1/2 each; at the left edge only
+    block 0 is in the grid and renormalisation gives it all the weight.  An
+    age mix of 1 and 2 gives 1.5, rounded half up to 2.  Moving right 1 px:
+    weights 1/4 (bx-1) and 3/4 (bx).  Moving (1, 3) px: rows by-1 / by get
+    3/4 / 1/4, columns 1/4 / 3/4."""
+    gx, gy = 4, 3
+    muA = np.arange(gx * gy, dtype=np.float64).reshape(gy, gx) * 10 + 5
+    varA = np.arange(gx * gy, dtype=np.float64).reshape(gy, gx) + 1
+    ageA = (np.arange(gx * gy).reshape(gy, gx) % 7 + 1).astype(np.int32)
+    prev = state_from_arrays(muA, varA, ageA, muA + 1, varA + 2, ageA)
+    img = np.zeros((gy * 4, gx * 4), np.uint8)
+
+    _, _, dg = oracle_step(img, translation(2, 0), prev, block=4, diag=True)
+    for by in range(gy):
+        for bx in range(gx):
+            if bx == 0:
+                e_mu, e_age = muA[by, 0], float(ageA[by, 0])
+                e_w = 0.5
+            else:
+                e_mu = 0.5 * muA[by, bx - 1] + 0.5 * muA[by, bx]
+                e_age = 0.5 * ageA[by, bx - 1] + 0.5 * ageA[by, bx]
+                e_w = 1.0
+            assert dg[by, bx, DIAG["WSUM"]] == e_w
+            assert dg[by, bx, DIAG["MU_A"]] == e_mu
+            assert dg[by, bx, DIAG["XAGE_A"]] == e_age
+    # rounding half up: ages 1 and 2 -> 1.5 -> 2
+    prev2 = state_from_arrays(muA, varA, np.array([[1, 2, 1, 2]] * gy, np.int32),
+                              muA, varA, np.array([[2, 3, 2, 3]] * gy, np.int32))
+    _, _, dg = oracle_step(img, translation(2, 0), prev2, block=4, diag=True)
+    assert dg[0, 1, DIAG["XAGE_A"]] == 1.5 and dg[0, 1, DIAG["XAGE_C"]] == 2.5
+
+    _, _, dg = oracle_step(img, translation(1, 0), prev, block=4, diag=True)
+    for bx in range(1, gx):
+        assert dg[1, bx, DIAG["MU_A"]] == 0.25 * muA[1, bx - 1] + 0.75 * muA[1, bx]
+
+    _, _, dg = oracle_step(img, translation(1, 3), prev, block=4, diag=True)
+    for by in range(1, gy):
+        for bx in range(1, gx):
+            e = (0.25 * 0.75 * muA[by - 1, bx - 1] + 0.75 * 0.75 * muA[by - 1, bx]
+                 + 0.25 * 0.25 * muA[by, bx - 1] + 0.75 * 0.25 * muA[by, bx])
+            assert abs(dg[by, bx, DIAG["MU_A"]] - e) < 1e-12
+
+
+def test_half_up_age_rounding_enters_the_update():
+    """A mixed age of 1.5 rounds to 2, so a matching block's stored age is 3
+    and its learning rate is 1/3 (Sec. 2.2 with the rounded age~)."""
+    gx, gy = 3, 1
+    mu = np.full((gy, gx), 100.0)
+    prev = state_from_arrays(mu, np.full((gy, gx), 50.0), np.array([[1, 2, 1]], np.int32),
+                             mu, np.full((gy, gx), 50.0), np.array([[1, 1, 1]], np.int32))
+    img = np.full((4, 12), 103, np.uint8)
+    st, _, dg = oracle_step(img, translation(2, 0), prev, block=4, diag=True)
+    assert dg[0, 1, DIAG["XAGE_A"]] == 1.5 and dg[0, 1, DIAG["BRANCH"]] == 0
+    assert st.ageA[0, 1] == 3
+    assert abs(st.muA[0, 1] - (2 / 3 * 100 + 1 / 3 * 103)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mixing_weights_equal_brute_force_overlap_area(seed):
+    """R6: the mixing weight of a previous block is the area that the
+    back-projected BxB square shares with it.  Shifts are multiples of B/16
+    px, so counting the 16x16 sub-cells of the square that fall in each
+    block is exact; the oracle's compensated mean must equal the area-
+    weighted mean of the in-grid blocks, renormalised."""
+    rng = np.random.default_rng(seed)
+    B, S = 4, 16
+    gx, gy = 6, 5
+    prev = state_from_arrays(*random_state(gy, gx, 30, seed=seed + 10))
+    dx = rng.integers(-3 * S, 3 * S) * B / S
+    dy = rng.integers(-3 * S, 3 * S) * B / S
+    img = np.zeros((gy * B, gx * B), np.uint8)
+    _, _, dg = oracle_step(img, translation(dx, dy), prev, block=B, diag=True)
+    for by in range(gy):
+        for bx in range(gx):
+            # square top-left in pixels (in the previous frame)
+            qx = bx * B - dx
+            qy = by * B - dy
+            area = {}
+            for sy in range(S):
+                for sx in range(S):
+                    px = qx + (sx + 0.5) * B / S
+                    py = qy + (sy + 0.5) * B / S
+                    cell = (int(np.floor(py / B)), int(np.floor(px / B)))
+                    area[cell] = area.get(cell, 0) + 1
+            inn = {c: a for c, a in area.items() if 0 <= c[0] < gy and 0 <= c[1] < gx}
+            tot = sum(inn.values())
+            assert dg[by, bx, DIAG["WSUM"]] == pytest.approx(tot / S ** 2, abs=1e-12)
+            if tot / S ** 2 < 1e-3:
+                assert dg[by, bx, DIAG["NOSRC"]] == 1
+                continue
+            e_mu = sum(a * prev.muA[c] for c, a in inn.items()) / tot
+            e_var = sum(a * prev.varC[c] for c, a in inn.items()) / tot
+            e_age = sum(a * prev.ageA[c] for c, a in inn.items()) / tot
+            assert dg[by, bx, DIAG["MU_A"]] == pytest.approx(e_mu, rel=1e-12)
+            assert dg[by, bx, DIAG["VAR_C"]] == pytest.approx(e_var, rel=1e-12)
+            assert dg[by, bx, DIAG["XAGE_A"]] == pytest.approx(e_age, rel=1e-12)
+
+
+def test_no_source_cases():
+    """R10: a homography that sends every block off the grid, one with
+    Z <= 0, and the first frame all restart both models at (M, 255, 1)."""
+    gx, gy = 4, 4
+    prev = state_from_arrays(*random_state(gy, gx, 30, seed=3))
+    rng = np.random.default_rng(0)
+    img = rng.integers(0, 256, (16, 16), dtype=np.uint8)
+    M = img.reshape(4, 4, 4, 4).mean(axis=(1, 3))
+    flip = np.diag([1.0, 1.0, -1.0])  # Z = -1 everywhere
+    for Hm in (translation(1000, 0), flip):
+        st, _, dg = oracle_step(img, Hm, prev, block=4, diag=True)
+        assert (dg[..., DIAG["NOSRC"]] == 1).all()
+        assert np.array_equal(st.muA, M) and np.array_equal(st.muC, M)
+        assert (st.varA == 255).all() and (st.ageA == 1).all() and (st.ageC == 1).all()
+
+
+# ---------------------------------------------------------------- symmetries
+def _random_case(seed, gx=9, gy=6, B=4):
+    rng = np.random.default_rng(seed)
+    prev = state_from_arrays(*random_state(gy, gx, 30, seed=seed))
+    # frames close to the state so that all three branches occur
+    base = np.kron(prev.muA, np.ones((B, B)))
+    img = np.clip(base + rng.normal(0, 6, base.shape) + (rng.random(base.shape) < 0.2) * 90,
+                  0, 255).round().astype(np.uint8)
+    th = np.radians(rng.uniform(-2, 2))
+    s = 1 + rng.uniform(-0.02, 0.02)
+    Hm = np.array([[s * np.cos(th), -s * np.sin(th), rng.uniform(-5, 5)],
+                   [s * np.sin(th), s * np.cos(th), rng.uniform(-5, 5)],
+                   [rng.uniform(-1e-4, 1e-4), rng.uniform(-1e-4, 1e-4), 1.0]])
+    return prev, img, Hm
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mirror_symmetry(seed):
+    """Mirroring the frame left-right, the state and the homography
+    (conjugated by x -> W - x) mirrors every output.  Catches swapped
+    neighbour weights and x/y index slips in the compensation."""
+    prev, img, Hm = _random_case(seed)
+    gy, gx = prev.muA.shape
+    W = gx * 4
+    Fm = np.array([[-1.0, 0, W], [0, 1, 0], [0, 0, 1]])
+    st, mask, dg = oracle_step(img, Hm, prev, block=4, diag=True)
+    fprev = state_from_arrays(*[getattr(prev, n)[:, ::-1] for n in
+                                ("muA", "varA", "ageA", "muC", "varC", "ageC")])
+    st2, mask2, dg2 = oracle_step(img[:, ::-1], Fm @ Hm @ Fm, fprev, block=4, diag=True)
+    assert len(set(dg[..., DIAG["BRANCH"]].ravel())) >= 3
+    for n in ("muA", "varA", "muC", "varC"):
+        np.testing.assert_allclose(getattr(st2, n)[:, ::-1], getattr(st, n), rtol=1e-10)
+    for n in ("ageA", "ageC"):
+        np.testing.assert_array_equal(getattr(st2, n)[:, ::-1], getattr(st, n))
+    np.testing.assert_array_equal(mask2[:, ::-1], mask)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_transpose_symmetry(seed):
+    """Swapping x and y in the frame, state and homography transposes every
+    output (square grid)."""
+    prev, img, Hm = _random_case(seed, gx=7, gy=7)
+    P = np.array([[0.0, 1, 0], [1, 0, 0], [0, 0, 1]])
+    st, mask = oracle_step(img, Hm, prev, block=4)
+    tprev = state_from_arrays(*[getattr(prev, n).T for n in
+                                ("muA", "varA", "ageA", "muC", "varC", "ageC")])
+    st2, mask2 = oracle_step(img.T, P @ Hm @ P, tprev, block=4)
+    for n in ("muA", "varA", "muC", "varC"):
+        np.testing.assert_allclose(getattr(st2, n).T, getattr(st, n), rtol=1e-10)
+    for n in ("ageA", "ageC"):
+        np.testing.assert_array_equal(getattr(st2, n).T, getattr(st, n))
+    np.testing.assert_array_equal(mask2.T, mask)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_negation_symmetry(seed):
+    """I -> 255 - I with mu -> 255 - mu and the same variances and ages gives
+    mu -> 255 - mu, var -> var, ages and mask unchanged: the equations only
+    use differences and squares.  Catches a sign slip in V or the tests."""
+    prev, img, Hm = _random_case(seed)
+    st, mask = oracle_step(img, Hm, prev, block=4)
+    nprev = state_from_arrays(255 - prev.muA, prev.varA, prev.ageA,
+                              255 - prev.muC, prev.varC, prev.ageC)
+    st2, mask2 = oracle_step(255 - img, Hm, nprev, block=4)
+    np.testing.assert_allclose(255 - st2.muA, st.muA, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(255 - st2.muC, st.muC, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(st2.varA, st.varA, rtol=1e-10)
+    np.testing.assert_allclose(st2.varC, st.varC, rtol=1e-10)
+    np.testing.assert_array_equal(st2.ageA, st.ageA)
+    np.testing.assert_array_equal(st2.ageC, st.ageC)
+    np.testing.assert_array_equal(mask2, mask)
+
+
+def test_interior_weights_sum_to_one():
+    """Away from the border all four overlapped blocks are in the grid and
+    the area weights sum to one for any homography."""
+    prev, img, Hm = _random_case(7, gx=12, gy=12)
+    _, _, dg = oracle_step(img, Hm, prev, block=4, diag=True)
+    np.testing.assert_allclose(dg[3:-3, 3:-3, DIAG["WSUM"]], 1.0, rtol=0, atol=1e-12)
+
+
+def test_variance_sample_min_max_identity():
+    """max_j (mu - I_j)^2 over a block equals max((mu - min)^2, (max - mu)^2)
+    (the shortcut the GPU uses), checked by brute force against the oracle's
+    own output: V recovered from the variance update equals the min/max
+    form built from the block's extreme pixels."""
+    prev, img, Hm = _random_case(11)
+    st, _, dg = oracle_step(img, Hm, prev, block=4, diag=True)
+    upd = dg[..., DIAG["BRANCH"]] == 0
+    a = np.floor(dg[..., DIAG["XAGE_A"]] + 0.5)
+    V = (st.varA - a / (a + 1) * dg[..., DIAG["VAR_A"]]) * (a + 1)
+    mn, mx = dg[..., DIAG["MIN"]], dg[..., DIAG["MAX"]]
+    Vmm = np.maximum((st.muA - mn) ** 2, (mx - st.muA) ** 2)
+    no_swap = dg[..., DIAG["SWAP"]] == 0
+    sel = upd & no_swap
+    assert sel.sum() > 5
+    np.testing.assert_allclose(V[sel], Vmm[sel], rtol=1e-8, atol=1e-8)
+
+
+def test_invalid_sizes_rejected():
+    with pytest.raises(ValueError):
+        oracle_step(np.zeros((6, 8), np.uint8), np.eye(3), None, block=4)
+
+
+def test_run_equals_repeated_steps():
+    rng = np.random.default_rng(2)
+    frames = rng.integers(0, 256, (5, 8, 16), dtype=np.uint8)
+    Hs = np.stack([np.eye(3), translation(1, 0), translation(0, 2), translation(-3, 1),
+                   np.eye(3)])
+    st_run, masks = oracle.oracle_run(frames, Hs, block=4)
+    st = None
+    for t in range(5):
+        st, m = oracle_step(frames[t], Hs[t], st, block=4)
+        np.testing.assert_array_equal(m, masks[t])
+    for n in ("muA", "varA", "ageA", "muC", "varC", "ageC"):
+        np.testing.assert_array_equal(getattr(st, n), getattr(st_run, n))
