@@ -1,0 +1,448 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 DMSGM motion-mask path.
+
+Workload (one "step"): one pass of the fused per-frame kernel over a
+pre-staged seeded synthetic 1920x1080 uint8 stream of 300 frames, block 4,
+FP32 state, theta_s = 2, theta_d = 4, age cap 30.  The 300 frames (622 MB)
+are larger than L2, so every frame is read from HBM; the model state (2 x
+2.3 MB) stays L2-resident across frames by the nature of the recurrence.
+The step's 300 launches go through the C ABI (dmsgm_process) inside a
+stream capture and are replayed as one CUDA graph.
+
+Output: ONE JSON line (rank 0).  value = Mpix/s over all ranks; e2e = the
+same metric through dmsgm_process_host (pinned host frames in, host masks
+out, copies inside the timed region); roofline = the fused kernel's
+algorithmic HBM bytes per launch / its average launch time vs the measured
+copy bandwidth; cpu_baseline = the FP64 oracle on this host's cores.
+
+--impl reference times the FP64 oracle (the only reference there is: the
+paper ships no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DMSGM Mpix/s & %HBM peak (1080p, 4K); batched vs plain Mpix/s; p99 frame ms"
+UNIT = "Mpix/s"
+
+
+def bytes_per_pixel(block: int, precision: str) -> float:
+    """Algorithmic HBM bytes per pixel of one frame step: the frame (1 B),
+    the mask (1/8 B) and the state read + write of the pixel's block
+    (2 x (4 values x s + 2 ages) / B^2)."""
+    s = 2 if precision == "fp16" else 4
+    return 1.0 + 1.0 / 8.0 + 2.0 * (4 * s + 2) / (block * block)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_tag: str, fingerprint: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_tag)
+    if not e or e.get("fingerprint") != fingerprint:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled in the background."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.samples = []
+        self.proc = None
+        self.index = index
+        self.t_lo = self.t_hi = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self, lo, hi):
+        self.t_lo, self.t_hi = lo, hi
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.samples:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((t, float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        inwin = [r for r in rows if self.t_lo is not None and self.t_lo - 0.05 <= r[0] <= self.t_hi + 0.05]
+        use = inwin or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use), "in_timed_window": len(inwin)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(frames_np, Hs, block, budget_s=12.0, min_frames=3):
+    """Time the FP64 oracle, one thread, frame by frame from the first frame
+    until the time budget is spent; returns (Mpix/s, frames, seconds)."""
+    from oracle import oracle_step
+    T, H, W = frames_np.shape
+    st = None
+    t0 = time.perf_counter()
+    n = 0
+    while n < T:
+        st, _ = oracle_step(frames_np[n], Hs[n], st, block=block)
+        n += 1
+        el = time.perf_counter() - t0
+        if n >= min_frames and el >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n * W * H / el / 1e6, n, el
+
+
+# --------------------------------------------------------------------- our arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1702_05156_gb300 import dmsgm, build as pbuild
+    from paper_1702_05156_gb300.synth import make_stream, spec_for
+
+    W, H, B, T, prec = args.width, args.height, args.block, args.frames, args.precision
+    frames, Hs = make_stream(spec_for(W, H, T, seed=args.seed + rank), device=dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl, tile_rows=args.tile_rows)
+    masks = dmsgm.new_mask(H, W, dev, n=T)
+
+    def one_pass():
+        for t in range(T):
+            m.process(frames[t], Hs[t], masks[t], stream=stream)
+
+    # first pass eager (initialises the state), then capture one pass
+    with torch.cuda.stream(stream):
+        one_pass()
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        one_pass()
+    stream.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g.replay()
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    h0 = time.time()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            g.replay()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    h1 = time.time()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if sampler:
+        sampler.mark(h0, h1)
+
+    # per-frame latency distribution (one eager pass, events around frames)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(T + 1)]
+    with torch.cuda.stream(stream):
+        for t in range(T):
+            evs[t].record(stream)
+            m.process(frames[t], Hs[t], masks[t], stream=stream)
+        evs[T].record(stream)
+    stream.synchronize()
+    fr_ms = np.array([evs[t].elapsed_time(evs[t + 1]) for t in range(T)])
+
+    # end to end through host buffers: pinned frames in, host masks out
+    host_frames = frames.cpu().pin_memory()
+    host_masks = torch.zeros((T, H, dmsgm.mask_words(W)), dtype=torch.int32, pin_memory=True)
+    me = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl, tile_rows=args.tile_rows)
+    for _ in range(max(1, min(args.warmup, 2))):
+        me.process_host(host_frames, Hs, host_masks, stream=stream)
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 10))
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        me.process_host(host_frames, Hs, host_masks, stream=stream)
+    f1.record(stream)
+    f1.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    if world > 1:
+        dist.barrier()
+    if sampler:
+        sampler.stop()
+
+    # aggregate: max time over ranks
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, e2e_ms = float(t[0]), float(t[1])
+    npx = W * H
+    value = world * args.steps * T * npx / (ms / 1e3) / 1e6
+    e2e_val = world * e2e_steps * T * npx / (e2e_ms / 1e3) / 1e6
+
+    if rank == 0:
+        peak, peak_kind = load_peaks()
+        bpp = bytes_per_pixel(B, prec)
+        per_launch_bytes = bpp * npx
+        avg_launch_s = ms / 1e3 / (args.steps * T)
+        achieved = per_launch_bytes / avg_launch_s / 1e9
+        tag = f"dmsgm_step_kernel {W}x{H} B{B} {prec}"
+        traffic = ncu_traffic(tag, pbuild._fingerprint())
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else "f16-state/f32-math", "data": "synthetic",
+            "config": {"workload": f"plain DMSGM {W}x{H} uint8, block {B}, {prec} state, "
+                                   f"{T} pre-staged frames per step, one fused kernel per frame "
+                                   f"replayed as a CUDA graph",
+                       "width": W, "height": H, "block": B, "frames_per_step": T,
+                       "precision": prec, "theta_s": 2.0, "theta_d": 4.0, "age_max": 30,
+                       "seed": args.seed, "pdl": bool(args.pdl),
+                       "l2": f"inputs larger than L2: {T} frames = {T * npx / 1e6:.0f} MB per step; "
+                             f"model state {2 * m.info().state_bytes / 2e6:.1f} MB stays "
+                             f"L2-resident between frames (recurrence)",
+                       "parallelism": f"replicas x{world} (one stream per GPU)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "bytes_per_launch": int(per_launch_bytes),
+                         "bytes_per_pixel": bpp, "avg_launch_us": round(avg_launch_s * 1e6, 3),
+                         "traffic": traffic, "kernel": "dmsgm_step_kernel"},
+            "frame_ms": {"p50": round(float(np.percentile(fr_ms, 50)), 5),
+                         "p99": round(float(np.percentile(fr_ms, 99)), 5),
+                         "note": "per-frame device time, eager launches, events between frames"},
+            "e2e": {"value": round(e2e_val, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": T * npx,
+                    "d2h_bytes_per_step": T * H * dmsgm.mask_words(W) * 4,
+                    "api": "dmsgm_process_host", "steps": e2e_steps},
+            "gpu_launches": args.steps * T,
+            "clocks": sampler.summary() if sampler else None,
+        }
+        if args.cpu_baseline:
+            fn = frames.cpu().numpy()
+            rate, nfr, el = cpu_oracle_rate(fn, Hs, B, budget_s=args.cpu_seconds)
+            out["cpu_baseline"] = {"value": round(rate, 3), "unit": UNIT, "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": f"first {nfr} frames of the same {W}x{H} stream, "
+                                             f"FP64 C oracle, 1 thread, {el:.1f} s"}
+        if args.extra:
+            out["extra"] = run_extras(args, dev, stream)
+        print(json.dumps(out), flush=True)
+    m.close()
+    me.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_extras(args, dev, stream):
+    """Other configurations of the same kernel, reported beside the headline:
+    4K at block 4/8, FP32/FP16 state (one pass of 100 frames per step)."""
+    import torch
+    from paper_1702_05156_gb300 import dmsgm
+    from paper_1702_05156_gb300.synth import make_stream, spec_for
+
+    res = {}
+    peak, _ = load_peaks()
+    W, H, T = 3840, 2160, args.extra_frames
+    frames, Hs = make_stream(spec_for(W, H, T, seed=args.seed), device=dev)
+    masks = dmsgm.new_mask(H, W, dev, n=T)
+    for B in (4, 8):
+        for prec in ("fp32", "fp16"):
+            m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl)
+
+            def one_pass():
+                for t in range(T):
+                    m.process(frames[t], Hs[t], masks[t], stream=stream)
+            with torch.cuda.stream(stream):
+                one_pass()
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                one_pass()
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    g.replay()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                for _ in range(reps):
+                    g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            per = ms / 1e3 / (reps * T)
+            bpp = bytes_per_pixel(B, prec)
+            ach = bpp * W * H / per / 1e9
+            res[f"4k_b{B}_{prec}"] = {"mpix_s": round(W * H / per / 1e6, 1),
+                                      "frame_us": round(per * 1e6, 3),
+                                      "bytes_per_frame": int(bpp * W * H),
+                                      "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4)}
+            m.close()
+    del frames, masks
+    torch.cuda.empty_cache()
+    return res
+
+
+# --------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    from oracle import build_oracle, oracle_step
+    from paper_1702_05156_gb300.synth import make_stream, spec_for
+
+    build_oracle()
+    W, H, B = args.width, args.height, args.block
+    per_step = args.ref_frames
+    need = per_step * (args.steps + args.warmup)
+    T = min(args.frames, need)
+    frames, Hs = make_stream(spec_for(W, H, T, seed=args.seed), device="cpu")
+    fn = frames.numpy()
+    st = None
+    idx = 0
+
+    def step():
+        nonlocal st, idx
+        for _ in range(per_step):
+            st, _ = oracle_step(fn[idx % T], Hs[idx % T], None if idx == 0 else st, block=B)
+            idx += 1
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps * per_step * W * H / el / 1e6
+    sample = (f"{per_step} frames per step of the {W}x{H} block-{B} stream, FP64 C oracle, "
+              f"1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"plain DMSGM {W}x{H} uint8, block {B}, FP64 oracle (the paper "
+                               f"ships no code; the reference arm is the oracle written from it)",
+                   "width": W, "height": H, "block": B},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }), flush=True)
+    del torch
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--block", type=int, default=4)
+    ap.add_argument("--frames", type=int, default=300)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--pdl", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--extra", type=int, default=1)
+    ap.add_argument("--extra-frames", type=int, default=100)
+    ap.add_argument("--ref-frames", type=int, default=4)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

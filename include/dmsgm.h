@@ -1,0 +1,177 @@
+/*
+ * dmsgm.h -- C ABI of the GB300 (sm_103a) DMSGM motion-mask library.
+ *
+ * The library runs the data-parallel hot path of the Dual-Mode Single
+ * Gaussian Model (Yi et al., restated in arXiv:1702.05156) on a block grid:
+ * per frame, in ONE fused kernel,
+ *   (a) motion-compensate the previous block models by the frame's
+ *       homography: each block's back-projected BxB square mixes mean,
+ *       variance and age of the <= 4 previous blocks it overlaps, weighted
+ *       by overlap area (Sec. 2.4; "tilde" values of Sec. 2.2);
+ *   (b) compute each block's mean M (Sec. 2.2, eq. for M_i) and run the
+ *       apparent/candidate match -> update -> reset -> swap (Sec. 2.2 mean,
+ *       variance and age equations; Sec. 2.3 match tests and swap rule);
+ *   (c) write the per-pixel foreground mask (I - mu_A)^2 > theta_d * var_A
+ *       (appendix "Dual-mode SGM Inner Update Code Snippet", threshold taken
+ *       against the apparent variance).
+ *
+ * Conventions
+ *   - Frames are W x H uint8, row-major, pitch W bytes, device memory,
+ *     16-byte aligned base.  W % 16 == 0, W % block == 0, H % block == 0.
+ *   - block is 4 or 8 on the GPU.  Block (bx, by) covers pixels
+ *     [bx*B, (bx+1)*B) x [by*B, (by+1)*B); pixel (x, y) has its centre at
+ *     (x + 0.5, y + 0.5).
+ *   - The homography is a host double[9], row-major, and maps CURRENT
+ *     pixel-centre coordinates to PREVIOUS ones.  It is reduced on the host
+ *     (FP64) to FP32 displacement coefficients; the GPU does no FP64 work.
+ *   - The mask is bit-packed: H rows of ceil(W/32) uint32 words; bit j of
+ *     word i in row y is pixel x = 32*i + j (LSB = leftmost).  1 = foreground.
+ *   - Model state lives on the device in two ping-pong buffers per handle
+ *     (read t-1, write t), each a structure of arrays over the Gx*Gy blocks
+ *     (row-major, bx fastest): mu_A, var_A, mu_C, var_C as FP32 or FP16,
+ *     then age_A, age_C as uint8.
+ *   - The first process() after create/reset (and any block whose
+ *     back-projection has no in-grid source) starts both models at
+ *     (M, 255, 1), the paper's candidate-reset values (Sec. 2.3).
+ *
+ * Errors: every call returns DMSGM_OK (0) or a negative code; the message of
+ * the last failure on the calling thread is in dmsgm_last_error().  Invalid
+ * arguments never touch device state.  Kernels that detect a fault on the
+ * device (a TMA wait that ran out) set a status word that dmsgm_status()
+ * reports and the next process() returns as DMSGM_ERR_DEVICE_STATUS.
+ *
+ * Threading: a handle must not be used from two host threads or two streams
+ * at once.  Different handles are independent.
+ */
+#ifndef DMSGM_H
+#define DMSGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmsgm_ctx* dmsgm_t;
+
+enum {
+    DMSGM_OK = 0,
+    DMSGM_ERR_INVALID_ARG = -1,
+    DMSGM_ERR_OOM = -2,
+    DMSGM_ERR_CUDA = -3,
+    DMSGM_ERR_TIMEOUT = -4,
+    DMSGM_ERR_DEVICE_STATUS = -5,
+    DMSGM_ERR_UNSUPPORTED = -6
+};
+
+enum { DMSGM_STATE_FP32 = 0, DMSGM_STATE_FP16 = 1 };
+
+/* Optional create-time settings; a zero-initialised struct means defaults. */
+typedef struct {
+    int precision;      /* DMSGM_STATE_FP32 (default) or DMSGM_STATE_FP16:
+                           FP16 storage of mu/var, FP32 arithmetic           */
+    void* state_mem;    /* optional caller-owned device memory for the state
+                           (>= dmsgm_state_bytes(), 256-byte aligned); it must
+                           outlive the handle.  NULL: the handle allocates.   */
+    size_t state_bytes; /* size of state_mem                                  */
+    int tile_rows;      /* rows of pixels per CTA tile (multiple of 4*block,
+                           <= 256); 0 = built-in choice                       */
+    int use_pdl;        /* 1: launch with programmatic dependent launch so a
+                           frame's pixel load overlaps the previous frame's
+                           tail; 0: plain stream order.  Default (-1 or 0
+                           from zero-init): see dmsgm_create_ex.              */
+} dmsgm_opts;
+
+/* Read-only description of a handle. */
+typedef struct {
+    int width, height, block, grid_w, grid_h, precision, age_max;
+    float theta_s, theta_d;
+    int initialized;             /* 0 until the first process()/set_state()  */
+    int parity;                  /* index of the buffer holding the state    */
+    unsigned long long frames;   /* process() calls since create/reset       */
+    size_t state_bytes;          /* device bytes (both buffers + control)    */
+    size_t host_state_bytes;     /* bytes of the packed image of get/set_state */
+    int tile_rows;               /* rows per CTA tile in use                 */
+    int device;                  /* CUDA device of the handle                */
+} dmsgm_info;
+
+/* Device bytes a handle needs for its state: a 256-byte control block plus
+ * two buffers of Gx*Gy*(4*s + 2) bytes each (s = 4 for FP32, 2 for FP16),
+ * every array 256-byte aligned.  Returns 0 for invalid sizes. */
+size_t dmsgm_state_bytes(int width, int height, int block, int precision);
+
+/* Bytes of the packed host image used by dmsgm_get_state/dmsgm_set_state:
+ * mu_A, var_A, mu_C, var_C (Gx*Gy values each, FP32 or FP16 as stored),
+ * then age_A, age_C (Gx*Gy bytes each), no padding. */
+size_t dmsgm_host_state_bytes(int width, int height, int block, int precision);
+
+/* Create a handle on the current CUDA device.  theta_s is the match
+ * threshold of Sec. 2.3, theta_d the foreground threshold, age_max the age
+ * cap of Sec. 2.2 (30 in the paper).  Validation: width, height > 0;
+ * block in {4, 8}; width % 16 == 0; width and height multiples of block;
+ * theta_s, theta_d finite and > 0; 1 <= age_max <= 255. */
+int dmsgm_create(int width, int height, int block, float theta_s, float theta_d,
+                 int age_max, dmsgm_t* out);
+int dmsgm_create_ex(int width, int height, int block, float theta_s, float theta_d,
+                    int age_max, const dmsgm_opts* opts, dmsgm_t* out);
+
+/* Destroy a handle (NULL-safe).  Synchronises the device work of the handle. */
+int dmsgm_destroy(dmsgm_t h);
+
+/* One frame, asynchronously on cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream).  frame_dev: W*H bytes of device memory, 16-byte aligned.
+ * H3x3: host, row-major, current -> previous coordinates, finite.
+ * mask_dev: device, H*ceil(W/32) uint32 words, 4-byte aligned.  frame_dev
+ * and mask_dev must stay valid until the stream reaches this work.  When a
+ * stream capture records a sequence of k calls, the handle's host-side
+ * buffer parity advances by k at capture time; replays are consistent with
+ * it when k is even (or the graph is replayed once). */
+int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9],
+                  uint32_t* mask_dev, void* cuda_stream);
+
+/* n frames from HOST memory (frames_host: n*W*H bytes, pinned for overlap)
+ * into host masks (masks_host: n*H*ceil(W/32) words), pipelined: host->device
+ * copies, kernels and device->host copies of consecutive chunks overlap on
+ * internal streams.  H3x3s: n*9 doubles.  Ordered after earlier work on
+ * cuda_stream; returns when all work is enqueued, and the results are in
+ * masks_host once cuda_stream reaches the end of it (synchronise it).  The
+ * first call allocates device staging owned by the handle. */
+int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n,
+                       const double* H3x3s, uint32_t* masks_host, void* cuda_stream);
+
+/* n handles, one frame each, in ONE persistent kernel launch over a
+ * (stream, tile) work list (handles may differ in size, block and
+ * precision; all on the current device; no handle twice).  frames_dev[i],
+ * masks_dev[i] and H3x3s[9*i..] are handle i's arguments as in
+ * dmsgm_process.  n <= DMSGM_MAX_BATCH. */
+#define DMSGM_MAX_BATCH 256
+int dmsgm_process_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
+                        const double* H3x3s, uint32_t* const* masks_dev, void* cuda_stream);
+
+/* Copy the current state to / from a packed host image (layout: see
+ * dmsgm_host_state_bytes).  Both synchronise the device.  set_state marks
+ * the handle initialised, so the next process() compensates from it. */
+int dmsgm_get_state(dmsgm_t h, void* host_buf, size_t bytes);
+int dmsgm_set_state(dmsgm_t h, const void* host_buf, size_t bytes);
+
+/* Forget the state: the next process() starts every block afresh. */
+int dmsgm_reset(dmsgm_t h);
+
+int dmsgm_get_info(dmsgm_t h, dmsgm_info* out);
+
+/* Synchronise the handle's device and read its device status word:
+ * DMSGM_OK, or DMSGM_ERR_TIMEOUT if a kernel gave up on a wait (the word is
+ * then cleared). */
+int dmsgm_status(dmsgm_t h);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* dmsgm_last_error(void);
+
+/* Library version string. */
+const char* dmsgm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMSGM_H */

@@ -1,0 +1,185 @@
+"""ctypes binding of ``libdmsgm.so`` (include/dmsgm.h).
+
+Argument marshalling only: every step of the motion-mask path runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  If the
+library is missing this module raises; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdmsgm.so")
+
+DMSGM_OK = 0
+DMSGM_ERR_INVALID_ARG = -1
+DMSGM_ERR_OOM = -2
+DMSGM_ERR_CUDA = -3
+DMSGM_ERR_TIMEOUT = -4
+DMSGM_ERR_DEVICE_STATUS = -5
+DMSGM_ERR_UNSUPPORTED = -6
+DMSGM_STATE_FP32 = 0
+DMSGM_STATE_FP16 = 1
+DMSGM_MAX_BATCH = 256
+
+# every symbol include/dmsgm.h declares
+EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm_create_ex",
+           "dmsgm_destroy", "dmsgm_process", "dmsgm_process_host", "dmsgm_process_batch",
+           "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
+           "dmsgm_status", "dmsgm_last_error", "dmsgm_version")
+
+
+class dmsgm_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("state_mem", ctypes.c_void_p),
+                ("state_bytes", ctypes.c_size_t), ("tile_rows", ctypes.c_int),
+                ("use_pdl", ctypes.c_int)]
+
+
+class dmsgm_info(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("block", ctypes.c_int),
+                ("grid_w", ctypes.c_int), ("grid_h", ctypes.c_int), ("precision", ctypes.c_int),
+                ("age_max", ctypes.c_int), ("theta_s", ctypes.c_float),
+                ("theta_d", ctypes.c_float), ("initialized", ctypes.c_int),
+                ("parity", ctypes.c_int), ("frames", ctypes.c_ulonglong),
+                ("state_bytes", ctypes.c_size_t), ("host_state_bytes", ctypes.c_size_t),
+                ("tile_rows", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class DmsgmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dmsgm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libdmsgm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"{p} is missing: build it with paper_1702_05156_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        F = ctypes.c_float
+        sig = {
+            "dmsgm_state_bytes": (S, [I, I, I, I]),
+            "dmsgm_host_state_bytes": (S, [I, I, I, I]),
+            "dmsgm_create": (I, [I, I, I, F, F, I, P]),
+            "dmsgm_create_ex": (I, [I, I, I, F, F, I, P, P]),
+            "dmsgm_destroy": (I, [P]),
+            "dmsgm_process": (I, [P, P, P, P, P]),
+            "dmsgm_process_host": (I, [P, P, I, P, P, P]),
+            "dmsgm_process_batch": (I, [I, P, P, P, P, P]),
+            "dmsgm_get_state": (I, [P, P, S]),
+            "dmsgm_set_state": (I, [P, P, S]),
+            "dmsgm_reset": (I, [P]),
+            "dmsgm_get_info": (I, [P, P]),
+            "dmsgm_status": (I, [P]),
+            "dmsgm_last_error": (ctypes.c_char_p, []),
+            "dmsgm_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != DMSGM_OK:
+        msg = load_library().dmsgm_last_error().decode(errors="replace")
+        raise DmsgmError(rc, msg)
+
+
+def _h9(H) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1))
+    return a
+
+
+# ----------------------------------------------------------- same-name functions
+def dmsgm_state_bytes(width, height, block, precision=DMSGM_STATE_FP32) -> int:
+    return load_library().dmsgm_state_bytes(width, height, block, precision)
+
+
+def dmsgm_host_state_bytes(width, height, block, precision=DMSGM_STATE_FP32) -> int:
+    return load_library().dmsgm_host_state_bytes(width, height, block, precision)
+
+
+def dmsgm_create(width, height, block, theta_s, theta_d, age_max, opts: dmsgm_opts | None = None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    if opts is None:
+        _check(lib.dmsgm_create(width, height, block, theta_s, theta_d, age_max, ctypes.byref(h)))
+    else:
+        _check(lib.dmsgm_create_ex(width, height, block, theta_s, theta_d, age_max,
+                                   ctypes.byref(opts), ctypes.byref(h)))
+    return h
+
+
+dmsgm_create_ex = dmsgm_create
+
+
+def dmsgm_destroy(h):
+    _check(load_library().dmsgm_destroy(h))
+
+
+def dmsgm_process(h, frame_ptr: int, H, mask_ptr: int, stream: int = 0):
+    Hm = _h9(H)
+    _check(load_library().dmsgm_process(h, frame_ptr, Hm.ctypes.data, mask_ptr, stream))
+
+
+def dmsgm_process_host(h, frames_ptr: int, n: int, Hs, masks_ptr: int, stream: int = 0):
+    Hm = _h9(Hs)
+    assert Hm.size == 9 * n
+    _check(load_library().dmsgm_process_host(h, frames_ptr, n, Hm.ctypes.data, masks_ptr, stream))
+
+
+def dmsgm_process_batch(handles, frame_ptrs, Hs, mask_ptrs, stream: int = 0):
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    fr = (ctypes.c_void_p * n)(*frame_ptrs)
+    mk = (ctypes.c_void_p * n)(*mask_ptrs)
+    Hm = _h9(Hs)
+    assert Hm.size == 9 * n
+    _check(load_library().dmsgm_process_batch(n, hs, fr, Hm.ctypes.data, mk, stream))
+
+
+def dmsgm_get_state(h, buf: np.ndarray):
+    _check(load_library().dmsgm_get_state(h, buf.ctypes.data, buf.nbytes))
+
+
+def dmsgm_set_state(h, buf: np.ndarray):
+    _check(load_library().dmsgm_set_state(h, buf.ctypes.data, buf.nbytes))
+
+
+def dmsgm_reset(h):
+    _check(load_library().dmsgm_reset(h))
+
+
+def dmsgm_get_info(h) -> dmsgm_info:
+    info = dmsgm_info()
+    _check(load_library().dmsgm_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def dmsgm_status(h) -> int:
+    return load_library().dmsgm_status(h)
+
+
+def dmsgm_last_error() -> str:
+    return load_library().dmsgm_last_error().decode(errors="replace")
+
+
+def dmsgm_version() -> str:
+    return load_library().dmsgm_version().decode()

@@ -1,0 +1,549 @@
+// dmsgm_api.cu -- the single-stream fused kernel and the C ABI of dmsgm.h.
+//
+// One launch per frame: a CTA loads its 256 x TILE_H pixel tile with one
+// 2-D TMA copy (cp.async.bulk.tensor) into shared memory, compensates its
+// blocks' models from the previous state buffer while the copy is in flight
+// (Sec. 2.4), then reduces the pixels, runs the dual-mode update (Sec.
+// 2.2-2.3), writes the next state buffer and the bit-packed mask.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "dmsgm_internal.h"
+
+namespace dmsgm {
+
+static thread_local char g_err[512];
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+void clear_error() { g_err[0] = 0; }
+
+// ------------------------------------------------------------------ kernel
+constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // 2 s: only a broken copy gets here
+
+template <int B, typename T, int RPT>
+__global__ void __launch_bounds__(kThreads)
+    dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, int* status) {
+    constexpr int TILE_H = 4 * B * RPT;
+    __shared__ __align__(128) uint8_t tile[TILE_H * kTileW];
+    __shared__ __align__(8) uint64_t bar;
+    const int tx0 = blockIdx.x * kTileW;
+    const int ty0 = blockIdx.y * TILE_H;
+    if (threadIdx.x == 0) {
+        prefetch_tensormap(&tmap);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, TILE_H * kTileW);
+        tma_load_2d(tile, &tmap, tx0, ty0, &bar);
+    }
+    // The pixels do not depend on the previous frame's kernel; the state does.
+    pdl_wait();
+    pdl_launch_dependents();
+    Comp comp[RPT];
+    compensate_tile<B, T, RPT>(a, tx0, ty0, comp);
+    const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
+    if (__syncthreads_or(!ok)) {
+        // report, give the copy one more bounded chance to land, and leave
+        if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+        mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
+        return;
+    }
+    finish_tile<B, T, RPT>(a, tile, tx0, ty0, comp);
+}
+
+template <int B, typename T, int RPT>
+static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, int* status,
+                                 cudaStream_t s, bool pdl) {
+    constexpr int TILE_H = 4 * B * RPT;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, dmsgm_step_kernel<B, T, RPT>, tmap, a, status);
+}
+
+static cudaError_t launch_step(int B, int prec, int rpt, const CUtensorMap& tmap,
+                               const StreamArgs& a, int* status, cudaStream_t s, bool pdl) {
+#define DMSGM_CASE(BB, TT, RR) \
+    if (B == BB && rpt == RR) return launch_step_t<BB, TT, RR>(tmap, a, status, s, pdl);
+    if (prec == DMSGM_STATE_FP32) {
+        DMSGM_CASE(4, float, 1) DMSGM_CASE(4, float, 2) DMSGM_CASE(4, float, 4)
+        DMSGM_CASE(8, float, 1) DMSGM_CASE(8, float, 2) DMSGM_CASE(8, float, 4)
+    } else {
+        DMSGM_CASE(4, __half, 1) DMSGM_CASE(4, __half, 2) DMSGM_CASE(4, __half, 4)
+        DMSGM_CASE(8, __half, 1) DMSGM_CASE(8, __half, 2) DMSGM_CASE(8, __half, 4)
+    }
+#undef DMSGM_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ helpers
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static bool valid_dims(int W, int H, int B) {
+    return W > 0 && H > 0 && (B == 4 || B == 8) && W % 16 == 0 && W % B == 0 && H % B == 0 &&
+           W <= (1 << 20) && H <= (1 << 20);
+}
+
+static size_t buf_bytes(size_t N, int prec) {
+    const size_t s = prec == DMSGM_STATE_FP16 ? 2 : 4;
+    return 4 * align256(N * s) + 2 * align256(N);
+}
+
+static void carve(dmsgm_ctx* h) {
+    const size_t N = size_t(h->Gx) * h->Gy;
+    const size_t s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
+    char* p = static_cast<char*>(h->mem);
+    h->status_dev = reinterpret_cast<int*>(p);
+    p += 256;
+    for (int b = 0; b < 2; ++b) {
+        StateBuf& sb = h->buf[b];
+        sb.muA = p; p += align256(N * s);
+        sb.varA = p; p += align256(N * s);
+        sb.muC = p; p += align256(N * s);
+        sb.varC = p; p += align256(N * s);
+        sb.ageA = reinterpret_cast<uint8_t*>(p); p += align256(N);
+        sb.ageC = reinterpret_cast<uint8_t*>(p); p += align256(N);
+    }
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a W x H uint8 frame with a kTileW x tile_rows box.
+static int encode_frame_map(const dmsgm_ctx* h, const void* frame, CUtensorMap* out) {
+    auto enc = encode_fn();
+    if (!enc) return fail(DMSGM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    cuuint64_t dims[2] = {cuuint64_t(h->W), cuuint64_t(h->H)};
+    cuuint64_t strides[1] = {cuuint64_t(h->W)};
+    cuuint32_t box[2] = {cuuint32_t(kTileW), cuuint32_t(h->tile_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(frame), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(DMSGM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+    return DMSGM_OK;
+}
+
+static int frame_map(dmsgm_ctx* h, const void* frame, const CUtensorMap** out) {
+    for (int i = 0; i < kTmapCache; ++i)
+        if (h->tmap[i].ptr == frame) { *out = &h->tmap[i].map; return DMSGM_OK; }
+    const int slot = h->tmap_next;
+    h->tmap_next = (h->tmap_next + 1) % kTmapCache;
+    h->tmap[slot].ptr = nullptr;
+    int rc = encode_frame_map(h, frame, &h->tmap[slot].map);
+    if (rc) return rc;
+    h->tmap[slot].ptr = frame;
+    *out = &h->tmap[slot].map;
+    return DMSGM_OK;
+}
+
+bool make_coef(const double m[9], Coef* c) {
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(m[i])) return false;
+    // displacement-form coefficients in FP64, each split into hi + lo floats
+    const double v[9] = {m[0] - m[8], m[1], m[2], m[3], m[4] - m[8], m[5], m[6], m[7], m[8]};
+    float* hi = &c->ax0;
+    float* lo = &c->ax0l;
+    for (int i = 0; i < 9; ++i) {
+        hi[i] = float(v[i]);
+        lo[i] = float(v[i] - double(hi[i]));
+        if (!std::isfinite(hi[i]) || !std::isfinite(lo[i])) return false;
+    }
+    return true;
+}
+
+void fill_args(const dmsgm_ctx* h, const Coef& c, uint32_t* mask_dev, StreamArgs* a) {
+    a->prev = h->buf[h->parity];
+    a->next = h->buf[h->parity ^ 1];
+    a->mask = mask_dev;
+    a->W = h->W;
+    a->H = h->H;
+    a->Gx = h->Gx;
+    a->Gy = h->Gy;
+    a->mask_words = (h->W + 31) / 32;
+    a->first = h->initialized ? 0 : 1;
+    a->age_max = h->age_max;
+    a->theta_s = h->theta_s;
+    a->theta_d = h->theta_d;
+    a->coef = c;
+}
+
+void advance(dmsgm_ctx* h) {
+    h->parity ^= 1;
+    h->initialized = true;
+    h->frames++;
+}
+
+static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x3,
+                       uint32_t* mask_dev, cudaStream_t s) {
+    Coef c;
+    if (!make_coef(H3x3, &c)) return fail(DMSGM_ERR_INVALID_ARG, "homography is not finite in FP32");
+    const CUtensorMap* tm = nullptr;
+    int rc = frame_map(h, frame_dev, &tm);
+    if (rc) return rc;
+    StreamArgs a;
+    fill_args(h, c, mask_dev, &a);
+    cudaError_t e = launch_step(h->B, h->prec, h->tile_rows / (4 * h->B), *tm, a, h->status_dev,
+                                s, h->use_pdl != 0);
+    if (e != cudaSuccess) return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    advance(h);
+    return DMSGM_OK;
+}
+
+static void free_stage(dmsgm_ctx* h) {
+    HostStage& st = h->stage;
+    for (int i = 0; i < 2; ++i) {
+        if (st.frames[i]) cudaFree(st.frames[i]);
+        if (st.masks[i]) cudaFree(st.masks[i]);
+        if (st.ev_in[i]) cudaEventDestroy(st.ev_in[i]);
+        if (st.ev_k[i]) cudaEventDestroy(st.ev_k[i]);
+        if (st.ev_out[i]) cudaEventDestroy(st.ev_out[i]);
+    }
+    if (st.ev_start) cudaEventDestroy(st.ev_start);
+    if (st.h2d) cudaStreamDestroy(st.h2d);
+    if (st.d2h) cudaStreamDestroy(st.d2h);
+    st = HostStage();
+}
+
+static int ensure_stage(dmsgm_ctx* h) {
+    HostStage& st = h->stage;
+    if (st.slots) return DMSGM_OK;
+    const size_t fbytes = size_t(h->W) * h->H;
+    const size_t mbytes = size_t(h->H) * ((h->W + 31) / 32) * 4;
+    // chunks of ~16 MB of frames, 1..32 frames
+    int chunk = int(std::max<size_t>(1, std::min<size_t>(32, (16u << 20) / fbytes)));
+    st.chunk = chunk;
+    auto bad = [&](cudaError_t e) {
+        free_stage(h);
+        return fail(e == cudaErrorMemoryAllocation ? DMSGM_ERR_OOM : DMSGM_ERR_CUDA,
+                    "staging setup failed: %s", cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    for (int i = 0; i < 2; ++i) {
+        if ((e = cudaMalloc(&st.frames[i], fbytes * chunk)) != cudaSuccess) return bad(e);
+        if ((e = cudaMalloc(&st.masks[i], mbytes * chunk)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&st.ev_in[i], cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&st.ev_k[i], cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&st.ev_out[i], cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+    }
+    if ((e = cudaEventCreateWithFlags(&st.ev_start, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+    if ((e = cudaStreamCreateWithFlags(&st.h2d, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+    if ((e = cudaStreamCreateWithFlags(&st.d2h, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+    st.slots = 2;
+    return DMSGM_OK;
+}
+
+}  // namespace dmsgm
+
+using namespace dmsgm;
+
+// ================================================================== C ABI
+extern "C" {
+
+const char* dmsgm_last_error(void) { return g_err; }
+
+const char* dmsgm_version(void) { return "dmsgm-gb300 0.1 (sm_103a)"; }
+
+size_t dmsgm_state_bytes(int W, int H, int B, int prec) {
+    if (!valid_dims(W, H, B) || (prec != DMSGM_STATE_FP32 && prec != DMSGM_STATE_FP16)) return 0;
+    const size_t N = size_t(W / B) * (H / B);
+    return 256 + 2 * buf_bytes(N, prec);
+}
+
+size_t dmsgm_host_state_bytes(int W, int H, int B, int prec) {
+    if (!valid_dims(W, H, B) || (prec != DMSGM_STATE_FP32 && prec != DMSGM_STATE_FP16)) return 0;
+    const size_t N = size_t(W / B) * (H / B);
+    return N * (4 * (prec == DMSGM_STATE_FP16 ? 2 : 4) + 2);
+}
+
+int dmsgm_create(int W, int H, int B, float ts, float td, int age_max, dmsgm_t* out) {
+    return dmsgm_create_ex(W, H, B, ts, td, age_max, nullptr, out);
+}
+
+int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const dmsgm_opts* o,
+                    dmsgm_t* out) {
+    clear_error();
+    if (!out) return fail(DMSGM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_dims(W, H, B))
+        return fail(DMSGM_ERR_INVALID_ARG,
+                    "invalid size %dx%d block %d (need block 4 or 8, W%%16==0, W and H "
+                    "multiples of block, <= 2^20)", W, H, B);
+    if (!(std::isfinite(ts) && ts > 0) || !(std::isfinite(td) && td > 0))
+        return fail(DMSGM_ERR_INVALID_ARG, "theta_s and theta_d must be finite and > 0");
+    if (age_max < 1 || age_max > 255) return fail(DMSGM_ERR_INVALID_ARG, "age_max must be in [1, 255]");
+    dmsgm_opts opts = {};
+    if (o) opts = *o;
+    if (opts.precision != DMSGM_STATE_FP32 && opts.precision != DMSGM_STATE_FP16)
+        return fail(DMSGM_ERR_INVALID_ARG, "unknown precision %d", opts.precision);
+    int tile_rows = opts.tile_rows ? opts.tile_rows : 32;
+    const int rpt = tile_rows / (4 * B);
+    if (tile_rows % (4 * B) != 0 || !(rpt == 1 || rpt == 2 || rpt == 4))
+        return fail(DMSGM_ERR_INVALID_ARG, "tile_rows %d must be 4*block*{1,2,4}", tile_rows);
+    const size_t need = dmsgm_state_bytes(W, H, B, opts.precision);
+    if (opts.state_mem) {
+        if (opts.state_bytes < need)
+            return fail(DMSGM_ERR_INVALID_ARG, "state_mem holds %zu bytes, need %zu", opts.state_bytes, need);
+        if (reinterpret_cast<uintptr_t>(opts.state_mem) % 256)
+            return fail(DMSGM_ERR_INVALID_ARG, "state_mem must be 256-byte aligned");
+    }
+    int dev = 0;
+    DMSGM_CUDA_TRY(cudaGetDevice(&dev));
+    dmsgm_ctx* h = new (std::nothrow) dmsgm_ctx();
+    if (!h) return fail(DMSGM_ERR_OOM, "host allocation failed");
+    h->W = W; h->H = H; h->B = B; h->Gx = W / B; h->Gy = H / B;
+    h->prec = opts.precision;
+    h->age_max = age_max;
+    h->theta_s = ts; h->theta_d = td;
+    h->device = dev;
+    h->tile_rows = tile_rows;
+    h->use_pdl = opts.use_pdl > 0 ? 1 : 0;
+    h->state_bytes = need;
+    if (opts.state_mem) {
+        h->mem = opts.state_mem;
+        h->owns_mem = false;
+    } else {
+        cudaError_t e = cudaMalloc(&h->mem, need);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail(e == cudaErrorMemoryAllocation ? DMSGM_ERR_OOM : DMSGM_ERR_CUDA,
+                        "cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+        }
+        h->owns_mem = true;
+    }
+    carve(h);
+    cudaError_t e = cudaMemset(h->mem, 0, need);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        if (h->owns_mem) cudaFree(h->mem);
+        delete h;
+        return fail(DMSGM_ERR_CUDA, "state init failed: %s", cudaGetErrorString(e));
+    }
+    h->parity = 0;
+    h->initialized = false;
+    h->frames = 0;
+    h->tmap_next = 0;
+    *out = h;
+    return DMSGM_OK;
+}
+
+int dmsgm_destroy(dmsgm_t h) {
+    clear_error();
+    if (!h) return DMSGM_OK;
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    free_stage(h);
+    if (h->owns_mem && h->mem) cudaFree(h->mem);
+    delete h;
+    if (e != cudaSuccess) return fail(DMSGM_ERR_CUDA, "synchronize failed: %s", cudaGetErrorString(e));
+    return DMSGM_OK;
+}
+
+int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9], uint32_t* mask_dev,
+                  void* stream) {
+    clear_error();
+    if (!h || !frame_dev || !H3x3 || !mask_dev) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(frame_dev) % 16)
+        return fail(DMSGM_ERR_INVALID_ARG, "frame must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(mask_dev) % 4)
+        return fail(DMSGM_ERR_INVALID_ARG, "mask must be 4-byte aligned");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", h->device);
+    return process_one(h, frame_dev, H3x3, mask_dev, static_cast<cudaStream_t>(stream));
+}
+
+int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n, const double* Hs,
+                       uint32_t* masks_host, void* stream) {
+    clear_error();
+    if (!h || n < 0 || (n > 0 && (!frames_host || !Hs || !masks_host)))
+        return fail(DMSGM_ERR_INVALID_ARG, "invalid argument");
+    for (long i = 0; i < 9L * n; ++i)
+        if (!std::isfinite(Hs[i])) return fail(DMSGM_ERR_INVALID_ARG, "homography %ld is not finite", i / 9);
+    if (n == 0) return DMSGM_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", h->device);
+    int rc = ensure_stage(h);
+    if (rc) return rc;
+    HostStage& st = h->stage;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t fbytes = size_t(h->W) * h->H;
+    const size_t mwords = size_t(h->H) * ((h->W + 31) / 32);
+    DMSGM_CUDA_TRY(cudaEventRecord(st.ev_start, s));
+    DMSGM_CUDA_TRY(cudaStreamWaitEvent(st.h2d, st.ev_start, 0));
+    for (int c0 = 0, ci = 0; c0 < n; c0 += st.chunk, ++ci) {
+        const int cnt = std::min(st.chunk, n - c0);
+        const int sl = ci & 1;
+        // frames of this chunk -> slot sl, once the kernels that read the
+        // slot two chunks ago are done
+        DMSGM_CUDA_TRY(cudaStreamWaitEvent(st.h2d, st.ev_k[sl], 0));
+        DMSGM_CUDA_TRY(cudaMemcpyAsync(st.frames[sl], frames_host + size_t(c0) * fbytes,
+                                       size_t(cnt) * fbytes, cudaMemcpyHostToDevice, st.h2d));
+        DMSGM_CUDA_TRY(cudaEventRecord(st.ev_in[sl], st.h2d));
+        DMSGM_CUDA_TRY(cudaStreamWaitEvent(s, st.ev_in[sl], 0));
+        DMSGM_CUDA_TRY(cudaStreamWaitEvent(s, st.ev_out[sl], 0));
+        for (int f = 0; f < cnt; ++f) {
+            rc = process_one(h, st.frames[sl] + size_t(f) * fbytes, Hs + 9 * size_t(c0 + f),
+                             st.masks[sl] + size_t(f) * mwords, s);
+            if (rc) return rc;
+        }
+        DMSGM_CUDA_TRY(cudaEventRecord(st.ev_k[sl], s));
+        DMSGM_CUDA_TRY(cudaStreamWaitEvent(st.d2h, st.ev_k[sl], 0));
+        DMSGM_CUDA_TRY(cudaMemcpyAsync(masks_host + size_t(c0) * mwords, st.masks[sl],
+                                       size_t(cnt) * mwords * 4, cudaMemcpyDeviceToHost, st.d2h));
+        DMSGM_CUDA_TRY(cudaEventRecord(st.ev_out[sl], st.d2h));
+    }
+    DMSGM_CUDA_TRY(cudaStreamWaitEvent(s, st.ev_out[0], 0));
+    DMSGM_CUDA_TRY(cudaStreamWaitEvent(s, st.ev_out[1], 0));
+    return DMSGM_OK;
+}
+
+int dmsgm_process_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
+                        const double* Hs, uint32_t* const* masks_dev, void* stream) {
+    clear_error();
+    if (n < 0 || n > DMSGM_MAX_BATCH) return fail(DMSGM_ERR_INVALID_ARG, "n=%d out of range", n);
+    if (n == 0) return DMSGM_OK;
+    if (!hs || !frames_dev || !Hs || !masks_dev) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !frames_dev[i] || !masks_dev[i])
+            return fail(DMSGM_ERR_INVALID_ARG, "NULL entry %d", i);
+        if (reinterpret_cast<uintptr_t>(frames_dev[i]) % 16 || reinterpret_cast<uintptr_t>(masks_dev[i]) % 4)
+            return fail(DMSGM_ERR_INVALID_ARG, "entry %d misaligned", i);
+        if (hs[i]->device != hs[0]->device)
+            return fail(DMSGM_ERR_INVALID_ARG, "handles on different devices");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(DMSGM_ERR_INVALID_ARG, "handle %d appears twice", i);
+        Coef c;
+        if (!make_coef(Hs + 9 * size_t(i), &c))
+            return fail(DMSGM_ERR_INVALID_ARG, "homography %d is not finite in FP32", i);
+    }
+    DeviceGuard g(hs[0]->device);
+    if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", hs[0]->device);
+    return launch_batch(n, hs, frames_dev, Hs, masks_dev, static_cast<cudaStream_t>(stream));
+}
+
+int dmsgm_get_state(dmsgm_t h, void* host_buf, size_t bytes) {
+    clear_error();
+    if (!h || !host_buf) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = dmsgm_host_state_bytes(h->W, h->H, h->B, h->prec);
+    if (bytes < need) return fail(DMSGM_ERR_INVALID_ARG, "buffer holds %zu bytes, need %zu", bytes, need);
+    DeviceGuard g(h->device);
+    DMSGM_CUDA_TRY(cudaDeviceSynchronize());
+    const size_t N = size_t(h->Gx) * h->Gy, s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
+    const StateBuf& sb = h->buf[h->parity];
+    char* p = static_cast<char*>(host_buf);
+    const void* src[6] = {sb.muA, sb.varA, sb.muC, sb.varC, sb.ageA, sb.ageC};
+    const size_t len[6] = {N * s, N * s, N * s, N * s, N, N};
+    for (int i = 0; i < 6; ++i) {
+        DMSGM_CUDA_TRY(cudaMemcpy(p, src[i], len[i], cudaMemcpyDeviceToHost));
+        p += len[i];
+    }
+    return DMSGM_OK;
+}
+
+int dmsgm_set_state(dmsgm_t h, const void* host_buf, size_t bytes) {
+    clear_error();
+    if (!h || !host_buf) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = dmsgm_host_state_bytes(h->W, h->H, h->B, h->prec);
+    if (bytes < need) return fail(DMSGM_ERR_INVALID_ARG, "buffer holds %zu bytes, need %zu", bytes, need);
+    DeviceGuard g(h->device);
+    DMSGM_CUDA_TRY(cudaDeviceSynchronize());
+    const size_t N = size_t(h->Gx) * h->Gy, s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
+    const StateBuf& sb = h->buf[h->parity];
+    const char* p = static_cast<const char*>(host_buf);
+    void* dst[6] = {sb.muA, sb.varA, sb.muC, sb.varC, sb.ageA, sb.ageC};
+    const size_t len[6] = {N * s, N * s, N * s, N * s, N, N};
+    for (int i = 0; i < 6; ++i) {
+        DMSGM_CUDA_TRY(cudaMemcpy(dst[i], p, len[i], cudaMemcpyHostToDevice));
+        p += len[i];
+    }
+    DMSGM_CUDA_TRY(cudaDeviceSynchronize());
+    h->initialized = true;
+    return DMSGM_OK;
+}
+
+int dmsgm_reset(dmsgm_t h) {
+    clear_error();
+    if (!h) return fail(DMSGM_ERR_INVALID_ARG, "NULL handle");
+    h->initialized = false;
+    h->frames = 0;
+    return DMSGM_OK;
+}
+
+int dmsgm_get_info(dmsgm_t h, dmsgm_info* o) {
+    clear_error();
+    if (!h || !o) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
+    o->width = h->W; o->height = h->H; o->block = h->B;
+    o->grid_w = h->Gx; o->grid_h = h->Gy;
+    o->precision = h->prec; o->age_max = h->age_max;
+    o->theta_s = h->theta_s; o->theta_d = h->theta_d;
+    o->initialized = h->initialized ? 1 : 0;
+    o->parity = h->parity;
+    o->frames = h->frames;
+    o->state_bytes = h->state_bytes;
+    o->host_state_bytes = dmsgm_host_state_bytes(h->W, h->H, h->B, h->prec);
+    o->tile_rows = h->tile_rows;
+    o->device = h->device;
+    return DMSGM_OK;
+}
+
+int dmsgm_status(dmsgm_t h) {
+    clear_error();
+    if (!h) return fail(DMSGM_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard g(h->device);
+    DMSGM_CUDA_TRY(cudaDeviceSynchronize());
+    int word = 0;
+    DMSGM_CUDA_TRY(cudaMemcpy(&word, h->status_dev, sizeof word, cudaMemcpyDeviceToHost));
+    if (word) {
+        DMSGM_CUDA_TRY(cudaMemset(h->status_dev, 0, sizeof word));
+        DMSGM_CUDA_TRY(cudaDeviceSynchronize());
+        return fail(DMSGM_ERR_TIMEOUT, "a kernel gave up waiting for its pixel tile (status 0x%x)", word);
+    }
+    return DMSGM_OK;
+}
+
+}  // extern "C"

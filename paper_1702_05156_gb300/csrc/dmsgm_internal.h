@@ -1,0 +1,82 @@
+// dmsgm_internal.h -- host-side internals shared by the library's translation
+// units (not part of the C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+
+#include "dmsgm.h"
+#include "dmsgm_device.cuh"
+
+namespace dmsgm {
+
+// Thread-local error message + code helper.
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+#define DMSGM_CUDA_TRY(call)                                                           \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return ::dmsgm::fail(DMSGM_ERR_CUDA, "%s failed: %s", #call,               \
+                                 cudaGetErrorString(e_));                              \
+    } while (0)
+
+constexpr int kTmapCache = 16;
+
+struct HostStage {              // device staging of dmsgm_process_host
+    int chunk = 0;              // frames per chunk
+    int slots = 0;
+    uint8_t* frames[2] = {nullptr, nullptr};
+    uint32_t* masks[2] = {nullptr, nullptr};
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr};
+    cudaEvent_t ev_k[2] = {nullptr, nullptr};
+    cudaEvent_t ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr;
+};
+
+}  // namespace dmsgm
+
+struct dmsgm_ctx {
+    int W, H, B, Gx, Gy, prec, age_max;
+    float theta_s, theta_d;
+    int device;
+    int tile_rows;
+    int use_pdl;
+    void* mem;                   // control block + two state buffers
+    bool owns_mem;
+    size_t state_bytes;
+    int* status_dev;             // device status word (inside mem)
+    dmsgm::StateBuf buf[2];
+    int parity;                  // buffer holding the current state
+    bool initialized;
+    unsigned long long frames;
+    struct {
+        const void* ptr;
+        CUtensorMap map;
+    } tmap[dmsgm::kTmapCache];
+    int tmap_next;
+    dmsgm::HostStage stage;
+};
+
+namespace dmsgm {
+
+// FP64 homography -> FP32 displacement coefficients; false if not finite.
+bool make_coef(const double H3x3[9], Coef* c);
+
+// Fill the per-frame kernel arguments of handle h (reads h->parity etc.).
+void fill_args(const dmsgm_ctx* h, const Coef& c, uint32_t* mask_dev, StreamArgs* a);
+
+// Advance the handle's bookkeeping after a frame has been enqueued.
+void advance(dmsgm_ctx* h);
+
+// Launch the batched persistent kernel (dmsgm_batch.cu).
+int launch_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
+                 const double* H3x3s, uint32_t* const* masks_dev, cudaStream_t stream);
+
+}  // namespace dmsgm

@@ -1,0 +1,154 @@
+"""Pythonic wrapper of the C ABI: a handle per video stream.
+
+``Dmsgm(W, H, block).process(frame, H3x3)`` runs one frame of the fused
+motion-compensated dual-mode SGM step on the GPU and returns the bit-packed
+foreground mask.  Tensors are only containers here; all the work happens in
+libdmsgm.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DMSGM_STATE_FP16, DMSGM_STATE_FP32
+
+
+def mask_words(width: int) -> int:
+    """uint32 words per mask row."""
+    return (width + 31) // 32
+
+
+def new_mask(height: int, width: int, device="cuda", n: int | None = None) -> torch.Tensor:
+    shape = (height, mask_words(width)) if n is None else (n, height, mask_words(width))
+    return torch.zeros(shape, dtype=torch.int32, device=device)
+
+
+def unpack_mask(words, width: int) -> np.ndarray:
+    """Bit-packed mask (..., H, ceil(W/32)) -> uint8 (..., H, W), 1 = foreground.
+    Bit j of word i is pixel 32*i + j (LSB first)."""
+    if isinstance(words, torch.Tensor):
+        words = words.detach().cpu().numpy()
+    w = np.ascontiguousarray(words).astype(np.uint32, copy=False)
+    bits = np.unpackbits(w.view(np.uint8), axis=-1, bitorder="little")
+    return bits[..., :width]
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Dmsgm:
+    """One video stream's model state on the current CUDA device."""
+
+    def __init__(self, width: int, height: int, block: int = 4, theta_s: float = 2.0,
+                 theta_d: float = 4.0, age_max: int = 30, precision: str = "fp32",
+                 tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None):
+        prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
+        opts = _lib.dmsgm_opts()
+        opts.precision = prec
+        opts.tile_rows = tile_rows
+        opts.use_pdl = 1 if use_pdl else 0
+        self._state_mem = state_mem
+        if state_mem is not None:
+            opts.state_mem = state_mem.data_ptr()
+            opts.state_bytes = state_mem.numel() * state_mem.element_size()
+        self.width, self.height, self.block = width, height, block
+        self.precision = precision
+        self._h = _lib.dmsgm_create(width, height, block, theta_s, theta_d, age_max, opts)
+        info = self.info()
+        self.grid_w, self.grid_h = info.grid_w, info.grid_h
+
+    # ------------------------------------------------------------------ frames
+    def process(self, frame: torch.Tensor, H, mask: torch.Tensor | None = None, stream=None):
+        """Enqueue one frame (uint8 (H, W) on the GPU); returns the int32 mask
+        tensor (H, ceil(W/32)) the kernel writes."""
+        assert frame.dtype == torch.uint8 and frame.is_cuda and frame.is_contiguous()
+        assert tuple(frame.shape) == (self.height, self.width)
+        if mask is None:
+            mask = new_mask(self.height, self.width, frame.device)
+        assert mask.is_cuda and mask.dtype == torch.int32 and mask.is_contiguous()
+        assert tuple(mask.shape) == (self.height, mask_words(self.width))
+        _lib.dmsgm_process(self._h, frame.data_ptr(), H, mask.data_ptr(), _stream_handle(stream))
+        return mask
+
+    def process_host(self, frames: torch.Tensor, Hs, masks: torch.Tensor | None = None,
+                     stream=None):
+        """Enqueue n frames from host memory (uint8 (n, H, W), pinned for
+        overlap) into host masks (int32 (n, H, ceil(W/32)))."""
+        assert frames.dtype == torch.uint8 and not frames.is_cuda and frames.is_contiguous()
+        n = frames.shape[0]
+        if masks is None:
+            masks = torch.zeros((n, self.height, mask_words(self.width)), dtype=torch.int32,
+                                pin_memory=True)
+        assert not masks.is_cuda and masks.is_contiguous()
+        _lib.dmsgm_process_host(self._h, frames.data_ptr(), n, np.asarray(Hs),
+                                masks.data_ptr(), _stream_handle(stream))
+        return masks
+
+    # ------------------------------------------------------------------ state
+    def _layout(self):
+        n = self.grid_w * self.grid_h
+        fdt = np.float16 if self.precision == "fp16" else np.float32
+        return n, fdt
+
+    def get_state(self) -> dict:
+        """Current state as arrays of shape (grid_h, grid_w) (synchronises)."""
+        n, fdt = self._layout()
+        buf = np.zeros(self.info().host_state_bytes, dtype=np.uint8)
+        _lib.dmsgm_get_state(self._h, buf)
+        fs = np.dtype(fdt).itemsize
+        out, off = {}, 0
+        for name in ("muA", "varA", "muC", "varC"):
+            out[name] = buf[off:off + n * fs].view(fdt).reshape(self.grid_h, self.grid_w).copy()
+            off += n * fs
+        for name in ("ageA", "ageC"):
+            out[name] = buf[off:off + n].reshape(self.grid_h, self.grid_w).copy()
+            off += n
+        return out
+
+    def set_state(self, st: dict):
+        n, fdt = self._layout()
+        parts = [np.ascontiguousarray(st[k], dtype=fdt).reshape(-1)
+                 for k in ("muA", "varA", "muC", "varC")]
+        parts += [np.ascontiguousarray(st[k], dtype=np.uint8).reshape(-1) for k in ("ageA", "ageC")]
+        buf = np.concatenate([p.view(np.uint8) for p in parts])
+        assert buf.size == self.info().host_state_bytes
+        _lib.dmsgm_set_state(self._h, buf)
+
+    def reset(self):
+        _lib.dmsgm_reset(self._h)
+
+    def info(self) -> _lib.dmsgm_info:
+        return _lib.dmsgm_get_info(self._h)
+
+    def status(self) -> int:
+        return _lib.dmsgm_status(self._h)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.dmsgm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def process_batch(models, frames, Hs, masks, stream=None):
+    """One frame for each of several handles in one launch."""
+    _lib.dmsgm_process_batch([m.handle for m in models], [f.data_ptr() for f in frames],
+                             np.asarray(Hs), [k.data_ptr() for k in masks],
+                             _stream_handle(stream))

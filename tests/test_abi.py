@@ -1,0 +1,98 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+symbol include/dmsgm.h declares; argument validation and size arithmetic
+need no GPU (they return before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1702_05156_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "dmsgm.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(dmsgm_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    lib = L.load_library()
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(L.EXPORTS), declared ^ set(L.EXPORTS)
+
+
+def test_version_and_sizes(L):
+    assert "sm_103a" in L.dmsgm_version()
+    # 1920x1080, B=4: 480x270 blocks; FP32 buffer = 4 arrays of N*4 + 2 of N,
+    # each rounded up to 256 bytes, two buffers plus a 256-byte control block
+    N = 480 * 270
+    r = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    assert L.dmsgm_state_bytes(1920, 1080, 4, 0) == 256 + 2 * (4 * r(4 * N) + 2 * r(N))
+    assert L.dmsgm_state_bytes(1920, 1080, 4, 1) == 256 + 2 * (4 * r(2 * N) + 2 * r(N))
+    assert L.dmsgm_host_state_bytes(1920, 1080, 4, 0) == N * 18
+    assert L.dmsgm_host_state_bytes(3840, 2160, 8, 1) == 480 * 270 * 10
+    assert L.dmsgm_state_bytes(100, 100, 4, 0) == 0       # W % 16 != 0
+    assert L.dmsgm_state_bytes(320, 240, 5, 0) == 0       # block 5
+    assert L.dmsgm_state_bytes(320, 242, 4, 0) == 0       # H % B != 0
+    assert L.dmsgm_state_bytes(320, 240, 4, 7) == 0       # precision
+
+
+@pytest.mark.parametrize("args", [
+    (100, 240, 4, 2.0, 4.0, 30),     # W % 16
+    (320, 240, 5, 2.0, 4.0, 30),     # block
+    (320, 244, 8, 2.0, 4.0, 30),     # H % B
+    (0, 240, 4, 2.0, 4.0, 30),
+    (320, 240, 4, 0.0, 4.0, 30),     # theta_s
+    (320, 240, 4, 2.0, float("nan"), 30),
+    (320, 240, 4, 2.0, 4.0, 0),      # age_max
+    (320, 240, 4, 2.0, 4.0, 256),
+])
+def test_create_rejects_invalid(L, args):
+    lib = L.load_library()
+    h = ctypes.c_void_p(123)
+    rc = lib.dmsgm_create(*args, ctypes.byref(h))
+    assert rc == L.DMSGM_ERR_INVALID_ARG
+    assert h.value is None
+    assert L.dmsgm_last_error()
+
+
+def test_null_arguments(L):
+    lib = L.load_library()
+    assert lib.dmsgm_destroy(None) == 0
+    assert lib.dmsgm_process(None, None, None, None, None) == L.DMSGM_ERR_INVALID_ARG
+    assert lib.dmsgm_reset(None) == L.DMSGM_ERR_INVALID_ARG
+    assert lib.dmsgm_process_batch(-1, None, None, None, None, None) == L.DMSGM_ERR_INVALID_ARG
+    assert lib.dmsgm_process_batch(0, None, None, None, None, None) == 0
+    assert lib.dmsgm_process_batch(L.DMSGM_MAX_BATCH + 1, None, None, None, None, None) == \
+        L.DMSGM_ERR_INVALID_ARG
+
+
+def test_package_import_does_not_need_library():
+    import importlib
+    import paper_1702_05156_gb300.synth as s  # noqa: F401
+    importlib.import_module("paper_1702_05156_gb300")
+
+
+def test_product_package_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_1702_05156_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                with open(os.path.join(dirpath, fn)) as f:
+                    src = f.read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), fn
+                assert "dmsgm_oracle" not in src, fn
