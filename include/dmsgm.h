@@ -28,8 +28,10 @@
  *     word i in row y is pixel x = 32*i + j (LSB = leftmost).  1 = foreground.
  *   - Model state lives on the device in two ping-pong buffers per handle
  *     (read t-1, write t), each a structure of arrays over the Gx*Gy blocks
- *     (row-major, bx fastest): mu_A, var_A, mu_C, var_C as FP32 or FP16,
- *     then age_A, age_C as uint8.
+ *     (row-major, bx fastest): mu, var and age, where entry k of each array
+ *     holds the apparent and the candidate value of block k side by side
+ *     ((mu_A, mu_C) and (var_A, var_C) as FP32 or FP16 pairs, (age_A, age_C)
+ *     as a byte pair).
  *   - The first process() after create/reset (and any block whose
  *     back-projection has no in-grid source) starts both models at
  *     (M, 255, 1), the paper's candidate-reset values (Sec. 2.3).
@@ -38,7 +40,7 @@
  * the last failure on the calling thread is in dmsgm_last_error().  Invalid
  * arguments never touch device state.  Kernels that detect a fault on the
  * device (a TMA wait that ran out) set a status word that dmsgm_status()
- * reports and the next process() returns as DMSGM_ERR_DEVICE_STATUS.
+ * reports.
  *
  * Threading: a handle must not be used from two host threads or two streams
  * at once.  Different handles are independent.
@@ -75,12 +77,13 @@ typedef struct {
                            (>= dmsgm_state_bytes(), 256-byte aligned); it must
                            outlive the handle.  NULL: the handle allocates.   */
     size_t state_bytes; /* size of state_mem                                  */
-    int tile_rows;      /* rows of pixels per CTA tile (multiple of 4*block,
-                           <= 256); 0 = built-in choice                       */
-    int use_pdl;        /* 1: launch with programmatic dependent launch so a
-                           frame's pixel load overlaps the previous frame's
-                           tail; 0: plain stream order.  Default (-1 or 0
-                           from zero-init): see dmsgm_create_ex.              */
+    int tile_rows;      /* rows of pixels per CTA tile: 4, 8 or 16 times the
+                           block size; 0 = built-in choice (32)              */
+    int use_pdl;        /* 1: programmatic dependent launch -- a frame's
+                           pixel load overlaps the previous kernel's tail, so
+                           the frame must not be written by the kernel that
+                           immediately precedes the call on the stream;
+                           0 (default): plain stream order                    */
 } dmsgm_opts;
 
 /* Read-only description of a handle. */
@@ -97,13 +100,15 @@ typedef struct {
 } dmsgm_info;
 
 /* Device bytes a handle needs for its state: a 256-byte control block plus
- * two buffers of Gx*Gy*(4*s + 2) bytes each (s = 4 for FP32, 2 for FP16),
- * every array 256-byte aligned.  Returns 0 for invalid sizes. */
+ * two buffers of three arrays (Gx*Gy*2*s, Gx*Gy*2*s and Gx*Gy*2 bytes; s = 4
+ * for FP32, 2 for FP16), every array 256-byte aligned.  Returns 0 for
+ * invalid sizes. */
 size_t dmsgm_state_bytes(int width, int height, int block, int precision);
 
 /* Bytes of the packed host image used by dmsgm_get_state/dmsgm_set_state:
- * mu_A, var_A, mu_C, var_C (Gx*Gy values each, FP32 or FP16 as stored),
- * then age_A, age_C (Gx*Gy bytes each), no padding. */
+ * the three state arrays back to back, no padding -- mu (Gx*Gy pairs
+ * (mu_A, mu_C)), var (Gx*Gy pairs (var_A, var_C)), both FP32 or FP16 as
+ * stored, then age (Gx*Gy byte pairs (age_A, age_C)). */
 size_t dmsgm_host_state_bytes(int width, int height, int block, int precision);
 
 /* Create a handle on the current CUDA device.  theta_s is the match
@@ -142,12 +147,30 @@ int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n,
 
 /* n handles, one frame each, in ONE persistent kernel launch over a
  * (stream, tile) work list (handles may differ in size, block and
- * precision; all on the current device; no handle twice).  frames_dev[i],
- * masks_dev[i] and H3x3s[9*i..] are handle i's arguments as in
- * dmsgm_process.  n <= DMSGM_MAX_BATCH. */
+ * precision; all on one device; no handle twice; width and height at most
+ * 65535).  frames_dev[i], masks_dev[i] and H3x3s[9*i..] are handle i's
+ * arguments as in dmsgm_process.  1 <= n <= DMSGM_MAX_BATCH (n == 0 is a
+ * no-op).  The per-stream descriptors travel in the launch's parameters:
+ * the call allocates nothing and copies nothing to the device, and a stream
+ * capture records one kernel node per call. */
 #define DMSGM_MAX_BATCH 256
 int dmsgm_process_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
                         const double* H3x3s, uint32_t* const* masks_dev, void* cuda_stream);
+
+/* Launch shape of the batched kernel; zero-initialised = built-in choice.
+ * A work item is a 256 x (8*block) pixel tile of one stream. */
+typedef struct {
+    int reserved;    /* must be 0                                             */
+    int ctas;        /* persistent CTAs; 0 = every CTA that fits on the GPU   */
+    int use_pdl;     /* 1: programmatic dependent launch (the first tile's
+                        pixels load while the previous kernel drains; frames
+                        must not be written by the immediately preceding
+                        kernel on the stream); 0: plain stream order          */
+} dmsgm_batch_opts;
+
+int dmsgm_process_batch_ex(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
+                           const double* H3x3s, uint32_t* const* masks_dev,
+                           const dmsgm_batch_opts* opts, void* cuda_stream);
 
 /* Copy the current state to / from a packed host image (layout: see
  * dmsgm_host_state_bytes).  Both synchronise the device.  set_state marks

@@ -29,6 +29,7 @@ DMSGM_MAX_BATCH = 256
 # every symbol include/dmsgm.h declares
 EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm_create_ex",
            "dmsgm_destroy", "dmsgm_process", "dmsgm_process_host", "dmsgm_process_batch",
+           "dmsgm_process_batch_ex",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
            "dmsgm_status", "dmsgm_last_error", "dmsgm_version")
 
@@ -37,6 +38,10 @@ class dmsgm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("state_mem", ctypes.c_void_p),
                 ("state_bytes", ctypes.c_size_t), ("tile_rows", ctypes.c_int),
                 ("use_pdl", ctypes.c_int)]
+
+
+class dmsgm_batch_opts(ctypes.Structure):
+    _fields_ = [("reserved", ctypes.c_int), ("ctas", ctypes.c_int), ("use_pdl", ctypes.c_int)]
 
 
 class dmsgm_info(ctypes.Structure):
@@ -80,6 +85,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_process": (I, [P, P, P, P, P]),
             "dmsgm_process_host": (I, [P, P, I, P, P, P]),
             "dmsgm_process_batch": (I, [I, P, P, P, P, P]),
+            "dmsgm_process_batch_ex": (I, [I, P, P, P, P, P, P]),
             "dmsgm_get_state": (I, [P, P, S]),
             "dmsgm_set_state": (I, [P, P, S]),
             "dmsgm_reset": (I, [P]),
@@ -145,14 +151,22 @@ def dmsgm_process_host(h, frames_ptr: int, n: int, Hs, masks_ptr: int, stream: i
     _check(load_library().dmsgm_process_host(h, frames_ptr, n, Hm.ctypes.data, masks_ptr, stream))
 
 
-def dmsgm_process_batch(handles, frame_ptrs, Hs, mask_ptrs, stream: int = 0):
+def dmsgm_process_batch(handles, frame_ptrs, Hs, mask_ptrs, stream: int = 0,
+                        opts: dmsgm_batch_opts | None = None):
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     fr = (ctypes.c_void_p * n)(*frame_ptrs)
     mk = (ctypes.c_void_p * n)(*mask_ptrs)
     Hm = _h9(Hs)
     assert Hm.size == 9 * n
-    _check(load_library().dmsgm_process_batch(n, hs, fr, Hm.ctypes.data, mk, stream))
+    lib = load_library()
+    if opts is None:
+        _check(lib.dmsgm_process_batch(n, hs, fr, Hm.ctypes.data, mk, stream))
+    else:
+        _check(lib.dmsgm_process_batch_ex(n, hs, fr, Hm.ctypes.data, mk, ctypes.byref(opts), stream))
+
+
+dmsgm_process_batch_ex = dmsgm_process_batch
 
 
 def dmsgm_get_state(h, buf: np.ndarray):

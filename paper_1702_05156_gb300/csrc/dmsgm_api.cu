@@ -31,29 +31,34 @@ void clear_error() { g_err[0] = 0; }
 // ------------------------------------------------------------------ kernel
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // 2 s: only a broken copy gets here
 
-template <int B, typename T, int RPT>
-__global__ void __launch_bounds__(kThreads)
+// 8x8 blocks: 32 registers (full occupancy) measured faster despite a small
+// spill; 4x4 blocks keep the compiler's choice.
+template <int B, int NW>
+constexpr int step_min_blocks() { return B == 8 ? 256 / NW : 1; }
+
+template <int B, typename T, int NW, int RPT>
+__global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
     dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, int* status) {
-    constexpr int TILE_H = 4 * B * RPT;
+    constexpr int STRIPS = NW * RPT;          // strip rows per tile
+    constexpr int TILE_H = STRIPS * B;
     __shared__ __align__(128) uint8_t tile[TILE_H * kTileW];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ Origin orig[2 * STRIPS];
     const int tx0 = blockIdx.x * kTileW;
     const int ty0 = blockIdx.y * TILE_H;
     if (threadIdx.x == 0) {
-        prefetch_tensormap(&tmap);
         mbar_init(&bar, 1);
         fence_mbar_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(&bar, TILE_H * kTileW);
         tma_load_2d(tile, &tmap, tx0, ty0, &bar);
     }
+    fill_origins<B>(a, tx0, ty0, STRIPS, orig);
+    __syncthreads();
     // The pixels do not depend on the previous frame's kernel; the state does.
     pdl_wait();
     pdl_launch_dependents();
-    Comp comp[RPT];
-    compensate_tile<B, T, RPT>(a, tx0, ty0, comp);
+    Comp comp[RPT][kLanePx / B];
+    compensate_tile<B, T, NW, RPT>(a, tx0, ty0, orig, comp);
     const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
     if (__syncthreads_or(!ok)) {
         // report, give the copy one more bounded chance to land, and leave
@@ -61,16 +66,16 @@ __global__ void __launch_bounds__(kThreads)
         mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
         return;
     }
-    finish_tile<B, T, RPT>(a, tile, tx0, ty0, comp);
+    finish_tile<B, T, NW, RPT>(a, tile, tx0, ty0, comp);
 }
 
-template <int B, typename T, int RPT>
+template <int B, typename T, int NW, int RPT>
 static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, int* status,
                                  cudaStream_t s, bool pdl) {
-    constexpr int TILE_H = 4 * B * RPT;
+    constexpr int TILE_H = NW * RPT * B;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(NW * 32, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -78,52 +83,41 @@ static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, i
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, dmsgm_step_kernel<B, T, RPT>, tmap, a, status);
+    return cudaLaunchKernelEx(&cfg, dmsgm_step_kernel<B, T, NW, RPT>, tmap, a, status);
 }
 
-static cudaError_t launch_step(int B, int prec, int rpt, const CUtensorMap& tmap,
+// tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1), (8, 2)}
+static cudaError_t launch_step(int B, int prec, int tile_rows, const CUtensorMap& tmap,
                                const StreamArgs& a, int* status, cudaStream_t s, bool pdl) {
-#define DMSGM_CASE(BB, TT, RR) \
-    if (B == BB && rpt == RR) return launch_step_t<BB, TT, RR>(tmap, a, status, s, pdl);
+    const int q = tile_rows / B;   // 4, 8 or 16
+#define DMSGM_CASE(BB, TT, QQ, NWW, RR) \
+    if (B == BB && q == QQ) return launch_step_t<BB, TT, NWW, RR>(tmap, a, status, s, pdl);
     if (prec == DMSGM_STATE_FP32) {
-        DMSGM_CASE(4, float, 1) DMSGM_CASE(4, float, 2) DMSGM_CASE(4, float, 4)
-        DMSGM_CASE(8, float, 1) DMSGM_CASE(8, float, 2) DMSGM_CASE(8, float, 4)
+        DMSGM_CASE(4, float, 4, 4, 1) DMSGM_CASE(4, float, 8, 8, 1) DMSGM_CASE(4, float, 16, 8, 2)
+        DMSGM_CASE(8, float, 4, 4, 1) DMSGM_CASE(8, float, 8, 8, 1) DMSGM_CASE(8, float, 16, 8, 2)
     } else {
-        DMSGM_CASE(4, __half, 1) DMSGM_CASE(4, __half, 2) DMSGM_CASE(4, __half, 4)
-        DMSGM_CASE(8, __half, 1) DMSGM_CASE(8, __half, 2) DMSGM_CASE(8, __half, 4)
+        DMSGM_CASE(4, __half, 4, 4, 1) DMSGM_CASE(4, __half, 8, 8, 1) DMSGM_CASE(4, __half, 16, 8, 2)
+        DMSGM_CASE(8, __half, 4, 4, 1) DMSGM_CASE(8, __half, 8, 8, 1) DMSGM_CASE(8, __half, 16, 8, 2)
     }
 #undef DMSGM_CASE
     return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ helpers
-static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
 static bool valid_dims(int W, int H, int B) {
     return W > 0 && H > 0 && (B == 4 || B == 8) && W % 16 == 0 && W % B == 0 && H % B == 0 &&
            W <= (1 << 20) && H <= (1 << 20);
 }
 
 static size_t buf_bytes(size_t N, int prec) {
-    const size_t s = prec == DMSGM_STATE_FP16 ? 2 : 4;
-    return 4 * align256(N * s) + 2 * align256(N);
+    return state_buf_bytes(N, prec == DMSGM_STATE_FP16 ? 2 : 4);
 }
 
 static void carve(dmsgm_ctx* h) {
     const size_t N = size_t(h->Gx) * h->Gy;
-    const size_t s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
-    char* p = static_cast<char*>(h->mem);
-    h->status_dev = reinterpret_cast<int*>(p);
-    p += 256;
-    for (int b = 0; b < 2; ++b) {
-        StateBuf& sb = h->buf[b];
-        sb.muA = p; p += align256(N * s);
-        sb.varA = p; p += align256(N * s);
-        sb.muC = p; p += align256(N * s);
-        sb.varC = p; p += align256(N * s);
-        sb.ageA = reinterpret_cast<uint8_t*>(p); p += align256(N);
-        sb.ageC = reinterpret_cast<uint8_t*>(p); p += align256(N);
-    }
+    const int s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
+    h->status_dev = reinterpret_cast<int*>(h->mem);
+    for (int b = 0; b < 2; ++b) h->buf[b] = state_buf(static_cast<char*>(h->mem), N, s, b);
 }
 
 struct DeviceGuard {
@@ -182,22 +176,46 @@ static int frame_map(dmsgm_ctx* h, const void* frame, const CUtensorMap** out) {
     return DMSGM_OK;
 }
 
-bool make_coef(const double m[9], Coef* c) {
+bool make_coef(const double m[9], int B, Coef* c, int* affine) {
     for (int i = 0; i < 9; ++i)
         if (!std::isfinite(m[i])) return false;
-    // displacement-form coefficients in FP64, each split into hi + lo floats
-    const double v[9] = {m[0] - m[8], m[1], m[2], m[3], m[4] - m[8], m[5], m[6], m[7], m[8]};
-    float* hi = &c->ax0;
-    float* lo = &c->ax0l;
+    double v[9];
+    *affine = 0;
+    if (m[6] == 0.0 && m[7] == 0.0 && m[8] > 0.0) {
+        // affine: block-unit displacement ex = ax*bx + bx_*by + cx (and ey)
+        const double ax = m[0] / m[8] - 1.0, bxx = m[1] / m[8];
+        const double ay = m[3] / m[8], byy = m[4] / m[8] - 1.0;
+        const double cx = 0.5 * ax + 0.5 * bxx + m[2] / (m[8] * B);
+        const double cy = 0.5 * ay + 0.5 * byy + m[5] / (m[8] * B);
+        const double lim = 1.0 / 31.0;   // per-lane step stays exact to ~1e-7
+        const double far = 1.0e6;
+        if (std::fabs(ax) <= lim && std::fabs(ay) <= lim && std::fabs(bxx) < far &&
+            std::fabs(byy) < far && std::fabs(cx) < far && std::fabs(cy) < far) {
+            const double a[6] = {ax, bxx, cx, ay, byy, cy};
+            for (int i = 0; i < 6; ++i) {
+                const float hi = float(a[i]);
+                c->c[2 * i] = hi;
+                c->c[2 * i + 1] = float(a[i] - double(hi));
+            }
+            for (int i = 12; i < 18; ++i) c->c[i] = 0.f;
+            *affine = 1;
+            return true;
+        }
+    }
+    // general: pixel-space displacement form
+    const double g[9] = {m[0] - m[8], m[1], m[2], m[3], m[4] - m[8], m[5], m[6], m[7], m[8]};
+    for (int i = 0; i < 9; ++i) v[i] = g[i];
     for (int i = 0; i < 9; ++i) {
-        hi[i] = float(v[i]);
-        lo[i] = float(v[i] - double(hi[i]));
-        if (!std::isfinite(hi[i]) || !std::isfinite(lo[i])) return false;
+        const float hi = float(v[i]);
+        const float lo = float(v[i] - double(hi));
+        if (!std::isfinite(hi) || !std::isfinite(lo)) return false;
+        c->c[2 * i] = hi;
+        c->c[2 * i + 1] = lo;
     }
     return true;
 }
 
-void fill_args(const dmsgm_ctx* h, const Coef& c, uint32_t* mask_dev, StreamArgs* a) {
+void fill_args(const dmsgm_ctx* h, const Coef& c, int affine, uint32_t* mask_dev, StreamArgs* a) {
     a->prev = h->buf[h->parity];
     a->next = h->buf[h->parity ^ 1];
     a->mask = mask_dev;
@@ -207,6 +225,7 @@ void fill_args(const dmsgm_ctx* h, const Coef& c, uint32_t* mask_dev, StreamArgs
     a->Gy = h->Gy;
     a->mask_words = (h->W + 31) / 32;
     a->first = h->initialized ? 0 : 1;
+    a->affine = affine;
     a->age_max = h->age_max;
     a->theta_s = h->theta_s;
     a->theta_d = h->theta_d;
@@ -222,14 +241,16 @@ void advance(dmsgm_ctx* h) {
 static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x3,
                        uint32_t* mask_dev, cudaStream_t s) {
     Coef c;
-    if (!make_coef(H3x3, &c)) return fail(DMSGM_ERR_INVALID_ARG, "homography is not finite in FP32");
+    int affine = 0;
+    if (!make_coef(H3x3, h->B, &c, &affine))
+        return fail(DMSGM_ERR_INVALID_ARG, "homography is not finite in FP32");
     const CUtensorMap* tm = nullptr;
     int rc = frame_map(h, frame_dev, &tm);
     if (rc) return rc;
     StreamArgs a;
-    fill_args(h, c, mask_dev, &a);
-    cudaError_t e = launch_step(h->B, h->prec, h->tile_rows / (4 * h->B), *tm, a, h->status_dev,
-                                s, h->use_pdl != 0);
+    fill_args(h, c, affine, mask_dev, &a);
+    cudaError_t e = launch_step(h->B, h->prec, h->tile_rows, *tm, a, h->status_dev, s,
+                                h->use_pdl != 0);
     if (e != cudaSuccess) return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     advance(h);
     return DMSGM_OK;
@@ -321,10 +342,9 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     if (o) opts = *o;
     if (opts.precision != DMSGM_STATE_FP32 && opts.precision != DMSGM_STATE_FP16)
         return fail(DMSGM_ERR_INVALID_ARG, "unknown precision %d", opts.precision);
-    int tile_rows = opts.tile_rows ? opts.tile_rows : 32;
-    const int rpt = tile_rows / (4 * B);
-    if (tile_rows % (4 * B) != 0 || !(rpt == 1 || rpt == 2 || rpt == 4))
-        return fail(DMSGM_ERR_INVALID_ARG, "tile_rows %d must be 4*block*{1,2,4}", tile_rows);
+    const int tile_rows = opts.tile_rows ? opts.tile_rows : 32;
+    if (!(tile_rows == 4 * B || tile_rows == 8 * B || tile_rows == 16 * B))
+        return fail(DMSGM_ERR_INVALID_ARG, "tile_rows %d must be 4, 8 or 16 times the block", tile_rows);
     const size_t need = dmsgm_state_bytes(W, H, B, opts.precision);
     if (opts.state_mem) {
         if (opts.state_bytes < need)
@@ -444,6 +464,12 @@ int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n, const doubl
 
 int dmsgm_process_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
                         const double* Hs, uint32_t* const* masks_dev, void* stream) {
+    return dmsgm_process_batch_ex(n, hs, frames_dev, Hs, masks_dev, nullptr, stream);
+}
+
+int dmsgm_process_batch_ex(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
+                           const double* Hs, uint32_t* const* masks_dev,
+                           const dmsgm_batch_opts* opts, void* stream) {
     clear_error();
     if (n < 0 || n > DMSGM_MAX_BATCH) return fail(DMSGM_ERR_INVALID_ARG, "n=%d out of range", n);
     if (n == 0) return DMSGM_OK;
@@ -458,12 +484,15 @@ int dmsgm_process_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_d
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return fail(DMSGM_ERR_INVALID_ARG, "handle %d appears twice", i);
         Coef c;
-        if (!make_coef(Hs + 9 * size_t(i), &c))
+        int affine = 0;
+        if (!make_coef(Hs + 9 * size_t(i), hs[i]->B, &c, &affine))
             return fail(DMSGM_ERR_INVALID_ARG, "homography %d is not finite in FP32", i);
     }
     DeviceGuard g(hs[0]->device);
     if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", hs[0]->device);
-    return launch_batch(n, hs, frames_dev, Hs, masks_dev, static_cast<cudaStream_t>(stream));
+    dmsgm_batch_opts o = {};
+    if (opts) o = *opts;
+    return launch_batch(n, hs, frames_dev, Hs, masks_dev, o, static_cast<cudaStream_t>(stream));
 }
 
 int dmsgm_get_state(dmsgm_t h, void* host_buf, size_t bytes) {
@@ -476,9 +505,9 @@ int dmsgm_get_state(dmsgm_t h, void* host_buf, size_t bytes) {
     const size_t N = size_t(h->Gx) * h->Gy, s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
     const StateBuf& sb = h->buf[h->parity];
     char* p = static_cast<char*>(host_buf);
-    const void* src[6] = {sb.muA, sb.varA, sb.muC, sb.varC, sb.ageA, sb.ageC};
-    const size_t len[6] = {N * s, N * s, N * s, N * s, N, N};
-    for (int i = 0; i < 6; ++i) {
+    const void* src[3] = {sb.mu, sb.var, sb.age};
+    const size_t len[3] = {2 * N * s, 2 * N * s, 2 * N};
+    for (int i = 0; i < 3; ++i) {
         DMSGM_CUDA_TRY(cudaMemcpy(p, src[i], len[i], cudaMemcpyDeviceToHost));
         p += len[i];
     }
@@ -495,9 +524,9 @@ int dmsgm_set_state(dmsgm_t h, const void* host_buf, size_t bytes) {
     const size_t N = size_t(h->Gx) * h->Gy, s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
     const StateBuf& sb = h->buf[h->parity];
     const char* p = static_cast<const char*>(host_buf);
-    void* dst[6] = {sb.muA, sb.varA, sb.muC, sb.varC, sb.ageA, sb.ageC};
-    const size_t len[6] = {N * s, N * s, N * s, N * s, N, N};
-    for (int i = 0; i < 6; ++i) {
+    void* dst[3] = {sb.mu, sb.var, sb.age};
+    const size_t len[3] = {2 * N * s, 2 * N * s, 2 * N};
+    for (int i = 0; i < 3; ++i) {
         DMSGM_CUDA_TRY(cudaMemcpy(dst[i], p, len[i], cudaMemcpyHostToDevice));
         p += len[i];
     }

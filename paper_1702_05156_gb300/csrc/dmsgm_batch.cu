@@ -1,15 +1,235 @@
-// dmsgm_batch.cu -- many streams per launch.
+// dmsgm_batch.cu -- many streams, one persistent launch per frame step.
+//
+// Every stream of the batch contributes its frame's 256 x TILE_H tiles to one
+// (stream, tile) work list.  A persistent grid of CTAs walks the list with a
+// static stride; each CTA double-buffers its tiles in shared memory: while
+// it runs the fused DMSGM step (Sec. 2.2-2.4) on tile k, the TMA engine
+// brings tile k+1 in by 1-D bulk copies (one per pixel row, so no tensor map
+// is needed for the streams' ever-changing frame pointers).  Streams may
+// differ in size, block size (4 / 8) and state precision (FP32 / FP16).
+//
+// The per-stream descriptors travel in the kernel's parameter space (up to
+// 256 x 120 bytes), so a launch needs no device scratch and no host->device
+// copy, and a stream capture bakes each step's descriptors into its graph
+// node.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "dmsgm_internal.h"
 
 namespace dmsgm {
 
-int launch_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev, const double* Hs,
-                 uint32_t* const* masks_dev, cudaStream_t stream) {
-    for (int i = 0; i < n; ++i) {
-        int rc = dmsgm_process(hs[i], frames_dev[i], Hs + 9 * size_t(i), masks_dev[i], stream);
-        if (rc) return rc;
+struct BatchItem {
+    const uint8_t* frame;
+    uint32_t* mask;
+    char* mem;           // the handle's device memory (control block + buffers)
+    Coef coef;
+    uint16_t W, H;
+    uint8_t B, prec, first, parity, affine, age_max;
+    float theta_s, theta_d;
+    int tile_begin;      // first work-list index of this stream
+};
+static_assert(sizeof(BatchItem) == 120, "BatchItem layout");
+
+template <int CAP>
+struct BatchParams {
+    int n;
+    int total;           // work-list length
+    BatchItem item[CAP];
+};
+static_assert(sizeof(BatchParams<DMSGM_MAX_BATCH>) <= 32764, "kernel parameter limit");
+
+// Stage setup (one warp): locate the item's stream, describe it in shared
+// memory, and start the bulk copies of its pixel rows.
+// Work items are tiles of kTileW x (8 * B) pixels: 8 warps, one strip row
+// each.  The stage buffers are sized for B = 8.
+constexpr int kBatchWarps = 8;
+constexpr int kStageRows = kBatchWarps * 8;
+
+template <int CAP>
+__device__ __forceinline__ void stage_item(const BatchParams<CAP>& p, int t, StreamArgs& sa,
+                                           int* meta, Origin* orig, uint8_t* tile, uint64_t* bar) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = p.n - 1;           // last stream with tile_begin <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.item[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
     }
+    const BatchItem& it = p.item[lo];
+    const int W = it.W, H = it.H, B = it.B;
+    const int th = kBatchWarps * B;     // tile height of this stream
+    const int tiles_x = (W + kTileW - 1) / kTileW;
+    const int lt = t - it.tile_begin;
+    const int tx0 = (lt % tiles_x) * kTileW;
+    const int ty0 = (lt / tiles_x) * th;
+    const int rows = min(th, H - ty0);
+    const uint32_t wbytes = static_cast<uint32_t>(min(kTileW, W - tx0));
+    if (lane == 0) {
+        const size_t N = size_t(W / B) * (H / B);
+        const int s = it.prec == DMSGM_STATE_FP16 ? 2 : 4;
+        sa.prev = state_buf(it.mem, N, s, it.parity);
+        sa.next = state_buf(it.mem, N, s, it.parity ^ 1);
+        sa.mask = it.mask;
+        sa.W = W;
+        sa.H = H;
+        sa.Gx = W / B;
+        sa.Gy = H / B;
+        sa.mask_words = (W + 31) / 32;
+        sa.first = it.first;
+        sa.affine = it.affine;
+        sa.age_max = it.age_max;
+        sa.theta_s = it.theta_s;
+        sa.theta_d = it.theta_d;
+        sa.coef = it.coef;
+        meta[0] = tx0;
+        meta[1] = ty0;
+        meta[2] = (B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
+        meta[3] = lo;
+        mbar_arrive_expect_tx(bar, wbytes * rows);
+    }
+    __syncwarp();
+    for (int r = lane; r < rows; r += 32)
+        bulk_load_1d(tile + r * kTileW, it.frame + size_t(ty0 + r) * W + tx0, wbytes, bar);
+    if (it.affine && !it.first && lane < 2 * kBatchWarps)   // the tile's affine origins
+        orig[lane] = affine_origin(it.coef, (tx0 + 128 * (lane & 1)) / B, ty0 / B + (lane >> 1));
+}
+
+template <int B, typename T>
+__device__ __forceinline__ bool run_item(const StreamArgs& sa, const int* meta, const Origin* orig,
+                                         const uint8_t* tile, uint64_t* bar, uint32_t parity) {
+    Comp comp[1][kLanePx / B];
+    compensate_tile<B, T, kBatchWarps, 1>(sa, meta[0], meta[1], orig, comp);
+    const bool ok = mbar_wait_bounded(bar, parity, 2000000000ull);
+    if (__syncthreads_or(!ok)) return false;
+    finish_tile<B, T, kBatchWarps, 1>(sa, tile, meta[0], meta[1], comp);
+    return true;
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(kBatchWarps * 32, 4)
+    dmsgm_batch_kernel(const __grid_constant__ BatchParams<CAP> p) {
+    __shared__ __align__(128) uint8_t tile[2][kStageRows * kTileW];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ StreamArgs sa[2];
+    __shared__ int meta[2][4];
+    __shared__ Origin orig[2][2 * kBatchWarps];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int t = blockIdx.x;
+    // the first tile's pixels do not depend on the previous step
+    if (t < p.total && threadIdx.x < 32) stage_item<CAP>(p, t, sa[0], meta[0], orig[0], tile[0], &bar[0]);
+    pdl_wait();
+    pdl_launch_dependents();
+    for (int k = 0; t < p.total; t += gridDim.x, ++k) {
+        const int st = k & 1;
+        __syncthreads();   // stage st described; stage st^1 free
+        const int tn = t + gridDim.x;
+        if (tn < p.total && threadIdx.x < 32)
+            stage_item<CAP>(p, tn, sa[st ^ 1], meta[st ^ 1], orig[st ^ 1], tile[st ^ 1], &bar[st ^ 1]);
+        const uint32_t par = (k >> 1) & 1;
+        bool ok;
+        switch (meta[st][2]) {
+            case 0: ok = run_item<4, float>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
+            case 1: ok = run_item<4, __half>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
+            case 2: ok = run_item<8, float>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
+            default: ok = run_item<8, __half>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
+        }
+        if (!ok) {
+            // report on the stream's status word; let in-flight copies land
+            if (threadIdx.x == 0)
+                atomicOr(reinterpret_cast<int*>(p.item[meta[st][3]].mem), kStatusWaitTimeout);
+            if (tn < p.total) mbar_wait_bounded(&bar[st ^ 1], ((k + 1) >> 1) & 1, 2000000000ull);
+            return;
+        }
+    }
+}
+
+template <int CAP>
+static cudaError_t launch_t(const BatchParams<CAP>& p, int ctas, cudaStream_t s, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas, 1, 1);
+    cfg.blockDim = dim3(kBatchWarps * 32, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, dmsgm_batch_kernel<CAP>, p);
+}
+
+template <int CAP>
+static int resident_ctas(int device) {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    std::lock_guard<std::mutex> g(mu);
+    if (device < 0 || device >= 64) return 1;
+    if (!cache[device]) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_batch_kernel<CAP>,
+                                                          kBatchWarps * 32, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+            return 1;
+        cache[device] = std::max(1, per_sm) * std::max(1, sms);
+    }
+    return cache[device];
+}
+
+template <int CAP>
+static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const double* Hs,
+                   uint32_t* const* masks, const dmsgm_batch_opts& o, cudaStream_t s) {
+    if (o.reserved != 0) return fail(DMSGM_ERR_INVALID_ARG, "dmsgm_batch_opts.reserved must be 0");
+    static thread_local BatchParams<CAP> p;   // ~CAP*120 bytes: keep it off the stack
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+        const dmsgm_ctx* h = hs[i];
+        if (h->W > 65535 || h->H > 65535)
+            return fail(DMSGM_ERR_INVALID_ARG, "batched streams must be at most 65535 px wide/high");
+        BatchItem& it = p.item[i];
+        it.frame = frames[i];
+        it.mask = masks[i];
+        it.mem = static_cast<char*>(h->mem);
+        int affine = 0;
+        if (!make_coef(Hs + 9 * size_t(i), h->B, &it.coef, &affine))
+            return fail(DMSGM_ERR_INVALID_ARG, "homography %d is not finite in FP32", i);
+        it.affine = uint8_t(affine);
+        it.W = uint16_t(h->W);
+        it.H = uint16_t(h->H);
+        it.B = uint8_t(h->B);
+        it.prec = uint8_t(h->prec);
+        it.first = h->initialized ? 0 : 1;
+        it.parity = uint8_t(h->parity);
+        it.theta_s = h->theta_s;
+        it.theta_d = h->theta_d;
+        it.age_max = uint8_t(h->age_max);
+        it.tile_begin = total;
+        const int th = kBatchWarps * h->B;
+        total += ((h->W + kTileW - 1) / kTileW) * ((h->H + th - 1) / th);
+    }
+    p.n = n;
+    p.total = total;
+    const int dev = hs[0]->device;
+    const int full = resident_ctas<CAP>(dev);
+    int ctas = o.ctas > 0 ? std::min(o.ctas, full) : full;
+    ctas = std::max(1, std::min(ctas, total));
+    cudaError_t e = launch_t<CAP>(p, ctas, s, o.use_pdl > 0);
+    if (e != cudaSuccess)
+        return fail(DMSGM_ERR_CUDA, "batch kernel launch failed: %s", cudaGetErrorString(e));
+    for (int i = 0; i < n; ++i) advance(hs[i]);
     return DMSGM_OK;
+}
+
+int launch_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev, const double* Hs,
+                 uint32_t* const* masks_dev, const dmsgm_batch_opts& o, cudaStream_t stream) {
+    if (n <= 16) return run_cap<16>(n, hs, frames_dev, Hs, masks_dev, o, stream);
+    if (n <= 64) return run_cap<64>(n, hs, frames_dev, Hs, masks_dev, o, stream);
+    return run_cap<DMSGM_MAX_BATCH>(n, hs, frames_dev, Hs, masks_dev, o, stream);
 }
 
 }  // namespace dmsgm

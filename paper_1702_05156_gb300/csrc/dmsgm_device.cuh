@@ -1,17 +1,17 @@
 // dmsgm_device.cuh -- device-side building blocks of the fused DMSGM step.
 //
-// One CTA owns a tile of kTileW x TILE_H pixels (TILE_H = 4 * B * RPT).  Its
-// pixels arrive in shared memory by TMA; every thread owns a "strip" of 4
-// pixel columns x B rows, i.e. one 4x4 block (B = 4) or half of an 8x8 block
-// (B = 8, two adjacent lanes per block).  Per strip the thread
-//   (a) compensates the block's previous models (Sec. 2.4): projects the
-//       block centre through the homography, mixes the <= 4 overlapped
-//       previous blocks by overlap area;
+// A CTA of NW warps owns a tile of kTileW x (NW * B * RPT) pixels whose
+// pixels arrive in shared memory by TMA.  Warp w takes strip rows w, w + NW,
+// ...; lane l owns the 8 pixel columns [8l, 8l + 8) of its strip row, that is
+// two 4x4 blocks (B = 4) or one 8x8 block (B = 8).  Per block the lane
+//   (a) compensates the previous models for camera motion (Sec. 2.4):
+//       projects the block centre through the homography and mixes the <= 4
+//       overlapped previous blocks by overlap area;
 //   (b) reduces sum / min / max of the block's pixels (Sec. 2.2, M_i and
 //       V_i) and runs match -> update -> reset -> swap (Sec. 2.2 and 2.3);
-//   (c) tests each pixel against the final apparent model and assembles
-//       the bit-packed mask with warp shuffles (appendix code, threshold
-//       theta_d * var_A).
+//   (c) tests each pixel against the final apparent model (appendix code,
+//       threshold theta_d * var_A) and writes one mask byte per pixel row.
+
 #pragma once
 
 #include <cuda.h>
@@ -25,38 +25,58 @@ constexpr float kVarInit = 255.0f;   // Sec. 2.3: reset variance
 constexpr float kVarFloor = 0.1f;    // appendix code: max(var, .1) in the match tests
 constexpr float kMinWeight = 1e-3f;  // in-grid weight below this: no source
 constexpr int kTileW = 256;          // pixels per tile row (one TMA box row)
-constexpr int kThreads = 256;        // threads per CTA
-constexpr int kStripCols = kTileW / 4;                     // 64 strips across a tile
-constexpr int kStripRowsPerPass = kThreads / kStripCols;   // 4 strip rows per pass
+constexpr int kLanePx = 8;           // pixel columns a lane owns (one mask byte per row)
 
 // device status word bits
 constexpr int kStatusWaitTimeout = 1;
 
-// Displacement form of the homography.  For a block centre (x, y):
-//   Z  = hz0*x + hz1*y + hz2
-//   dx = (ax0*x + ax1*y + ax2 - (hz0*x + hz1*y)*x) / Z      (= X/Z - x)
-//   dy = (ay0*x + ay1*y + ay2 - (hz0*x + hz1*y)*y) / Z      (= Y/Z - y)
-// with ax0 = h00 - h22, ax1 = h01, ax2 = h02, ay0 = h10, ay1 = h11 - h22,
-// ay2 = h12, (hz0, hz1, hz2) = (h20, h21, h22).  Each coefficient arrives as
-// an unevaluated sum of two floats (hi + lo) rounded once from FP64 on the
-// host, and the displacement is evaluated in double-float arithmetic (error-
-// free products and sums, Dekker/Knuth), so the fractional block position
-// that sets the mixing weights is exact to ~1e-7 even for 150 px shifts at
-// 4K -- all in FP32 instructions, no FP64 on the GPU.
+// The frame's homography, reduced on the host from FP64 to pairs of floats
+// (hi + lo, "double-float") in one of two forms:
+//  * affine (h20 = h21 = 0, h22 > 0, displacements bounded): the block-unit
+//    displacement of block (bx, by) is linear,
+//        ex = c0*bx + c2*by + c4,   ey = c6*bx + c8*by + c10
+//    (pair (c[2k], c[2k+1]) is one coefficient); ex, ey is where the block's
+//    back-projected square starts relative to (bx, by), in blocks;
+//  * general: the pixel-space displacement form.  For a centre (x, y):
+//        Z  = c12*x + c14*y + c16
+//        dx = (c0*x + c2*y + c4 - (c12*x + c14*y)*x) / Z       (= X/Z - x)
+//        dy = (c6*x + c8*y + c10 - (c12*x + c14*y)*y) / Z      (= Y/Z - y)
+//    with c0 = h00 - h22, c2 = h01, c4 = h02, c6 = h10, c8 = h11 - h22,
+//    c10 = h12, (c12, c14, c16) = (h20, h21, h22).
+// Evaluating displacements (not absolute positions) in double-float keeps the
+// fractional block position that sets the mixing weights exact to ~1e-7 even
+// for 150 px shifts at 4K, with FP32 instructions only.
 struct Coef {
-    float ax0, ax1, ax2, ay0, ay1, ay2, hz0, hz1, hz2;            // hi parts
-    float ax0l, ax1l, ax2l, ay0l, ay1l, ay2l, hz0l, hz1l, hz2l;   // lo parts
+    float c[18];
 };
 
-// One ping-pong buffer of model state (structure of arrays over the blocks).
+// One ping-pong buffer of model state, a structure of arrays over the
+// blocks; in each array the apparent (A) and candidate (C) values of a block
+// sit side by side, so one 8-byte (FP32) or 4-byte (FP16) load fetches both:
+//   mu[k]  = (mu_A, mu_C)     float2 or __half2
+//   var[k] = (var_A, var_C)   float2 or __half2
+//   age[k] = age_A | age_C << 8
 struct StateBuf {
-    void* muA;
-    void* varA;
-    void* muC;
-    void* varC;
-    uint8_t* ageA;
-    uint8_t* ageC;
+    void* mu;
+    void* var;
+    uint16_t* age;
 };
+
+// Device-memory layout of a handle: a 256-byte control block (status word
+// first), then the two buffers, every array 256-byte aligned.  s is the size
+// of one stored value (4: FP32, 2: FP16).
+__host__ __device__ __forceinline__ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+__host__ __device__ __forceinline__ size_t state_buf_bytes(size_t N, int s) {
+    return 2 * align256(N * 2 * s) + align256(N * 2);
+}
+__host__ __device__ __forceinline__ StateBuf state_buf(char* mem, size_t N, int s, int which) {
+    char* p = mem + 256 + size_t(which) * state_buf_bytes(N, s);
+    StateBuf b;
+    b.mu = p; p += align256(N * 2 * s);
+    b.var = p; p += align256(N * 2 * s);
+    b.age = reinterpret_cast<uint16_t*>(p);
+    return b;
+}
 
 // Everything one stream's frame step needs besides its pixels.
 struct StreamArgs {
@@ -65,6 +85,7 @@ struct StreamArgs {
     int W, H, Gx, Gy;
     int mask_words;     // uint32 words per mask row = ceil(W / 32)
     int first;          // 1: no previous state (first frame after create/reset)
+    int affine;         // 1: coef holds the affine block-unit form
     int age_max;
     float theta_s, theta_d;
     Coef coef;
@@ -155,19 +176,31 @@ __device__ __forceinline__ void pdl_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+
 // ------------------------------------------------------------------ state I/O
-__device__ __forceinline__ float ld_state(const void* base, int i, float*) {
-    return __ldg(static_cast<const float*>(base) + i);
+// Both models of a block, as (A, C) float pairs.
+__device__ __forceinline__ float2 ld2(const void* base, int k, float*) {
+    return __ldg(static_cast<const float2*>(base) + k);
 }
-__device__ __forceinline__ float ld_state(const void* base, int i, __half*) {
-    return __half2float(__ldg(static_cast<const __half*>(base) + i));
+__device__ __forceinline__ float2 ld2(const void* base, int k, __half*) {
+    return __half22float2(__ldg(static_cast<const __half2*>(base) + k));
 }
-__device__ __forceinline__ void st_state(void* base, int i, float v, float*) {
-    static_cast<float*>(base)[i] = v;
+__device__ __forceinline__ void st2(void* base, int k, float2 v, float*) {
+    static_cast<float2*>(base)[k] = v;
 }
-__device__ __forceinline__ void st_state(void* base, int i, float v, __half*) {
-    static_cast<__half*>(base)[i] = __float2half_rn(v);
+__device__ __forceinline__ void st2(void* base, int k, float2 v, __half*) {
+    static_cast<__half2*>(base)[k] = __float22half2_rn(v);
 }
+
+// (age_A, age_C) bytes -> exact floats, no conversion instruction: each byte
+// becomes the low mantissa byte of 2^23 + byte, then 2^23 is subtracted.
+__device__ __forceinline__ float2 age2f(uint32_t a) {
+    const float2 m = make_float2(__int_as_float(__byte_perm(a, 0x4B000000u, 0x7540)),
+                                 __int_as_float(__byte_perm(a, 0x4B000000u, 0x7541)));
+    return __fadd2_rn(m, make_float2(-8388608.0f, -8388608.0f));
+}
+
+__device__ __forceinline__ float2 dup2(float w) { return make_float2(w, w); }
 
 struct Model {
     float mu, var;
@@ -179,6 +212,7 @@ struct Comp {
     Model A, C;
     bool src;
 };
+
 
 // ---------------------------------------------------- double-float helpers
 // A value is hi + lo with |lo| <= ulp(hi)/2.  Only additions, subtractions
@@ -218,14 +252,24 @@ __device__ __forceinline__ DF df_div(DF a, DF b) {
     return df_quick(q1, q2);
 }
 
-// Block-unit displacement (ex, ey) of the centre (x, y); false if Z <= 0.
-__device__ __forceinline__ bool project_df(const Coef& c, float x, float y, DF& ex, DF& ey,
-                                           float inv_b) {
-    const DF t = df_add(df_mul(c.hz0, c.hz0l, x), df_mul(c.hz1, c.hz1l, y));   // h20 x + h21 y
-    const DF Z = df_add(t, DF{c.hz2, c.hz2l});
+// floor and fraction of hi + lo: fl integer-valued, f in [0, 1]
+__device__ __forceinline__ void df_floor_frac(DF v, float& fl, float& f) {
+    fl = floorf(v.hi);
+    if (v.hi == fl && v.lo < 0.f) fl -= 1.f;
+    f = (v.hi - fl) + v.lo;
+    f = fminf(fmaxf(f, 0.f), 1.f);
+}
+
+// General form: block-unit displacement (ex, ey) of the centre (x, y); false
+// if Z <= 0.
+__device__ __forceinline__ bool project_general(const Coef& k, float x, float y, DF& ex, DF& ey,
+                                                float inv_b) {
+    const float* c = k.c;
+    const DF t = df_add(df_mul(c[12], c[13], x), df_mul(c[14], c[15], y));   // h20 x + h21 y
+    const DF Z = df_add(t, DF{c[16], c[17]});
     if (!(Z.hi > 0.f)) return false;
-    DF nx = df_add(df_add(df_mul(c.ax0, c.ax0l, x), df_mul(c.ax1, c.ax1l, y)), DF{c.ax2, c.ax2l});
-    DF ny = df_add(df_add(df_mul(c.ay0, c.ay0l, x), df_mul(c.ay1, c.ay1l, y)), DF{c.ay2, c.ay2l});
+    DF nx = df_add(df_add(df_mul(c[0], c[1], x), df_mul(c[2], c[3], y)), DF{c[4], c[5]});
+    DF ny = df_add(df_add(df_mul(c[6], c[7], x), df_mul(c[8], c[9], y)), DF{c[10], c[11]});
     nx = df_add(nx, df_neg(df_mulv(t, x)));
     ny = df_add(ny, df_neg(df_mulv(t, y)));
     ex = df_div(nx, Z);
@@ -235,75 +279,144 @@ __device__ __forceinline__ bool project_df(const Coef& c, float x, float y, DF& 
     return true;
 }
 
-// floor and fraction of hi + lo: fl integer-valued, f in [0, 1]
-__device__ __forceinline__ void df_floor_frac(DF v, float& fl, float& f) {
-    fl = floorf(v.hi);
-    if (v.hi == fl && v.lo < 0.f) fl -= 1.f;
-    f = (v.hi - fl) + v.lo;
-    f = fminf(fmaxf(f, 0.f), 1.f);
+
+// ------------------------------------------------------------------ (a)
+// Affine form: the displacement at the first block bx0 of a half-warp's
+// strip (by), split into integer parts and fractions.  One thread per
+// origin computes it in double-float and publishes it in shared memory; a
+// lane then steps from bx0 to its own block (at most 31 blocks away) with
+// one FMA, whose rounding stays below 1.2e-7 blocks because the host admits
+// the affine form only when |d ex / d bx| * 31 <= 2.
+struct Origin {
+    int nx, ny;
+    float fx, fy;
+};
+
+__device__ __forceinline__ Origin affine_origin(const Coef& k, int bx0, int by) {
+    const float* c = k.c;
+    const DF ux = df_add(df_add(df_mul(c[0], c[1], float(bx0)), df_mul(c[2], c[3], float(by))),
+                         DF{c[4], c[5]});
+    const DF uy = df_add(df_add(df_mul(c[6], c[7], float(bx0)), df_mul(c[8], c[9], float(by))),
+                         DF{c[10], c[11]});
+    float nx, ny;
+    Origin o;
+    df_floor_frac(ux, nx, o.fx);
+    df_floor_frac(uy, ny, o.fy);
+    o.nx = int(nx);
+    o.ny = int(ny);
+    return o;
 }
 
-// (a) motion compensation of block (bx, by): area-weighted mix of the
-// previous blocks that the back-projected BxB square overlaps (Sec. 2.4).
+// Origins of a tile with `strips` strip rows: entry (s << 1) | h belongs to
+// strip row s, half-warp h, whose first block is (tx0 + 128 h) / B.  Threads
+// 0 .. 2*strips-1 fill one entry each.
+template <int B>
+__device__ __forceinline__ void fill_origins(const StreamArgs& a, int tx0, int ty0, int strips,
+                                             Origin* orig) {
+    const int t = threadIdx.x;
+    if (a.affine && !a.first && t < 2 * strips)
+        orig[t] = affine_origin(a.coef, (tx0 + 128 * (t & 1)) / B, ty0 / B + (t >> 1));
+}
+
+// Motion compensation of block (bx, by): area-weighted mix of the previous
+// blocks that the back-projected BxB square overlaps (Sec. 2.4).  For the
+// affine form, o is the origin of the lane's half-warp, bx0 its first block.
 template <int B, typename T>
-__device__ __forceinline__ Comp compensate(const StreamArgs& a, int bx, int by) {
+__device__ __forceinline__ Comp compensate(const StreamArgs& a, int bx, int by, int bx0,
+                                           const Origin& o) {
     Comp r;
     r.src = false;
     r.A = Model{0.f, 0.f, 0};
     r.C = r.A;
     if (a.first) return r;
-    const float x = (bx + 0.5f) * B, y = (by + 0.5f) * B;
-    DF ex, ey;
-    if (!project_df(a.coef, x, y, ex, ey, 1.0f / B)) return r;
-    // the back-projected square's top-left corner sits at (bx + ex, by + ey)
-    if (!(fabsf(ex.hi) < 1.0e7f) || !(fabsf(ey.hi) < 1.0e7f)) return r;  // NaN/inf/far: off grid
-    float flx, fly, fx, fy;
-    df_floor_frac(ex, flx, fx);
-    df_floor_frac(ey, fly, fy);
-    const int i0 = bx + static_cast<int>(flx);
-    const int j0 = by + static_cast<int>(fly);
-    float wsum = 0.f, sAm = 0.f, sAv = 0.f, sAa = 0.f, sCm = 0.f, sCv = 0.f, sCa = 0.f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int di = q & 1, dj = q >> 1;
-        const int i = i0 + di, j = j0 + dj;
-        const float w = (di ? fx : 1.f - fx) * (dj ? fy : 1.f - fy);
-        if (i >= 0 && i < a.Gx && j >= 0 && j < a.Gy) {
-            const int k = j * a.Gx + i;
-            wsum += w;
-            sAm = fmaf(w, ld_state(a.prev.muA, k, (T*)nullptr), sAm);
-            sAv = fmaf(w, ld_state(a.prev.varA, k, (T*)nullptr), sAv);
-            sAa = fmaf(w, static_cast<float>(__ldg(a.prev.ageA + k)), sAa);
-            sCm = fmaf(w, ld_state(a.prev.muC, k, (T*)nullptr), sCm);
-            sCv = fmaf(w, ld_state(a.prev.varC, k, (T*)nullptr), sCv);
-            sCa = fmaf(w, static_cast<float>(__ldg(a.prev.ageC + k)), sCa);
-        }
+    const float* c = a.coef.c;
+    float fx, fy;
+    int i0, j0;
+    if (a.affine) {
+        const float dl = float(bx - bx0);
+        const float wx = fmaf(c[1], dl, fmaf(c[0], dl, o.fx));
+        const float wy = fmaf(c[7], dl, fmaf(c[6], dl, o.fy));
+        const float flx = floorf(wx), fly = floorf(wy);
+        fx = wx - flx;
+        fy = wy - fly;
+        i0 = bx + o.nx + int(flx);
+        j0 = by + o.ny + int(fly);
+    } else {
+        DF ex, ey;
+        if (!project_general(a.coef, (bx + 0.5f) * B, (by + 0.5f) * B, ex, ey, 1.0f / B)) return r;
+        if (!(fabsf(ex.hi) < 1.0e7f) || !(fabsf(ey.hi) < 1.0e7f)) return r;  // NaN/inf/far: off grid
+        float flx, fly;
+        df_floor_frac(ex, flx, fx);
+        df_floor_frac(ey, fly, fy);
+        i0 = bx + int(flx);
+        j0 = by + int(fly);
     }
-    if (!(wsum >= kMinWeight)) return r;
+    const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy);
+    const float w01 = (1.f - fx) * fy, w11 = fx * fy;
+    float2 mu, var, ag;
+    if (i0 >= 0 && i0 + 1 < a.Gx && j0 >= 0 && j0 + 1 < a.Gy) {
+        // interior: all four overlapped blocks exist and the weights sum to 1
+        const int k0 = j0 * a.Gx + i0, k1 = k0 + a.Gx;
+        const float2 W00 = dup2(w00), W10 = dup2(w10), W01 = dup2(w01), W11 = dup2(w11);
+        mu = __fmul2_rn(W00, ld2(a.prev.mu, k0, (T*)nullptr));
+        mu = __ffma2_rn(W10, ld2(a.prev.mu, k0 + 1, (T*)nullptr), mu);
+        mu = __ffma2_rn(W01, ld2(a.prev.mu, k1, (T*)nullptr), mu);
+        mu = __ffma2_rn(W11, ld2(a.prev.mu, k1 + 1, (T*)nullptr), mu);
+        var = __fmul2_rn(W00, ld2(a.prev.var, k0, (T*)nullptr));
+        var = __ffma2_rn(W10, ld2(a.prev.var, k0 + 1, (T*)nullptr), var);
+        var = __ffma2_rn(W01, ld2(a.prev.var, k1, (T*)nullptr), var);
+        var = __ffma2_rn(W11, ld2(a.prev.var, k1 + 1, (T*)nullptr), var);
+        ag = __fmul2_rn(W00, age2f(__ldg(a.prev.age + k0)));
+        ag = __ffma2_rn(W10, age2f(__ldg(a.prev.age + k0 + 1)), ag);
+        ag = __ffma2_rn(W01, age2f(__ldg(a.prev.age + k1)), ag);
+        ag = __ffma2_rn(W11, age2f(__ldg(a.prev.age + k1 + 1)), ag);
+    } else {
+        // border: drop out-of-grid blocks and renormalise the rest
+        float wsum = 0.f;
+        mu = var = ag = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + (q & 1), j = j0 + (q >> 1);
+            const float w = q == 0 ? w00 : q == 1 ? w10 : q == 2 ? w01 : w11;
+            if (i >= 0 && i < a.Gx && j >= 0 && j < a.Gy) {
+                const int k = j * a.Gx + i;
+                const float2 W = dup2(w);
+                wsum += w;
+                mu = __ffma2_rn(W, ld2(a.prev.mu, k, (T*)nullptr), mu);
+                var = __ffma2_rn(W, ld2(a.prev.var, k, (T*)nullptr), var);
+                ag = __ffma2_rn(W, age2f(__ldg(a.prev.age + k)), ag);
+            }
+        }
+        if (!(wsum >= kMinWeight)) return r;
+        mu = make_float2(mu.x / wsum, mu.y / wsum);
+        var = make_float2(var.x / wsum, var.y / wsum);
+        ag = make_float2(ag.x / wsum, ag.y / wsum);
+    }
     r.src = true;
-    r.A.mu = sAm / wsum;
-    r.A.var = sAv / wsum;
-    r.A.age = static_cast<int>(floorf(sAa / wsum + 0.5f));   // mixed age, half up
-    r.C.mu = sCm / wsum;
-    r.C.var = sCv / wsum;
-    r.C.age = static_cast<int>(floorf(sCa / wsum + 0.5f));
+    r.A.mu = mu.x;
+    r.C.mu = mu.y;
+    r.A.var = var.x;
+    r.C.var = var.y;
+    r.A.age = __float2int_rd(ag.x + 0.5f);   // mixed age, rounded half up
+    r.C.age = __float2int_rd(ag.y + 0.5f);
     return r;
 }
 
+// ------------------------------------------------------------------ (b)
 // Sec. 2.2 update with learning rate 1/(age~ + 1), written incrementally:
 // mu = mu~ + (M - mu~)/(age~+1), V = max_j (mu - I_j)^2 = max((mu-min)^2,
 // (max-mu)^2), var = var~ + (V - var~)/(age~+1), age + 1 below the cap.
 __device__ __forceinline__ void sgm_update(Model& m, float M, float mn, float mx, int age_max) {
-    const float a1 = static_cast<float>(m.age) + 1.0f;
-    const float mu = m.mu + (M - m.mu) / a1;
+    const float rcp = __fdividef(1.0f, static_cast<float>(m.age) + 1.0f);   // ~2 ulp
+    const float mu = fmaf(M - m.mu, rcp, m.mu);
     const float d0 = mu - mn, d1 = mx - mu;
     const float V = fmaxf(d0 * d0, d1 * d1);
-    m.var = m.var + (V - m.var) / a1;
+    m.var = fmaf(V - m.var, rcp, m.var);
     m.mu = mu;
     m.age = (m.age < age_max) ? m.age + 1 : m.age;
 }
 
-// (b) match -> update -> reset -> swap (Sec. 2.3) from the compensated models.
+// Match -> update -> reset -> swap (Sec. 2.3) from the compensated models.
 __device__ __forceinline__ void dual_mode_step(Comp& c, float M, float mn, float mx,
                                                const StreamArgs& a) {
     const Model reset{M, kVarInit, 1};
@@ -326,106 +439,175 @@ __device__ __forceinline__ void dual_mode_step(Comp& c, float M, float mn, float
     }
 }
 
-// Foreground bits of 4 pixels packed in a little-endian word.
-__device__ __forceinline__ uint32_t fg_nibble(uint32_t px4, float mu, float thr) {
-    uint32_t nib = 0;
+// Byte statistics of a block given as N words (4 pixels each): the sum by
+// 4-way dot products, min and max on 16-bit lanes (bytes 0/2 and 1/3 of each
+// word) with the 3-input DPX min/max instructions.
+template <int N>
+__device__ __forceinline__ void block_stats(const uint32_t* w, float& M, float& mn, float& mx) {
+    uint32_t s = 0, lo2 = 0x00FF00FFu, hi2 = 0u;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float d = static_cast<float>((px4 >> (8 * j)) & 0xffu) - mu;
-        nib |= (d * d > thr) ? (1u << j) : 0u;
+    for (int i = 0; i < N; ++i) {
+        s = __dp4a(w[i], 0x01010101u, s);
+        const uint32_t e = w[i] & 0x00FF00FFu, o = (w[i] >> 8) & 0x00FF00FFu;
+        lo2 = __vimin3_u16x2(lo2, e, o);
+        hi2 = __vimax3_u16x2(hi2, e, o);
     }
-    return nib;
+    M = static_cast<float>(s) * (1.0f / (4 * N));   // exact: 4N is a power of two
+    mn = static_cast<float>(min(lo2 & 0xFFFFu, lo2 >> 16));
+    mx = static_cast<float>(max(hi2 & 0xFFFFu, hi2 >> 16));
 }
 
-// Sum / min / max of the 4 bytes of a word, accumulated.
-__device__ __forceinline__ void stats4(uint32_t w, uint32_t& sum, uint32_t& mn4, uint32_t& mx4) {
-    sum = __dp4a(w, 0x01010101u, sum);
-    mn4 = __vminu4(mn4, w);
-    mx4 = __vmaxu4(mx4, w);
+// ------------------------------------------------------------------ (c)
+// The per-pixel test (I - mu)^2 > thr, evaluated in FP32, is monotone in
+// |I - mu|, so its background set is an interval [lo, hi] of intensities.
+// bg_interval finds that interval exactly (the FP32 test itself decides the
+// boundary integers) and fg_nibble then tests 4 pixels at once on bytes.
+__device__ __forceinline__ bool is_bg(float I, float mu, float thr) {
+    const float d = I - mu;
+    return d * d <= thr;
 }
 
-__device__ __forceinline__ uint32_t min_byte(uint32_t v) {
-    v = __vminu4(v, v >> 16);
-    v = __vminu4(v, v >> 8);
-    return v & 0xffu;
-}
-__device__ __forceinline__ uint32_t max_byte(uint32_t v) {
-    v = __vmaxu4(v, v >> 16);
-    v = __vmaxu4(v, v >> 8);
-    return v & 0xffu;
+struct Thresh {
+    uint32_t c_gt;   // 255 - hi in every byte: x > hi  <=>  x + c_gt carries
+    uint32_t c_lt;   // lo in every byte:       x < lo  <=>  ~x + c_lt carries
+    uint32_t all;    // 0x80808080 when no intensity is background
+};
+
+__device__ __forceinline__ Thresh bg_interval(float mu, float thr) {
+    // s slightly below sqrt(thr) (the approximate rsqrt is within 3e-7), so
+    // every integer within s of mu is background and the true ends of the
+    // interval lie at most one step beyond floor(mu + s) / ceil(mu - s)
+    const float s = thr * rsqrtf(fmaxf(thr, 1.0e-30f)) * (1.0f - 1.0e-6f);
+    float hi = floorf(mu + s);
+    float lo = ceilf(mu - s);
+    hi += is_bg(hi + 1.f, mu, thr) ? 1.f : 0.f;
+    lo -= is_bg(lo - 1.f, mu, thr) ? 1.f : 0.f;
+    const int ih = min(max(__float2int_rd(hi), -1), 255);
+    const int il = min(max(__float2int_rd(lo), 0), 256);
+    Thresh t;
+    t.all = il > ih ? 0x80808080u : 0u;
+    t.c_gt = uint32_t(255 - max(ih, 0)) * 0x01010101u;
+    t.c_lt = uint32_t(min(il, 255)) * 0x01010101u;
+    return t;
 }
 
-// Process one tile whose pixels are in shared memory (row pitch kTileW).
-// tx0 / ty0: pixel origin of the tile.  The caller has compensated every
-// strip of the thread into comp[] (before waiting for the pixels).
-template <int B, typename T, int RPT>
+// Per-byte carry out of x + c (bit 7 of every byte), no carries between bytes:
+// the majority of the two top bits and the carry into bit 7.
+__device__ __forceinline__ uint32_t carry8(uint32_t x, uint32_t c) {
+    const uint32_t s = (x & 0x7f7f7f7fu) + (c & 0x7f7f7f7fu);
+    return ((x & c) | ((x | c) & s)) & 0x80808080u;
+}
+
+// Foreground bits of the 4 pixels of w (byte j -> bit j), at bits 28..31.
+__device__ __forceinline__ uint32_t fg_nibble_hi(uint32_t w, const Thresh& t) {
+    const uint32_t f = carry8(w, t.c_gt) | carry8(~w, t.c_lt) | t.all;
+    // byte j's flag -> bit 28 + j; the cross terms of the product all land
+    // below bit 28 (on distinct bits, so nothing carries) and are masked off
+    return (((f >> 7) & 0x01010101u) * 0x10204080u) & 0xF0000000u;
+}
+
+// Store a block's next state (both models).
+template <typename T>
+__device__ __forceinline__ void store_block(const StreamArgs& a, int k, const Comp& c) {
+    st2(a.next.mu, k, make_float2(c.A.mu, c.C.mu), (T*)nullptr);
+    st2(a.next.var, k, make_float2(c.A.var, c.C.var), (T*)nullptr);
+    a.next.age[k] = static_cast<uint16_t>(min(c.A.age, 255) | (min(c.C.age, 255) << 8));
+}
+
+// ------------------------------------------------------------------ tiles
+// Lane layout: warp w of the CTA takes strip rows w, w + NW, ...; lane l owns
+// pixel columns [tx0 + 8l, tx0 + 8l + 8) of its strip row, i.e. two 4x4
+// blocks (B = 4) or one 8x8 block (B = 8), and writes one mask byte per row.
+// A tile is kTileW x (NW * B * RPT) pixels.
+template <int B, typename T, int NW, int RPT>
+__device__ __forceinline__ void compensate_tile(const StreamArgs& a, int tx0, int ty0,
+                                                const Origin* orig,
+                                                Comp (&comp)[RPT][kLanePx / B]) {
+    constexpr int BPL = kLanePx / B;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = tx0 + kLanePx * lane;
+    const int bx = x / B;
+    const int half = lane >> 4;
+    const int bx0 = (tx0 + 128 * half) / B;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int s = warp + NW * r;
+        const int by = ty0 / B + s;
+        const bool in = x < a.W && by < a.Gy;
+#pragma unroll
+        for (int j = 0; j < BPL; ++j) {
+            if (in) comp[r][j] = compensate<B, T>(a, bx + j, by, bx0, orig[(s << 1) | half]);
+            else comp[r][j].src = false;
+        }
+    }
+}
+
+// Finish a tile whose pixels are in shared memory (row pitch kTileW): block
+// statistics, the dual-mode update, the next state and the mask bytes.
+template <int B, typename T, int NW, int RPT>
 __device__ __forceinline__ void finish_tile(const StreamArgs& a, const uint8_t* tile, int tx0,
-                                            int ty0, Comp (&comp)[RPT]) {
-    const int sc = threadIdx.x % kStripCols;
-    const int sr = threadIdx.x / kStripCols;
-    const int lane = threadIdx.x & 31;
-    const int x = tx0 + 4 * sc;
+                                            int ty0, Comp (&comp)[RPT][kLanePx / B]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = tx0 + kLanePx * lane;
     const bool xin = x < a.W;
     const int bx = x / B;
+    const size_t mrow = size_t(a.mask_words) * 4;            // mask bytes per row
+    uint8_t* mcol = reinterpret_cast<uint8_t*>(a.mask) + (x >> 3);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-        const int s = sr + kStripRowsPerPass * r;        // strip row inside the tile
+        const int s = warp + NW * r;
         const int by = ty0 / B + s;
-        if (by >= a.Gy) break;                           // warp-uniform
-        uint32_t px[B];
-        uint32_t sum = 0, mn4 = 0xffffffffu, mx4 = 0u;
+        if (by >= a.Gy) break;                                 // warp-uniform
+        uint32_t lw[B], rw[B];                                 // left / right 4 pixels per row
 #pragma unroll
         for (int i = 0; i < B; ++i) {
-            px[i] = xin ? *reinterpret_cast<const uint32_t*>(tile + (B * s + i) * kTileW + 4 * sc)
-                        : 0u;
-            stats4(px[i], sum, mn4, mx4);
+            const uint2 v = xin ? *reinterpret_cast<const uint2*>(tile + (B * s + i) * kTileW +
+                                                                  kLanePx * lane)
+                                : make_uint2(0u, 0u);
+            lw[i] = v.x;
+            rw[i] = v.y;
         }
-        uint32_t mn = min_byte(mn4), mx = max_byte(mx4);
-        if (B == 8) {  // the other half of the block sits in the neighbour lane
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, 1));
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-        }
-        const float M = static_cast<float>(sum) * (1.0f / (B * B));   // exact
-        Comp c = comp[r];
-        dual_mode_step(c, M, static_cast<float>(mn), static_cast<float>(mx), a);
+        uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
         const int k = by * a.Gx + bx;
-        if (xin && (B == 4 || (lane & 1) == 0)) {
-            st_state(a.next.muA, k, c.A.mu, (T*)nullptr);
-            st_state(a.next.varA, k, c.A.var, (T*)nullptr);
-            st_state(a.next.muC, k, c.C.mu, (T*)nullptr);
-            st_state(a.next.varC, k, c.C.var, (T*)nullptr);
-            a.next.ageA[k] = static_cast<uint8_t>(min(c.A.age, 255));
-            a.next.ageC[k] = static_cast<uint8_t>(min(c.C.age, 255));
-        }
-        // (c) the mask, with the final apparent model
-        const float thr = a.theta_d * c.A.var;
-        const int y0 = ty0 + B * s;
+        if (B == 4) {
+            float M, mn, mx;
+            Comp cl = comp[r][0], cr = comp[r][kLanePx / B - 1];
+            block_stats<4>(lw, M, mn, mx);
+            dual_mode_step(cl, M, mn, mx, a);
+            block_stats<4>(rw, M, mn, mx);
+            dual_mode_step(cr, M, mn, mx, a);
+            if (xin) {
+                store_block<T>(a, k, cl);
+                store_block<T>(a, k + 1, cr);
+            }
+            const Thresh tl = bg_interval(cl.A.mu, a.theta_d * cl.A.var);
+            const Thresh tr = bg_interval(cr.A.mu, a.theta_d * cr.A.var);
+            if (xin) {
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-            uint32_t v = xin ? (fg_nibble(px[i], c.A.mu, thr) << (4 * (lane & 7))) : 0u;
-            v |= __shfl_xor_sync(0xffffffffu, v, 1);
-            v |= __shfl_xor_sync(0xffffffffu, v, 2);
-            v |= __shfl_xor_sync(0xffffffffu, v, 4);
-            if ((lane & 7) == 0 && xin)
-                a.mask[static_cast<size_t>(y0 + i) * a.mask_words + (x >> 5)] = v;
-        }
-    }
-}
-
-// Compensation of every strip the thread owns in a tile.
-template <int B, typename T, int RPT>
-__device__ __forceinline__ void compensate_tile(const StreamArgs& a, int tx0, int ty0,
-                                                Comp (&comp)[RPT]) {
-    const int sc = threadIdx.x % kStripCols;
-    const int sr = threadIdx.x / kStripCols;
-    const int x = tx0 + 4 * sc;
-    const int bx = x / B;
+                for (int i = 0; i < B; ++i)
+                    m[i * mrow] = uint8_t((fg_nibble_hi(lw[i], tl) >> 28) |
+                                          (fg_nibble_hi(rw[i], tr) >> 24));
+            }
+        } else {
+            uint32_t all[2 * B];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int by = ty0 / B + sr + kStripRowsPerPass * r;
-        if (x < a.W && by < a.Gy) comp[r] = compensate<B, T>(a, bx, by);
-        else comp[r].src = false;
+            for (int i = 0; i < B; ++i) {
+                all[2 * i] = lw[i];
+                all[2 * i + 1] = rw[i];
+            }
+            float M, mn, mx;
+            Comp c = comp[r][0];
+            block_stats<2 * B>(all, M, mn, mx);
+            dual_mode_step(c, M, mn, mx, a);
+            if (xin) store_block<T>(a, k, c);
+            const Thresh t = bg_interval(c.A.mu, a.theta_d * c.A.var);
+            if (xin) {
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    m[i * mrow] = uint8_t((fg_nibble_hi(lw[i], t) >> 28) |
+                                          (fg_nibble_hi(rw[i], t) >> 24));
+            }
+        }
     }
 }
 

@@ -66,17 +66,20 @@ struct dmsgm_ctx {
 
 namespace dmsgm {
 
-// FP64 homography -> FP32 displacement coefficients; false if not finite.
-bool make_coef(const double H3x3[9], Coef* c);
+// FP64 homography -> double-float coefficients for block size B, in the
+// affine form when it applies (affine = 1) or the general form; false if a
+// coefficient is not finite in FP32.
+bool make_coef(const double H3x3[9], int B, Coef* c, int* affine);
 
 // Fill the per-frame kernel arguments of handle h (reads h->parity etc.).
-void fill_args(const dmsgm_ctx* h, const Coef& c, uint32_t* mask_dev, StreamArgs* a);
+void fill_args(const dmsgm_ctx* h, const Coef& c, int affine, uint32_t* mask_dev, StreamArgs* a);
 
 // Advance the handle's bookkeeping after a frame has been enqueued.
 void advance(dmsgm_ctx* h);
 
 // Launch the batched persistent kernel (dmsgm_batch.cu).
 int launch_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
-                 const double* H3x3s, uint32_t* const* masks_dev, cudaStream_t stream);
+                 const double* H3x3s, uint32_t* const* masks_dev, const dmsgm_batch_opts& o,
+                 cudaStream_t stream);
 
 }  // namespace dmsgm

@@ -99,26 +99,29 @@ class Dmsgm:
         return n, fdt
 
     def get_state(self) -> dict:
-        """Current state as arrays of shape (grid_h, grid_w) (synchronises)."""
+        """Current state as arrays of shape (grid_h, grid_w) (synchronises).
+        The packed image holds mu (A, C pairs), var (A, C pairs), age (A, C
+        byte pairs), block by block."""
         n, fdt = self._layout()
         buf = np.zeros(self.info().host_state_bytes, dtype=np.uint8)
         _lib.dmsgm_get_state(self._h, buf)
         fs = np.dtype(fdt).itemsize
-        out, off = {}, 0
-        for name in ("muA", "varA", "muC", "varC"):
-            out[name] = buf[off:off + n * fs].view(fdt).reshape(self.grid_h, self.grid_w).copy()
-            off += n * fs
-        for name in ("ageA", "ageC"):
-            out[name] = buf[off:off + n].reshape(self.grid_h, self.grid_w).copy()
-            off += n
-        return out
+        shp = (self.grid_h, self.grid_w)
+        mu = buf[:2 * n * fs].view(fdt).reshape(n, 2)
+        var = buf[2 * n * fs:4 * n * fs].view(fdt).reshape(n, 2)
+        age = buf[4 * n * fs:4 * n * fs + 2 * n].reshape(n, 2)
+        return {"muA": mu[:, 0].reshape(shp).copy(), "muC": mu[:, 1].reshape(shp).copy(),
+                "varA": var[:, 0].reshape(shp).copy(), "varC": var[:, 1].reshape(shp).copy(),
+                "ageA": age[:, 0].reshape(shp).copy(), "ageC": age[:, 1].reshape(shp).copy()}
 
     def set_state(self, st: dict):
         n, fdt = self._layout()
-        parts = [np.ascontiguousarray(st[k], dtype=fdt).reshape(-1)
-                 for k in ("muA", "varA", "muC", "varC")]
-        parts += [np.ascontiguousarray(st[k], dtype=np.uint8).reshape(-1) for k in ("ageA", "ageC")]
-        buf = np.concatenate([p.view(np.uint8) for p in parts])
+        pair = lambda a, c, dt: np.stack(  # noqa: E731
+            [np.asarray(st[a], dtype=dt).reshape(-1), np.asarray(st[c], dtype=dt).reshape(-1)],
+            axis=1)
+        parts = [pair("muA", "muC", fdt), pair("varA", "varC", fdt),
+                 pair("ageA", "ageC", np.uint8)]
+        buf = np.concatenate([np.ascontiguousarray(p).view(np.uint8).reshape(-1) for p in parts])
         assert buf.size == self.info().host_state_bytes
         _lib.dmsgm_set_state(self._h, buf)
 
@@ -147,8 +150,9 @@ class Dmsgm:
             pass
 
 
-def process_batch(models, frames, Hs, masks, stream=None):
-    """One frame for each of several handles in one launch."""
+def process_batch(models, frames, Hs, masks, stream=None, ctas: int = 0, use_pdl: bool = False):
+    """One frame for each of several handles in one persistent launch."""
+    opts = _lib.dmsgm_batch_opts(0, ctas, 1 if use_pdl else 0)
     _lib.dmsgm_process_batch([m.handle for m in models], [f.data_ptr() for f in frames],
                              np.asarray(Hs), [k.data_ptr() for k in masks],
-                             _stream_handle(stream))
+                             _stream_handle(stream), opts)

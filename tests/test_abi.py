@@ -37,12 +37,13 @@ def test_exports_every_declared_symbol(L):
 
 def test_version_and_sizes(L):
     assert "sm_103a" in L.dmsgm_version()
-    # 1920x1080, B=4: 480x270 blocks; FP32 buffer = 4 arrays of N*4 + 2 of N,
-    # each rounded up to 256 bytes, two buffers plus a 256-byte control block
+    # 1920x1080, B=4: 480x270 blocks; a buffer = mu and var arrays of N
+    # (A, C) pairs and an age array of N byte pairs, each rounded up to 256
+    # bytes; two buffers plus a 256-byte control block
     N = 480 * 270
     r = lambda x: (x + 255) // 256 * 256  # noqa: E731
-    assert L.dmsgm_state_bytes(1920, 1080, 4, 0) == 256 + 2 * (4 * r(4 * N) + 2 * r(N))
-    assert L.dmsgm_state_bytes(1920, 1080, 4, 1) == 256 + 2 * (4 * r(2 * N) + 2 * r(N))
+    assert L.dmsgm_state_bytes(1920, 1080, 4, 0) == 256 + 2 * (2 * r(8 * N) + r(2 * N))
+    assert L.dmsgm_state_bytes(1920, 1080, 4, 1) == 256 + 2 * (2 * r(4 * N) + r(2 * N))
     assert L.dmsgm_host_state_bytes(1920, 1080, 4, 0) == N * 18
     assert L.dmsgm_host_state_bytes(3840, 2160, 8, 1) == 480 * 270 * 10
     assert L.dmsgm_state_bytes(100, 100, 4, 0) == 0       # W % 16 != 0

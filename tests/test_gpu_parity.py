@@ -53,11 +53,12 @@ def test_plain_320x240_all_frames_teacher_forced(lib, block):
     assert rep.exempt <= 1e-3 * rep.blocks, rep
 
 
-@pytest.mark.parametrize("tile_rows", [16, 32, 64])
-def test_tile_shapes_agree(lib, tile_rows):
-    """Every tile height gives the same bits (a ragged tail in y for 240 rows)."""
+@pytest.mark.parametrize("block,tile_rows", [(4, 16), (4, 32), (4, 64), (8, 32), (8, 64),
+                                             (8, 128)])
+def test_tile_shapes_agree(lib, block, tile_rows):
+    """Every tile height passes (a ragged tail in y for 240 rows)."""
     frames, Hs = make_stream(StreamSpec(320, 240, 12, seed=3), device="cuda")
-    rep = _run_teacher_forced(lib, frames, Hs, block=4, tile_rows=tile_rows)
+    rep = _run_teacher_forced(lib, frames, Hs, block=block, tile_rows=tile_rows)
     rep.assert_ok()
 
 
@@ -258,3 +259,48 @@ def test_caller_owned_state_memory(lib):
     for t in range(5):
         assert torch.equal(a.process(frames[t], Hs[t]), b.process(frames[t], Hs[t]))
     a.close()
+
+
+@pytest.mark.parametrize("ctas,pdl", [(0, False), (0, True), (1, False), (3, True), (7, True)])
+def test_batch_launch_shapes(lib, ctas, pdl):
+    """The persistent batched kernel with every launch shape (a single CTA
+    walks the whole work list through its two-stage ring) matches the
+    single-stream kernel bit for bit, over several steps."""
+    cfgs = [(1920, 1080, 4, "fp32"), (320, 240, 8, "fp32"), (640, 480, 4, "fp16"),
+            (272, 40, 8, "fp16")]
+    streams = [make_stream(StreamSpec(w, h, 4, seed=200 + i), device="cuda")
+               for i, (w, h, b, p) in enumerate(cfgs)]
+    solo = [lib.Dmsgm(w, h, b, precision=p) for (w, h, b, p) in cfgs]
+    bat = [lib.Dmsgm(w, h, b, precision=p) for (w, h, b, p) in cfgs]
+    for t in range(4):
+        ref = [m.process(fr[t], Hs[t]).clone() for m, (fr, Hs) in zip(solo, streams)]
+        outs = [lib.new_mask(h, w) for (w, h, b, p) in cfgs]
+        lib.process_batch(bat, [fr[t] for fr, _ in streams],
+                          np.stack([Hs[t] for _, Hs in streams]), outs,
+                          ctas=ctas, use_pdl=pdl)
+        for r, o in zip(ref, outs):
+            assert torch.equal(r, o)
+    for a, b in zip(solo, bat):
+        sa, sb = a.get_state(), b.get_state()
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), k
+    for m in bat:
+        assert m.status() == 0
+
+
+def test_batch_teacher_forced_vs_oracle(lib):
+    """A 64-stream-like mix (fewer frames) checked against the oracle."""
+    cfgs = [(320, 240, 4), (640, 480, 8), (1280, 720, 4)]
+    streams = [make_stream(spec_for(w, h, 3, seed=1000 + i), device="cuda")
+               for i, (w, h, b) in enumerate(cfgs)]
+    ms = [lib.Dmsgm(w, h, b) for (w, h, b) in cfgs]
+    rep = StepReport()
+    for t in range(3):
+        prev = [m.get_state() for m in ms] if t else [None] * len(ms)
+        outs = [lib.new_mask(h, w) for (w, h, b) in cfgs]
+        lib.process_batch(ms, [fr[t] for fr, _ in streams],
+                          np.stack([Hs[t] for _, Hs in streams]), outs)
+        for m, (w, h, b), (fr, Hs), o, p in zip(ms, cfgs, streams, outs, prev):
+            rep.add(compare_step(p, m.get_state(), lib.unpack_mask(o, w), fr[t].cpu().numpy(),
+                                 Hs[t], block=b))
+    rep.assert_ok()
