@@ -111,7 +111,9 @@ size_t dmsgm_state_bytes(int width, int height, int block, int precision);
  * stored, then age (Gx*Gy byte pairs (age_A, age_C)). */
 size_t dmsgm_host_state_bytes(int width, int height, int block, int precision);
 
-/* Create a handle on the current CUDA device.  theta_s is the match
+/* Create a handle on the current CUDA device.  The state is undefined until
+ * the first process() (which starts every block afresh) or set_state().
+ * theta_s is the match
  * threshold of Sec. 2.3, theta_d the foreground threshold, age_max the age
  * cap of Sec. 2.2 (30 in the paper).  Validation: width, height > 0;
  * block in {4, 8}; width % 16 == 0; width and height multiples of block;
@@ -121,7 +123,10 @@ int dmsgm_create(int width, int height, int block, float theta_s, float theta_d,
 int dmsgm_create_ex(int width, int height, int block, float theta_s, float theta_d,
                     int age_max, const dmsgm_opts* opts, dmsgm_t* out);
 
-/* Destroy a handle (NULL-safe).  Synchronises the device work of the handle. */
+/* Destroy a handle (NULL-safe).  If the handle allocated its own state or
+ * staging memory, the device is synchronised before that memory is freed;
+ * with caller-owned state memory (dmsgm_opts.state_mem) nothing waits, and
+ * the caller keeps the memory alive until its queued work is done. */
 int dmsgm_destroy(dmsgm_t h);
 
 /* One frame, asynchronously on cuda_stream (a cudaStream_t; NULL = legacy
@@ -161,7 +166,8 @@ int dmsgm_process_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_d
  * A work item is a 256 x (8*block) pixel tile of one stream. */
 typedef struct {
     int reserved;    /* must be 0                                             */
-    int ctas;        /* persistent CTAs; 0 = every CTA that fits on the GPU   */
+    int ctas;        /* CTAs of the launch (each walks the work list with a
+                        stride of ctas); 0 = as many as fit on the GPU at once */
     int use_pdl;     /* 1: programmatic dependent launch (the first tile's
                         pixels load while the previous kernel drains; frames
                         must not be written by the immediately preceding

@@ -1,0 +1,166 @@
+"""Many streams per launch: a runner that captures frame-steps of a set of
+streams into one CUDA graph, and an autotuner for the batched kernel's
+launch shape.
+
+A "step" advances every stream of the batch by one frame in ONE launch of
+the persistent batched kernel (dmsgm_process_batch_ex); a captured graph
+replays `steps` consecutive steps.  The plain path (one launch of the
+single-stream kernel per stream per step, also captured) is kept alongside
+for comparison.  All arithmetic happens in libdmsgm.so.
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from .dmsgm import Dmsgm, new_mask
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+@dataclass(frozen=True)
+class LaunchShape:
+    ctas: int = 0          # persistent CTAs (0: all that fit)
+    use_pdl: bool = True
+
+    def opts(self) -> _lib.dmsgm_batch_opts:
+        return _lib.dmsgm_batch_opts(0, self.ctas, 1 if self.use_pdl else 0)
+
+
+def _ptr_arrays(models, frames_t, masks_t):
+    n = len(models)
+    hs = (_lib.ctypes.c_void_p * n)(*[m.handle.value for m in models])
+    fr = (_lib.ctypes.c_void_p * n)(*[f.data_ptr() for f in frames_t])
+    mk = (_lib.ctypes.c_void_p * n)(*[k.data_ptr() for k in masks_t])
+    return hs, fr, mk
+
+
+class BatchRunner:
+    """Streams of mixed size / block / precision stepped together.
+
+    frames[i]: uint8 (T, H_i, W_i) device tensor of stream i; Hs[i]: (T, 3, 3)
+    homographies.  Masks are written to per-stream device tensors
+    (T, H_i, ceil(W_i/32)).
+    """
+
+    def __init__(self, specs, frames, Hs, precision="fp32", device="cuda"):
+        self.specs = specs           # [(W, H, B)]
+        self.frames = frames
+        self.Hs = [np.ascontiguousarray(h, dtype=np.float64) for h in Hs]
+        self.T = min(f.shape[0] for f in frames)
+        self.precision = precision
+        self.models = [Dmsgm(w, h, b, precision=precision) for (w, h, b) in specs]
+        self.masks = [new_mask(h, w, device, n=self.T) for (w, h, b) in specs]
+        self.pixels_per_step = sum(w * h for (w, h, b) in specs)
+        self._H_steps = [np.stack([self.Hs[i][t] for i in range(len(specs))]).reshape(-1)
+                         for t in range(self.T)]
+
+    # -------------------------------------------------------------- launches
+    def step_batched(self, t: int, shape: LaunchShape, stream: int):
+        hs, fr, mk = _ptr_arrays(self.models, [f[t] for f in self.frames],
+                                 [k[t] for k in self.masks])
+        opts = shape.opts()
+        rc = _lib.load_library().dmsgm_process_batch_ex(
+            len(self.models), hs, fr, self._H_steps[t].ctypes.data, mk, _lib.ctypes.byref(opts),
+            stream)
+        _lib._check(rc)
+
+    def step_plain(self, t: int, stream: int):
+        for i, m in enumerate(self.models):
+            _lib.dmsgm_process(m.handle, self.frames[i][t].data_ptr(), self.Hs[i][t],
+                               self.masks[i][t].data_ptr(), stream)
+
+    def capture(self, mode: str, shape: LaunchShape | None = None, steps: int | None = None,
+                stream: torch.cuda.Stream | None = None) -> torch.cuda.CUDAGraph:
+        """Capture `steps` (default T, even) consecutive steps into a graph."""
+        steps = steps or self.T
+        assert steps % 2 == 0, "an even number of steps keeps the handles' parity consistent"
+        stream = stream or torch.cuda.Stream()
+        sh = stream.cuda_stream
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for k in range(steps):
+                t = k % self.T
+                if mode == "batched":
+                    self.step_batched(t, shape or LaunchShape(), sh)
+                else:
+                    self.step_plain(t, sh)
+        return g
+
+    def warm(self, mode: str, shape: LaunchShape | None = None, stream=None):
+        stream = stream or torch.cuda.current_stream()
+        for t in range(2):
+            if mode == "batched":
+                self.step_batched(t, shape or LaunchShape(), stream.cuda_stream)
+            else:
+                self.step_plain(t, stream.cuda_stream)
+        stream.synchronize()
+
+    def close(self):
+        for m in self.models:
+            m.close()
+
+
+def time_graph(g: torch.cuda.CUDAGraph, stream: torch.cuda.Stream, reps: int = 3) -> float:
+    """Mean milliseconds per replay (CUDA events on the replay stream)."""
+    with torch.cuda.stream(stream):
+        g.replay()
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            g.replay()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _key(specs, precision, sms):
+    sig = sorted(f"{w}x{h}b{b}" for (w, h, b) in specs)
+    return json.dumps([sig, precision, sms])
+
+
+def autotune(runner: BatchRunner, candidates=None, steps: int = 8, use_cache: bool = True):
+    """Pick the launch shape (CTA count, PDL) of the batched kernel that gives
+    the shortest step on this GPU for this stream mix; cached on disk by the
+    mix, the precision and the SM count."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    key = _key(runner.specs, runner.precision, sms)
+    cache = {}
+    if use_cache and os.path.exists(_CACHE):
+        try:
+            with open(_CACHE) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        d = cache[key]
+        return LaunchShape(d["ctas"], d["use_pdl"]), d.get("results", [])
+    if candidates is None:
+        candidates = [LaunchShape(0, True), LaunchShape(0, False)]
+        for per_sm in (1, 2, 3, 4):
+            candidates.append(LaunchShape(per_sm * sms, True))
+        candidates.append(LaunchShape(1 << 30, True))   # one work item per CTA
+    stream = torch.cuda.Stream()
+    results = []
+    for c in candidates:
+        runner.warm("batched", c, stream)
+        g = runner.capture("batched", c, steps=steps, stream=stream)
+        ms = time_graph(g, stream, reps=3) / steps
+        results.append({"ctas": c.ctas, "use_pdl": c.use_pdl, "ms_per_step": ms})
+        del g
+    best = min(results, key=lambda r: r["ms_per_step"])
+    shape = LaunchShape(best["ctas"], best["use_pdl"])
+    if use_cache:
+        cache[key] = {"ctas": shape.ctas, "use_pdl": shape.use_pdl, "results": results}
+        os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+        with open(_CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return shape, results

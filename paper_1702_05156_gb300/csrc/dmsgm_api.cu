@@ -34,11 +34,12 @@ constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // 2 s: only a broken copy 
 // 8x8 blocks: 32 registers (full occupancy) measured faster despite a small
 // spill; 4x4 blocks keep the compiler's choice.
 template <int B, int NW>
-constexpr int step_min_blocks() { return B == 8 ? 256 / NW : 1; }
+constexpr int step_min_blocks() { return B == 8 ? 64 / NW : 1; }
 
 template <int B, typename T, int NW, int RPT>
 __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
-    dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, int* status) {
+    dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, const Coef k,
+                      int* status) {
     constexpr int STRIPS = NW * RPT;          // strip rows per tile
     constexpr int TILE_H = STRIPS * B;
     __shared__ __align__(128) uint8_t tile[TILE_H * kTileW];
@@ -52,13 +53,13 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
         mbar_arrive_expect_tx(&bar, TILE_H * kTileW);
         tma_load_2d(tile, &tmap, tx0, ty0, &bar);
     }
-    fill_origins<B>(a, tx0, ty0, STRIPS, orig);
+    fill_origins<B>(a, k, tx0, ty0, STRIPS, orig);
     __syncthreads();
     // The pixels do not depend on the previous frame's kernel; the state does.
     pdl_wait();
     pdl_launch_dependents();
     Comp comp[RPT][kLanePx / B];
-    compensate_tile<B, T, NW, RPT>(a, tx0, ty0, orig, comp);
+    compensate_tile<B, T, NW, RPT>(a, k, tx0, ty0, orig, comp);
     const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
     if (__syncthreads_or(!ok)) {
         // report, give the copy one more bounded chance to land, and leave
@@ -70,8 +71,8 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
 }
 
 template <int B, typename T, int NW, int RPT>
-static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, int* status,
-                                 cudaStream_t s, bool pdl) {
+static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, const Coef& k,
+                                 int* status, cudaStream_t s, bool pdl) {
     constexpr int TILE_H = NW * RPT * B;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
@@ -83,15 +84,16 @@ static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, i
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, dmsgm_step_kernel<B, T, NW, RPT>, tmap, a, status);
+    return cudaLaunchKernelEx(&cfg, dmsgm_step_kernel<B, T, NW, RPT>, tmap, a, k, status);
 }
 
 // tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1), (8, 2)}
 static cudaError_t launch_step(int B, int prec, int tile_rows, const CUtensorMap& tmap,
-                               const StreamArgs& a, int* status, cudaStream_t s, bool pdl) {
+                               const StreamArgs& a, const Coef& k, int* status, cudaStream_t s,
+                               bool pdl) {
     const int q = tile_rows / B;   // 4, 8 or 16
 #define DMSGM_CASE(BB, TT, QQ, NWW, RR) \
-    if (B == BB && q == QQ) return launch_step_t<BB, TT, NWW, RR>(tmap, a, status, s, pdl);
+    if (B == BB && q == QQ) return launch_step_t<BB, TT, NWW, RR>(tmap, a, k, status, s, pdl);
     if (prec == DMSGM_STATE_FP32) {
         DMSGM_CASE(4, float, 4, 4, 1) DMSGM_CASE(4, float, 8, 8, 1) DMSGM_CASE(4, float, 16, 8, 2)
         DMSGM_CASE(8, float, 4, 4, 1) DMSGM_CASE(8, float, 8, 8, 1) DMSGM_CASE(8, float, 16, 8, 2)
@@ -215,7 +217,7 @@ bool make_coef(const double m[9], int B, Coef* c, int* affine) {
     return true;
 }
 
-void fill_args(const dmsgm_ctx* h, const Coef& c, int affine, uint32_t* mask_dev, StreamArgs* a) {
+void fill_args(const dmsgm_ctx* h, int affine, uint32_t* mask_dev, StreamArgs* a) {
     a->prev = h->buf[h->parity];
     a->next = h->buf[h->parity ^ 1];
     a->mask = mask_dev;
@@ -229,7 +231,6 @@ void fill_args(const dmsgm_ctx* h, const Coef& c, int affine, uint32_t* mask_dev
     a->age_max = h->age_max;
     a->theta_s = h->theta_s;
     a->theta_d = h->theta_d;
-    a->coef = c;
 }
 
 void advance(dmsgm_ctx* h) {
@@ -248,8 +249,8 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
     int rc = frame_map(h, frame_dev, &tm);
     if (rc) return rc;
     StreamArgs a;
-    fill_args(h, c, affine, mask_dev, &a);
-    cudaError_t e = launch_step(h->B, h->prec, h->tile_rows, *tm, a, h->status_dev, s,
+    fill_args(h, affine, mask_dev, &a);
+    cudaError_t e = launch_step(h->B, h->prec, h->tile_rows, *tm, a, c, h->status_dev, s,
                                 h->use_pdl != 0);
     if (e != cudaSuccess) return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     advance(h);
@@ -377,8 +378,11 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
         h->owns_mem = true;
     }
     carve(h);
-    cudaError_t e = cudaMemset(h->mem, 0, need);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    // Only the control block needs a defined value (the status word); the
+    // state buffers are written by the first process() or set_state().  A
+    // synchronous copy from the host orders it without a device-wide sync.
+    static const unsigned char zeros[256] = {0};
+    cudaError_t e = cudaMemcpy(h->mem, zeros, sizeof zeros, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (h->owns_mem) cudaFree(h->mem);
         delete h;
@@ -396,7 +400,10 @@ int dmsgm_destroy(dmsgm_t h) {
     clear_error();
     if (!h) return DMSGM_OK;
     DeviceGuard g(h->device);
-    cudaError_t e = cudaDeviceSynchronize();
+    // Memory the handle owns may still be in use by queued work; memory the
+    // caller lent it is the caller's to order.
+    cudaError_t e = cudaSuccess;
+    if (h->owns_mem || h->stage.slots) e = cudaDeviceSynchronize();
     free_stage(h);
     if (h->owns_mem && h->mem) cudaFree(h->mem);
     delete h;

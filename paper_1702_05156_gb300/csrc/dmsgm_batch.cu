@@ -47,46 +47,41 @@ static_assert(sizeof(BatchParams<DMSGM_MAX_BATCH>) <= 32764, "kernel parameter l
 constexpr int kBatchWarps = 8;
 constexpr int kStageRows = kBatchWarps * 8;
 
+// Stream whose work items contain t (the last with tile_begin <= t).
 template <int CAP>
-__device__ __forceinline__ void stage_item(const BatchParams<CAP>& p, int t, StreamArgs& sa,
-                                           int* meta, Origin* orig, uint8_t* tile, uint64_t* bar) {
-    const int lane = threadIdx.x & 31;
-    int lo = 0, hi = p.n - 1;           // last stream with tile_begin <= t
+__device__ __forceinline__ int find_stream(const BatchParams<CAP>& p, int t) {
+    int lo = 0, hi = p.n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (p.item[mid].tile_begin <= t) lo = mid;
         else hi = mid - 1;
     }
-    const BatchItem& it = p.item[lo];
-    const int W = it.W, H = it.H, B = it.B;
-    const int th = kBatchWarps * B;     // tile height of this stream
-    const int tiles_x = (W + kTileW - 1) / kTileW;
+    return lo;
+}
+
+// Tile origin of work item t of stream `si`.
+__device__ __forceinline__ void item_origin(const BatchItem& it, int t, int& tx0, int& ty0) {
+    const int tiles_x = (it.W + kTileW - 1) / kTileW;
     const int lt = t - it.tile_begin;
-    const int tx0 = (lt % tiles_x) * kTileW;
-    const int ty0 = (lt / tiles_x) * th;
-    const int rows = min(th, H - ty0);
+    tx0 = (lt % tiles_x) * kTileW;
+    ty0 = (lt / tiles_x) * (kBatchWarps * it.B);
+}
+
+// Stage setup (one warp): start the bulk copies of the item's pixel rows and
+// compute its affine origins.
+template <int CAP>
+__device__ __forceinline__ void stage_item(const BatchParams<CAP>& p, int t, int* meta,
+                                           Origin* orig, uint8_t* tile, uint64_t* bar) {
+    const int lane = threadIdx.x & 31;
+    const int si = find_stream(p, t);
+    const BatchItem& it = p.item[si];
+    const int W = it.W, H = it.H, B = it.B;
+    int tx0, ty0;
+    item_origin(it, t, tx0, ty0);
+    const int rows = min(kBatchWarps * B, H - ty0);
     const uint32_t wbytes = static_cast<uint32_t>(min(kTileW, W - tx0));
     if (lane == 0) {
-        const size_t N = size_t(W / B) * (H / B);
-        const int s = it.prec == DMSGM_STATE_FP16 ? 2 : 4;
-        sa.prev = state_buf(it.mem, N, s, it.parity);
-        sa.next = state_buf(it.mem, N, s, it.parity ^ 1);
-        sa.mask = it.mask;
-        sa.W = W;
-        sa.H = H;
-        sa.Gx = W / B;
-        sa.Gy = H / B;
-        sa.mask_words = (W + 31) / 32;
-        sa.first = it.first;
-        sa.affine = it.affine;
-        sa.age_max = it.age_max;
-        sa.theta_s = it.theta_s;
-        sa.theta_d = it.theta_d;
-        sa.coef = it.coef;
-        meta[0] = tx0;
-        meta[1] = ty0;
-        meta[2] = (B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
-        meta[3] = lo;
+        meta[0] = si;
         mbar_arrive_expect_tx(bar, wbytes * rows);
     }
     __syncwarp();
@@ -96,14 +91,40 @@ __device__ __forceinline__ void stage_item(const BatchParams<CAP>& p, int t, Str
         orig[lane] = affine_origin(it.coef, (tx0 + 128 * (lane & 1)) / B, ty0 / B + (lane >> 1));
 }
 
+// The per-frame arguments of a stream, built in registers from the kernel's
+// parameters (uniform constant-bank loads).
+__device__ __forceinline__ StreamArgs item_args(const BatchItem& it) {
+    StreamArgs a;
+    const int B = it.B;
+    const size_t N = size_t(it.W / B) * (it.H / B);
+    const int s = it.prec == DMSGM_STATE_FP16 ? 2 : 4;
+    a.prev = state_buf(it.mem, N, s, it.parity);
+    a.next = state_buf(it.mem, N, s, it.parity ^ 1);
+    a.mask = it.mask;
+    a.W = it.W;
+    a.H = it.H;
+    a.Gx = it.W / B;
+    a.Gy = it.H / B;
+    a.mask_words = (it.W + 31) / 32;
+    a.first = it.first;
+    a.affine = it.affine;
+    a.age_max = it.age_max;
+    a.theta_s = it.theta_s;
+    a.theta_d = it.theta_d;
+    return a;
+}
+
 template <int B, typename T>
-__device__ __forceinline__ bool run_item(const StreamArgs& sa, const int* meta, const Origin* orig,
+__device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origin* orig,
                                          const uint8_t* tile, uint64_t* bar, uint32_t parity) {
+    const StreamArgs a = item_args(it);
+    int tx0, ty0;
+    item_origin(it, t, tx0, ty0);
     Comp comp[1][kLanePx / B];
-    compensate_tile<B, T, kBatchWarps, 1>(sa, meta[0], meta[1], orig, comp);
+    compensate_tile<B, T, kBatchWarps, 1>(a, it.coef, tx0, ty0, orig, comp);
     const bool ok = mbar_wait_bounded(bar, parity, 2000000000ull);
     if (__syncthreads_or(!ok)) return false;
-    finish_tile<B, T, kBatchWarps, 1>(sa, tile, meta[0], meta[1], comp);
+    finish_tile<B, T, kBatchWarps, 1>(a, tile, tx0, ty0, comp);
     return true;
 }
 
@@ -112,8 +133,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4)
     dmsgm_batch_kernel(const __grid_constant__ BatchParams<CAP> p) {
     __shared__ __align__(128) uint8_t tile[2][kStageRows * kTileW];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ StreamArgs sa[2];
-    __shared__ int meta[2][4];
+    __shared__ int meta[2][2];
     __shared__ Origin orig[2][2 * kBatchWarps];
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -123,27 +143,29 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4)
     __syncthreads();
     int t = blockIdx.x;
     // the first tile's pixels do not depend on the previous step
-    if (t < p.total && threadIdx.x < 32) stage_item<CAP>(p, t, sa[0], meta[0], orig[0], tile[0], &bar[0]);
+    if (t < p.total && threadIdx.x < 32) stage_item<CAP>(p, t, meta[0], orig[0], tile[0], &bar[0]);
     pdl_wait();
     pdl_launch_dependents();
     for (int k = 0; t < p.total; t += gridDim.x, ++k) {
         const int st = k & 1;
-        __syncthreads();   // stage st described; stage st^1 free
+        __syncthreads();   // stage st staged; stage st^1 free
         const int tn = t + gridDim.x;
         if (tn < p.total && threadIdx.x < 32)
-            stage_item<CAP>(p, tn, sa[st ^ 1], meta[st ^ 1], orig[st ^ 1], tile[st ^ 1], &bar[st ^ 1]);
+            stage_item<CAP>(p, tn, meta[st ^ 1], orig[st ^ 1], tile[st ^ 1], &bar[st ^ 1]);
+        const int si = meta[st][0];
+        const BatchItem& it = p.item[si];
         const uint32_t par = (k >> 1) & 1;
+        const int kind = (it.B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
         bool ok;
-        switch (meta[st][2]) {
-            case 0: ok = run_item<4, float>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
-            case 1: ok = run_item<4, __half>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
-            case 2: ok = run_item<8, float>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
-            default: ok = run_item<8, __half>(sa[st], meta[st], orig[st], tile[st], &bar[st], par); break;
+        switch (kind) {
+            case 0: ok = run_item<4, float>(it, t, orig[st], tile[st], &bar[st], par); break;
+            case 1: ok = run_item<4, __half>(it, t, orig[st], tile[st], &bar[st], par); break;
+            case 2: ok = run_item<8, float>(it, t, orig[st], tile[st], &bar[st], par); break;
+            default: ok = run_item<8, __half>(it, t, orig[st], tile[st], &bar[st], par); break;
         }
         if (!ok) {
             // report on the stream's status word; let in-flight copies land
-            if (threadIdx.x == 0)
-                atomicOr(reinterpret_cast<int*>(p.item[meta[st][3]].mem), kStatusWaitTimeout);
+            if (threadIdx.x == 0) atomicOr(reinterpret_cast<int*>(it.mem), kStatusWaitTimeout);
             if (tn < p.total) mbar_wait_bounded(&bar[st ^ 1], ((k + 1) >> 1) & 1, 2000000000ull);
             return;
         }
@@ -214,9 +236,9 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
     }
     p.n = n;
     p.total = total;
-    const int dev = hs[0]->device;
-    const int full = resident_ctas<CAP>(dev);
-    int ctas = o.ctas > 0 ? std::min(o.ctas, full) : full;
+    // 0: every CTA that fits at once; otherwise as asked (CTAs never wait on
+    // one another, so more than fit at once is fine: one item each at most)
+    int ctas = o.ctas > 0 ? o.ctas : resident_ctas<CAP>(hs[0]->device);
     ctas = std::max(1, std::min(ctas, total));
     cudaError_t e = launch_t<CAP>(p, ctas, s, o.use_pdl > 0);
     if (e != cudaSuccess)

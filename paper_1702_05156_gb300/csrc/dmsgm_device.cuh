@@ -88,7 +88,6 @@ struct StreamArgs {
     int affine;         // 1: coef holds the affine block-unit form
     int age_max;
     float theta_s, theta_d;
-    Coef coef;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -311,25 +310,25 @@ __device__ __forceinline__ Origin affine_origin(const Coef& k, int bx0, int by) 
 // strip row s, half-warp h, whose first block is (tx0 + 128 h) / B.  Threads
 // 0 .. 2*strips-1 fill one entry each.
 template <int B>
-__device__ __forceinline__ void fill_origins(const StreamArgs& a, int tx0, int ty0, int strips,
-                                             Origin* orig) {
+__device__ __forceinline__ void fill_origins(const StreamArgs& a, const Coef& k, int tx0, int ty0,
+                                             int strips, Origin* orig) {
     const int t = threadIdx.x;
     if (a.affine && !a.first && t < 2 * strips)
-        orig[t] = affine_origin(a.coef, (tx0 + 128 * (t & 1)) / B, ty0 / B + (t >> 1));
+        orig[t] = affine_origin(k, (tx0 + 128 * (t & 1)) / B, ty0 / B + (t >> 1));
 }
 
 // Motion compensation of block (bx, by): area-weighted mix of the previous
 // blocks that the back-projected BxB square overlaps (Sec. 2.4).  For the
 // affine form, o is the origin of the lane's half-warp, bx0 its first block.
 template <int B, typename T>
-__device__ __forceinline__ Comp compensate(const StreamArgs& a, int bx, int by, int bx0,
-                                           const Origin& o) {
+__device__ __forceinline__ Comp compensate(const StreamArgs& a, const Coef& k, int bx, int by,
+                                           int bx0, const Origin& o) {
     Comp r;
     r.src = false;
     r.A = Model{0.f, 0.f, 0};
     r.C = r.A;
     if (a.first) return r;
-    const float* c = a.coef.c;
+    const float* c = k.c;
     float fx, fy;
     int i0, j0;
     if (a.affine) {
@@ -343,7 +342,7 @@ __device__ __forceinline__ Comp compensate(const StreamArgs& a, int bx, int by, 
         j0 = by + o.ny + int(fly);
     } else {
         DF ex, ey;
-        if (!project_general(a.coef, (bx + 0.5f) * B, (by + 0.5f) * B, ex, ey, 1.0f / B)) return r;
+        if (!project_general(k, (bx + 0.5f) * B, (by + 0.5f) * B, ex, ey, 1.0f / B)) return r;
         if (!(fabsf(ex.hi) < 1.0e7f) || !(fabsf(ey.hi) < 1.0e7f)) return r;  // NaN/inf/far: off grid
         float flx, fly;
         df_floor_frac(ex, flx, fx);
@@ -520,8 +519,8 @@ __device__ __forceinline__ void store_block(const StreamArgs& a, int k, const Co
 // blocks (B = 4) or one 8x8 block (B = 8), and writes one mask byte per row.
 // A tile is kTileW x (NW * B * RPT) pixels.
 template <int B, typename T, int NW, int RPT>
-__device__ __forceinline__ void compensate_tile(const StreamArgs& a, int tx0, int ty0,
-                                                const Origin* orig,
+__device__ __forceinline__ void compensate_tile(const StreamArgs& a, const Coef& k, int tx0,
+                                                int ty0, const Origin* orig,
                                                 Comp (&comp)[RPT][kLanePx / B]) {
     constexpr int BPL = kLanePx / B;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -536,7 +535,7 @@ __device__ __forceinline__ void compensate_tile(const StreamArgs& a, int tx0, in
         const bool in = x < a.W && by < a.Gy;
 #pragma unroll
         for (int j = 0; j < BPL; ++j) {
-            if (in) comp[r][j] = compensate<B, T>(a, bx + j, by, bx0, orig[(s << 1) | half]);
+            if (in) comp[r][j] = compensate<B, T>(a, k, bx + j, by, bx0, orig[(s << 1) | half]);
             else comp[r][j].src = false;
         }
     }

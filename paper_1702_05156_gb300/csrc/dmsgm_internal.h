@@ -72,7 +72,7 @@ namespace dmsgm {
 bool make_coef(const double H3x3[9], int B, Coef* c, int* affine);
 
 // Fill the per-frame kernel arguments of handle h (reads h->parity etc.).
-void fill_args(const dmsgm_ctx* h, const Coef& c, int affine, uint32_t* mask_dev, StreamArgs* a);
+void fill_args(const dmsgm_ctx* h, int affine, uint32_t* mask_dev, StreamArgs* a);
 
 // Advance the handle's bookkeeping after a frame has been enqueued.
 void advance(dmsgm_ctx* h);

@@ -1,0 +1,324 @@
+"""Continuous-batching server of DMSGM video streams on one GPU.
+
+Requests are frames of independent streams.  A scheduler thread admits
+streams while their device memory (model state plus frame / mask slots)
+fits a fixed HBM budget, keeps admitted streams' state resident, and at
+every step gathers at most one pending frame per stream (frames of one
+stream form a recurrence) into ONE batched kernel launch.  Frames that
+arrive while a step runs join the next step.  The host->device copies of
+step k+1 overlap the kernel of step k (separate copy stream, double-buffered
+per-stream slots); a completer thread resolves each request's future when
+its mask is back in host memory and records its latency.
+
+The engine (device memory, copies, kernel launches) is behind a small
+interface; GpuEngine is the only one in the product.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib
+from .dmsgm import Dmsgm, mask_words
+
+
+@dataclass
+class Request:
+    sid: int
+    frame: torch.Tensor            # uint8 (H, W), host (pinned for overlap)
+    H: np.ndarray                  # (3, 3) current -> previous
+    t_submit: float
+    future: Future = field(default_factory=Future)
+    t_done: float = 0.0
+
+
+@dataclass
+class StreamInfo:
+    sid: int
+    W: int
+    H: int
+    block: int
+    nbytes: int
+    queue: collections.deque = field(default_factory=collections.deque)
+    closing: bool = False
+    in_flight: int = 0
+    frames_done: int = 0
+
+
+class GpuEngine:
+    """Device side of the server: per-stream handles and double-buffered
+    frame / mask slots, one copy stream and one compute stream."""
+
+    def __init__(self, precision: str = "fp32", device: int = 0, use_pdl: bool = True):
+        self.precision = precision
+        self.device = torch.device("cuda", device)
+        self.h2d = torch.cuda.Stream(device=self.device)
+        self.compute = torch.cuda.Stream(device=self.device)
+        self.d2h = torch.cuda.Stream(device=self.device)
+        self.slots = {}
+        self.use_pdl = use_pdl
+
+    def stream_bytes(self, W, H, block) -> int:
+        prec = _lib.DMSGM_STATE_FP16 if self.precision == "fp16" else _lib.DMSGM_STATE_FP32
+        return (_lib.dmsgm_state_bytes(W, H, block, prec) + 2 * W * H
+                + 2 * H * mask_words(W) * 4)
+
+    def open(self, sid, W, H, block):
+        # state memory from the caching allocator: admitting or retiring a
+        # stream then never synchronises the device
+        prec = _lib.DMSGM_STATE_FP16 if self.precision == "fp16" else _lib.DMSGM_STATE_FP32
+        nbytes = _lib.dmsgm_state_bytes(W, H, block, prec)
+        with torch.cuda.device(self.device):
+            raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            off = (-raw.data_ptr()) % 256
+            m = Dmsgm(W, H, block, precision=self.precision, state_mem=raw[off:off + nbytes])
+            frames = torch.empty((2, H, W), dtype=torch.uint8, device=self.device)
+            masks = torch.empty((2, H, mask_words(W)), dtype=torch.int32, device=self.device)
+        self.slots[sid] = [m, frames, masks, 0, raw]
+
+    def close(self, sid):
+        # called once every step of the stream has completed
+        sl = self.slots.pop(sid)
+        sl[0].close()
+        sl.clear()
+
+    def launch(self, reqs):
+        """Copy the requests' frames in (h2d stream), run one batched step
+        (compute stream), copy the masks out (d2h stream); returns an event
+        that completes with the step.  The server keeps at most two steps in
+        flight, so a stream's slot is never reused before the step that last
+        used it has completed."""
+        entries = []
+        with torch.cuda.stream(self.h2d):
+            for r in reqs:
+                sl = self.slots[r.sid]
+                k = sl[3] & 1
+                sl[3] += 1
+                sl[1][k].copy_(r.frame, non_blocking=True)
+                r.mask_host = torch.empty((sl[2].shape[1], sl[2].shape[2]), dtype=torch.int32,
+                                          pin_memory=True)
+                entries.append((sl, k, r))
+        ev_in = torch.cuda.Event()
+        ev_in.record(self.h2d)
+        self.compute.wait_event(ev_in)
+        models = [sl[0] for sl, _, _ in entries]
+        frames = [sl[1][k] for sl, k, _ in entries]
+        masks = [sl[2][k] for sl, k, _ in entries]
+        Hs = np.stack([np.asarray(r.H, dtype=np.float64) for _, _, r in entries])
+        opts = _lib.dmsgm_batch_opts(0, 0, 1 if self.use_pdl else 0)
+        for lo in range(0, len(entries), _lib.DMSGM_MAX_BATCH):
+            hi = min(lo + _lib.DMSGM_MAX_BATCH, len(entries))
+            _lib.dmsgm_process_batch([m.handle for m in models[lo:hi]],
+                                     [f.data_ptr() for f in frames[lo:hi]], Hs[lo:hi],
+                                     [k.data_ptr() for k in masks[lo:hi]],
+                                     self.compute.cuda_stream, opts)
+        ev_k = torch.cuda.Event()
+        ev_k.record(self.compute)
+        self.d2h.wait_event(ev_k)
+        with torch.cuda.stream(self.d2h):
+            for sl, k, r in entries:
+                r.mask_host.copy_(sl[2][k], non_blocking=True)
+        ev_done = torch.cuda.Event()
+        ev_done.record(self.d2h)
+        return ev_done
+
+    @staticmethod
+    def wait(ev):
+        ev.synchronize()
+
+
+class Server:
+    """Admission by memory budget + continuous batching over an engine."""
+
+    def __init__(self, engine, hbm_budget: int, max_batch: int = 1 << 30,
+                 max_in_flight_steps: int = 2):
+        self.engine = engine
+        self.budget = int(hbm_budget)
+        self.max_batch = max_batch
+        self.max_steps = max_in_flight_steps
+        self.used = 0
+        self.waiting = collections.deque()       # streams not admitted yet
+        self.active = collections.OrderedDict()  # sid -> StreamInfo
+        self.known = {}
+        self.cv = threading.Condition()
+        self.done_q = collections.deque()
+        self.in_flight_steps = 0
+        self.running = True
+        self.steps = 0
+        self.step_sizes = []
+        self.latencies = []
+        self.pixels = 0
+        self.admit_log = []
+        self._sched = threading.Thread(target=self._schedule_loop, daemon=True)
+        self._comp = threading.Thread(target=self._complete_loop, daemon=True)
+        self._sched.start()
+        self._comp.start()
+
+    # ------------------------------------------------------------- client API
+    def open_stream(self, sid: int, W: int, H: int, block: int = 4):
+        with self.cv:
+            if sid in self.known:
+                raise ValueError(f"stream {sid} already open")
+            info = StreamInfo(sid, W, H, block, self.engine.stream_bytes(W, H, block))
+            if info.nbytes > self.budget:
+                raise ValueError(f"stream {sid} needs {info.nbytes} bytes, budget {self.budget}")
+            self.known[sid] = info
+            self.waiting.append(info)
+            self.cv.notify_all()
+
+    def submit(self, sid: int, frame: torch.Tensor, H) -> Future:
+        req = Request(sid, frame, np.asarray(H, dtype=np.float64), time.perf_counter())
+        with self.cv:
+            info = self.known.get(sid)
+            if info is None or info.closing:
+                raise ValueError(f"stream {sid} is not open")
+            info.queue.append(req)
+            self.cv.notify_all()
+        return req.future
+
+    def close_stream(self, sid: int):
+        """No more frames; the stream's memory is released once its queued
+        frames are done."""
+        with self.cv:
+            self.known[sid].closing = True
+            self.cv.notify_all()
+
+    def shutdown(self, timeout: float = 30.0):
+        t_end = time.perf_counter() + timeout
+        with self.cv:
+            while (any(s.queue or s.in_flight for s in self.known.values())
+                   and time.perf_counter() < t_end):
+                self.cv.wait(0.05)
+            self.running = False
+            self.cv.notify_all()
+        self._sched.join(timeout)
+        self._comp.join(timeout)
+
+    def stats(self) -> dict:
+        lat = np.array(self.latencies) * 1e3 if self.latencies else np.zeros(1)
+        return {"frames": len(self.latencies), "steps": self.steps,
+                "mean_batch": float(np.mean(self.step_sizes)) if self.step_sizes else 0.0,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "pixels": self.pixels}
+
+    # ------------------------------------------------------------- internals
+    def _admit(self):
+        while self.waiting:
+            info = self.waiting[0]
+            if self.used + info.nbytes > self.budget:
+                break
+            self.waiting.popleft()
+            self.engine.open(info.sid, info.W, info.H, info.block)
+            self.used += info.nbytes
+            self.active[info.sid] = info
+            self.admit_log.append((time.perf_counter(), info.sid))
+
+    def _release(self, info):
+        self.engine.close(info.sid)
+        self.used -= info.nbytes
+        del self.active[info.sid]
+        del self.known[info.sid]
+
+    def _schedule_loop(self):
+        while True:
+            with self.cv:
+                while self.running:
+                    for info in list(self.active.values()):
+                        if info.closing and not info.queue and not info.in_flight:
+                            self._release(info)
+                    self._admit()
+                    # a stream may sit in two consecutive steps: the device runs
+                    # steps in order, so its recurrence is kept
+                    ready = [s for s in self.active.values()
+                             if s.queue and s.in_flight < self.max_steps]
+                    if ready and self.in_flight_steps < self.max_steps:
+                        break
+                    self.cv.wait(0.002)
+                if not self.running:
+                    return
+                batch = []
+                for s in ready[: self.max_batch]:
+                    batch.append(s.queue.popleft())
+                    s.in_flight += 1
+                self.in_flight_steps += 1
+            ev = self.engine.launch(batch)
+            with self.cv:
+                self.steps += 1
+                self.step_sizes.append(len(batch))
+                self.done_q.append((ev, batch))
+                self.cv.notify_all()
+
+    def _complete_loop(self):
+        while True:
+            with self.cv:
+                while self.running and not self.done_q:
+                    self.cv.wait(0.01)
+                if not self.done_q:
+                    return
+                ev, batch = self.done_q.popleft()
+            self.engine.wait(ev)
+            t = time.perf_counter()
+            with self.cv:
+                for r in batch:
+                    r.t_done = t
+                    self.latencies.append(t - r.t_submit)
+                    info = self.active.get(r.sid)
+                    if info is not None:
+                        info.in_flight -= 1
+                        info.frames_done += 1
+                        self.pixels += info.W * info.H
+                self.in_flight_steps -= 1
+                self.cv.notify_all()
+            for r in batch:
+                r.future.set_result(getattr(r, "mask_host", None))
+
+
+def simulate(server: Server, n_streams: int, rate: float, fps: float, dur_lo: float,
+             dur_hi: float, resolutions, pools, seed: int = 7, block: int = 4):
+    """Drive `server` with `n_streams` streams arriving as a Poisson process
+    (rate per second), each submitting frames at `fps` for U(dur_lo, dur_hi)
+    seconds of wall time.  pools[(W, H)] = (frames pinned (K, H, W), Hs (K,3,3)):
+    a stream cycles through its resolution's pool from a random offset.
+    Returns (wall seconds, futures)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    events = []   # (time, kind, sid, payload)
+    for sid in range(n_streams):
+        t += rng.exponential(1.0 / rate)
+        W, H = resolutions[rng.integers(len(resolutions))]
+        dur = rng.uniform(dur_lo, dur_hi)
+        nfr = max(1, int(dur * fps))
+        off = int(rng.integers(len(pools[(W, H)][0])))
+        events.append((t, 0, sid, (W, H, nfr, off)))
+        for k in range(nfr):
+            events.append((t + k / fps, 1, sid, k))
+        events.append((t + (nfr - 1) / fps + 1e-6, 2, sid, None))
+    events.sort(key=lambda e: (e[0], e[1]))
+    meta = {}
+    futures = []
+    t0 = time.perf_counter()
+    for (te, kind, sid, pl) in events:
+        now = time.perf_counter() - t0
+        if te > now:
+            time.sleep(te - now)
+        if kind == 0:
+            W, H, nfr, off = pl
+            meta[sid] = (W, H, off)
+            server.open_stream(sid, W, H, block)
+        elif kind == 1:
+            W, H, off = meta[sid]
+            fr, Hs = pools[(W, H)]
+            i = (off + pl) % len(fr)
+            futures.append(server.submit(sid, fr[i], np.eye(3) if pl == 0 else Hs[i]))
+        else:
+            server.close_stream(sid)
+    for f in futures:
+        f.result(timeout=120)
+    wall = time.perf_counter() - t0
+    return wall, futures
