@@ -178,6 +178,21 @@ int dmsgm_process_batch_ex(int n, const dmsgm_t* hs, const uint8_t* const* frame
                            const double* H3x3s, uint32_t* const* masks_dev,
                            const dmsgm_batch_opts* opts, void* cuda_stream);
 
+/* One serving step: n handles, one frame each, with host buffers.  For
+ * every i, frames_host[i] (W_i*H_i bytes, pinned for overlap) is copied to
+ * the caller's device slot frames_dev[i] on h2d_stream; one batched launch
+ * (as dmsgm_process_batch_ex, opts may be NULL) runs on compute_stream after
+ * those copies; then masks_dev[i] is copied to masks_host[i] on d2h_stream
+ * after the launch.  All three streams are cudaStream_t and must differ.
+ * Returns once everything is enqueued; the masks are in host memory when
+ * d2h_stream reaches the end of this call's work.  The caller must not
+ * reuse a device slot before the step that last used it has completed. */
+int dmsgm_process_batch_host(int n, const dmsgm_t* hs, const uint8_t* const* frames_host,
+                             uint8_t* const* frames_dev, const double* H3x3s,
+                             uint32_t* const* masks_dev, uint32_t* const* masks_host,
+                             const dmsgm_batch_opts* opts, void* h2d_stream,
+                             void* compute_stream, void* d2h_stream);
+
 /* Copy the current state to / from a packed host image (layout: see
  * dmsgm_host_state_bytes).  Both synchronise the device.  set_state marks
  * the handle initialised, so the next process() compensates from it. */

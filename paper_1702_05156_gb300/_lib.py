@@ -29,7 +29,7 @@ DMSGM_MAX_BATCH = 256
 # every symbol include/dmsgm.h declares
 EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm_create_ex",
            "dmsgm_destroy", "dmsgm_process", "dmsgm_process_host", "dmsgm_process_batch",
-           "dmsgm_process_batch_ex",
+           "dmsgm_process_batch_ex", "dmsgm_process_batch_host",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
            "dmsgm_status", "dmsgm_last_error", "dmsgm_version")
 
@@ -86,6 +86,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_process_host": (I, [P, P, I, P, P, P]),
             "dmsgm_process_batch": (I, [I, P, P, P, P, P]),
             "dmsgm_process_batch_ex": (I, [I, P, P, P, P, P, P]),
+            "dmsgm_process_batch_host": (I, [I, P, P, P, P, P, P, P, P, P, P]),
             "dmsgm_get_state": (I, [P, P, S]),
             "dmsgm_set_state": (I, [P, P, S]),
             "dmsgm_reset": (I, [P]),

@@ -502,6 +502,47 @@ int dmsgm_process_batch_ex(int n, const dmsgm_t* hs, const uint8_t* const* frame
     return launch_batch(n, hs, frames_dev, Hs, masks_dev, o, static_cast<cudaStream_t>(stream));
 }
 
+int dmsgm_process_batch_host(int n, const dmsgm_t* hs, const uint8_t* const* frames_host,
+                             uint8_t* const* frames_dev, const double* Hs,
+                             uint32_t* const* masks_dev, uint32_t* const* masks_host,
+                             const dmsgm_batch_opts* opts, void* h2d, void* compute, void* d2h) {
+    clear_error();
+    if (n < 0 || n > DMSGM_MAX_BATCH) return fail(DMSGM_ERR_INVALID_ARG, "n=%d out of range", n);
+    if (n == 0) return DMSGM_OK;
+    if (!hs || !frames_host || !frames_dev || !masks_dev || !masks_host)
+        return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
+    if (h2d == compute || compute == d2h || h2d == d2h)
+        return fail(DMSGM_ERR_INVALID_ARG, "the three streams must differ");
+    for (int i = 0; i < n; ++i)
+        if (!hs[i] || !frames_host[i] || !masks_host[i])
+            return fail(DMSGM_ERR_INVALID_ARG, "NULL entry %d", i);
+    DeviceGuard g(hs[0]->device);
+    if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", hs[0]->device);
+    // per-thread events, reused across calls (a re-record only moves the
+    // point later waits refer to; waits already enqueued keep theirs)
+    static thread_local cudaEvent_t ev_in = nullptr, ev_k = nullptr;
+    if (!ev_in) {
+        DMSGM_CUDA_TRY(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+        DMSGM_CUDA_TRY(cudaEventCreateWithFlags(&ev_k, cudaEventDisableTiming));
+    }
+    cudaStream_t sh = static_cast<cudaStream_t>(h2d), sc = static_cast<cudaStream_t>(compute),
+                 sd = static_cast<cudaStream_t>(d2h);
+    for (int i = 0; i < n; ++i)
+        DMSGM_CUDA_TRY(cudaMemcpyAsync(frames_dev[i], frames_host[i], size_t(hs[i]->W) * hs[i]->H,
+                                       cudaMemcpyHostToDevice, sh));
+    DMSGM_CUDA_TRY(cudaEventRecord(ev_in, sh));
+    DMSGM_CUDA_TRY(cudaStreamWaitEvent(sc, ev_in, 0));
+    int rc = dmsgm_process_batch_ex(n, hs, frames_dev, Hs, masks_dev, opts, compute);
+    if (rc) return rc;
+    DMSGM_CUDA_TRY(cudaEventRecord(ev_k, sc));
+    DMSGM_CUDA_TRY(cudaStreamWaitEvent(sd, ev_k, 0));
+    for (int i = 0; i < n; ++i)
+        DMSGM_CUDA_TRY(cudaMemcpyAsync(masks_host[i], masks_dev[i],
+                                       size_t(hs[i]->H) * ((hs[i]->W + 31) / 32) * 4,
+                                       cudaMemcpyDeviceToHost, sd));
+    return DMSGM_OK;
+}
+
 int dmsgm_get_state(dmsgm_t h, void* host_buf, size_t bytes) {
     clear_error();
     if (!h || !host_buf) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");

@@ -80,50 +80,55 @@ class GpuEngine:
             m = Dmsgm(W, H, block, precision=self.precision, state_mem=raw[off:off + nbytes])
             frames = torch.empty((2, H, W), dtype=torch.uint8, device=self.device)
             masks = torch.empty((2, H, mask_words(W)), dtype=torch.int32, device=self.device)
-        self.slots[sid] = [m, frames, masks, 0, raw]
+        # pinned result ring: a request's mask stays valid for RING more of
+        # the stream's frames
+        ring = torch.empty((self.RING, H, mask_words(W)), dtype=torch.int32, pin_memory=True)
+        self.slots[sid] = {"m": m, "frames": frames, "masks": masks, "n": 0, "raw": raw,
+                           "ring": ring, "handle": m.handle.value,
+                           "fptr": [frames[0].data_ptr(), frames[1].data_ptr()],
+                           "mptr": [masks[0].data_ptr(), masks[1].data_ptr()]}
+
+    RING = 8
 
     def close(self, sid):
         # called once every step of the stream has completed
         sl = self.slots.pop(sid)
-        sl[0].close()
+        sl["m"].close()
         sl.clear()
 
     def launch(self, reqs):
-        """Copy the requests' frames in (h2d stream), run one batched step
-        (compute stream), copy the masks out (d2h stream); returns an event
-        that completes with the step.  The server keeps at most two steps in
-        flight, so a stream's slot is never reused before the step that last
-        used it has completed."""
-        entries = []
-        with torch.cuda.stream(self.h2d):
-            for r in reqs:
+        """One native call enqueues the frames' host->device copies (h2d
+        stream), one batched step (compute stream) and the masks' copies
+        back (d2h stream); returns an event that completes with the step.
+        The server keeps at most two steps in flight, so a stream's device
+        slot is never reused before the step that last used it completed."""
+        n = len(reqs)
+        for lo in range(0, n, _lib.DMSGM_MAX_BATCH):
+            part = reqs[lo:lo + _lib.DMSGM_MAX_BATCH]
+            k = len(part)
+            hs = np.empty(k, np.uint64)
+            fh = np.empty(k, np.uint64)
+            fd = np.empty(k, np.uint64)
+            md = np.empty(k, np.uint64)
+            mh = np.empty(k, np.uint64)
+            Hs = np.empty((k, 9), np.float64)
+            for i, r in enumerate(part):
                 sl = self.slots[r.sid]
-                k = sl[3] & 1
-                sl[3] += 1
-                sl[1][k].copy_(r.frame, non_blocking=True)
-                r.mask_host = torch.empty((sl[2].shape[1], sl[2].shape[2]), dtype=torch.int32,
-                                          pin_memory=True)
-                entries.append((sl, k, r))
-        ev_in = torch.cuda.Event()
-        ev_in.record(self.h2d)
-        self.compute.wait_event(ev_in)
-        models = [sl[0] for sl, _, _ in entries]
-        frames = [sl[1][k] for sl, k, _ in entries]
-        masks = [sl[2][k] for sl, k, _ in entries]
-        Hs = np.stack([np.asarray(r.H, dtype=np.float64) for _, _, r in entries])
-        opts = _lib.dmsgm_batch_opts(0, 0, 1 if self.use_pdl else 0)
-        for lo in range(0, len(entries), _lib.DMSGM_MAX_BATCH):
-            hi = min(lo + _lib.DMSGM_MAX_BATCH, len(entries))
-            _lib.dmsgm_process_batch([m.handle for m in models[lo:hi]],
-                                     [f.data_ptr() for f in frames[lo:hi]], Hs[lo:hi],
-                                     [k.data_ptr() for k in masks[lo:hi]],
-                                     self.compute.cuda_stream, opts)
-        ev_k = torch.cuda.Event()
-        ev_k.record(self.compute)
-        self.d2h.wait_event(ev_k)
-        with torch.cuda.stream(self.d2h):
-            for sl, k, r in entries:
-                r.mask_host.copy_(sl[2][k], non_blocking=True)
+                j = sl["n"]
+                sl["n"] = j + 1
+                hs[i] = sl["handle"]
+                fh[i] = r.frame.data_ptr()
+                fd[i] = sl["fptr"][j & 1]
+                md[i] = sl["mptr"][j & 1]
+                r.mask_host = sl["ring"][j % self.RING]
+                mh[i] = r.mask_host.data_ptr()
+                Hs[i] = r.H.reshape(9)
+            opts = _lib.dmsgm_batch_opts(0, 0, 1 if self.use_pdl else 0)
+            rc = _lib.load_library().dmsgm_process_batch_host(
+                k, hs.ctypes.data, fh.ctypes.data, fd.ctypes.data, Hs.ctypes.data,
+                md.ctypes.data, mh.ctypes.data, _lib.ctypes.byref(opts), self.h2d.cuda_stream,
+                self.compute.cuda_stream, self.d2h.cuda_stream)
+            _lib._check(rc)
         ev_done = torch.cuda.Event()
         ev_done.record(self.d2h)
         return ev_done
