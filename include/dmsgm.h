@@ -84,6 +84,10 @@ typedef struct {
                            the frame must not be written by the kernel that
                            immediately precedes the call on the stream;
                            0 (default): plain stream order                    */
+    int seq_tile_rows;  /* tile height of dmsgm_process_seq: 8, 16, 32 or 64
+                           times the block size / 2 (32, 64, 128, 256 rows
+                           for block 4; 64, 128, 256 for block 8); 0 = the
+                           built-in choice                                    */
 } dmsgm_opts;
 
 /* Read-only description of a handle. */
@@ -99,10 +103,11 @@ typedef struct {
     int device;                  /* CUDA device of the handle                */
 } dmsgm_info;
 
-/* Device bytes a handle needs for its state: a 256-byte control block plus
- * two buffers of three arrays (Gx*Gy*2*s, Gx*Gy*2*s and Gx*Gy*2 bytes; s = 4
- * for FP32, 2 for FP16), every array 256-byte aligned.  Returns 0 for
- * invalid sizes. */
+/* Device bytes a handle needs for its state: a 256-byte control block, one
+ * int per 256 x (8*block) pixel tile (the multi-frame kernel's progress
+ * counters), and two buffers of three arrays (Gx*Gy*2*s, Gx*Gy*2*s and
+ * Gx*Gy*2 bytes; s = 4 for FP32, 2 for FP16), every part 256-byte aligned.
+ * Returns 0 for invalid sizes. */
 size_t dmsgm_state_bytes(int width, int height, int block, int precision);
 
 /* Bytes of the packed host image used by dmsgm_get_state/dmsgm_set_state:
@@ -139,6 +144,20 @@ int dmsgm_destroy(dmsgm_t h);
  * it when k is even (or the graph is replayed once). */
 int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9],
                   uint32_t* mask_dev, void* cuda_stream);
+
+/* n consecutive frames of the handle's stream from device memory in
+ * persistent launches (at most 256 frames each): frames_dev holds frame t at
+ * t*W*H (16-byte aligned), masks_dev receives frame t's mask at
+ * t*H*ceil(W/32) words, H3x3s holds n host homographies.  Each CTA owns one
+ * tile for the whole launch and starts frame t+1 as soon as the tiles within
+ * the dependency radius of the frames' homographies have published frame t
+ * (per-tile progress counters in the handle's memory, Sec. 2.4 fixes that
+ * radius); the launch is cooperative and every wait is bounded (a timeout
+ * sets the status word).  Results equal n calls of dmsgm_process.  If the
+ * tiles cannot all be resident at once, the call falls back to one launch
+ * per frame.  Asynchronous on cuda_stream. */
+int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double* H3x3s,
+                      uint32_t* masks_dev, void* cuda_stream);
 
 /* n frames from HOST memory (frames_host: n*W*H bytes, pinned for overlap)
  * into host masks (masks_host: n*H*ceil(W/32) words), pipelined: host->device

@@ -28,7 +28,7 @@ DMSGM_MAX_BATCH = 256
 
 # every symbol include/dmsgm.h declares
 EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm_create_ex",
-           "dmsgm_destroy", "dmsgm_process", "dmsgm_process_host", "dmsgm_process_batch",
+           "dmsgm_destroy", "dmsgm_process", "dmsgm_process_seq", "dmsgm_process_host", "dmsgm_process_batch",
            "dmsgm_process_batch_ex", "dmsgm_process_batch_host",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
            "dmsgm_status", "dmsgm_last_error", "dmsgm_version")
@@ -37,7 +37,7 @@ EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm
 class dmsgm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("state_mem", ctypes.c_void_p),
                 ("state_bytes", ctypes.c_size_t), ("tile_rows", ctypes.c_int),
-                ("use_pdl", ctypes.c_int)]
+                ("use_pdl", ctypes.c_int), ("seq_tile_rows", ctypes.c_int)]
 
 
 class dmsgm_batch_opts(ctypes.Structure):
@@ -83,6 +83,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_create_ex": (I, [I, I, I, F, F, I, P, P]),
             "dmsgm_destroy": (I, [P]),
             "dmsgm_process": (I, [P, P, P, P, P]),
+            "dmsgm_process_seq": (I, [P, P, I, P, P, P]),
             "dmsgm_process_host": (I, [P, P, I, P, P, P]),
             "dmsgm_process_batch": (I, [I, P, P, P, P, P]),
             "dmsgm_process_batch_ex": (I, [I, P, P, P, P, P, P]),
@@ -144,6 +145,12 @@ def dmsgm_destroy(h):
 def dmsgm_process(h, frame_ptr: int, H, mask_ptr: int, stream: int = 0):
     Hm = _h9(H)
     _check(load_library().dmsgm_process(h, frame_ptr, Hm.ctypes.data, mask_ptr, stream))
+
+
+def dmsgm_process_seq(h, frames_ptr: int, n: int, Hs, masks_ptr: int, stream: int = 0):
+    Hm = _h9(Hs)
+    assert Hm.size == 9 * n
+    _check(load_library().dmsgm_process_seq(h, frames_ptr, n, Hm.ctypes.data, masks_ptr, stream))
 
 
 def dmsgm_process_host(h, frames_ptr: int, n: int, Hs, masks_ptr: int, stream: int = 0):

@@ -116,26 +116,14 @@ static size_t buf_bytes(size_t N, int prec) {
 }
 
 static void carve(dmsgm_ctx* h) {
-    const size_t N = size_t(h->Gx) * h->Gy;
     const int s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
     h->status_dev = reinterpret_cast<int*>(h->mem);
-    for (int b = 0; b < 2; ++b) h->buf[b] = state_buf(static_cast<char*>(h->mem), N, s, b);
+    h->flags_dev = reinterpret_cast<int*>(static_cast<char*>(h->mem) + 256);
+    for (int b = 0; b < 2; ++b)
+        h->buf[b] = state_buf(static_cast<char*>(h->mem), h->W, h->H, h->B, s, b);
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -314,7 +302,7 @@ const char* dmsgm_version(void) { return "dmsgm-gb300 0.1 (sm_103a)"; }
 size_t dmsgm_state_bytes(int W, int H, int B, int prec) {
     if (!valid_dims(W, H, B) || (prec != DMSGM_STATE_FP32 && prec != DMSGM_STATE_FP16)) return 0;
     const size_t N = size_t(W / B) * (H / B);
-    return 256 + 2 * buf_bytes(N, prec);
+    return 256 + seq_flags_bytes(W, H, B) + 2 * buf_bytes(N, prec);
 }
 
 size_t dmsgm_host_state_bytes(int W, int H, int B, int prec) {
@@ -364,6 +352,12 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     h->device = dev;
     h->tile_rows = tile_rows;
     h->use_pdl = opts.use_pdl > 0 ? 1 : 0;
+    if (opts.seq_tile_rows && !(opts.seq_tile_rows % (8 * B) == 0 && opts.seq_tile_rows <= 256 &&
+                                ((opts.seq_tile_rows / (8 * B)) & (opts.seq_tile_rows / (8 * B) - 1)) == 0)) {
+        delete h;
+        return fail(DMSGM_ERR_INVALID_ARG, "seq_tile_rows %d invalid", opts.seq_tile_rows);
+    }
+    h->seq_tile_rows = opts.seq_tile_rows;
     h->state_bytes = need;
     if (opts.state_mem) {
         h->mem = opts.state_mem;
@@ -422,6 +416,33 @@ int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9], uin
     DeviceGuard g(h->device);
     if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", h->device);
     return process_one(h, frame_dev, H3x3, mask_dev, static_cast<cudaStream_t>(stream));
+}
+
+int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double* Hs,
+                      uint32_t* masks_dev, void* stream) {
+    clear_error();
+    if (!h || n < 0 || (n > 0 && (!frames_dev || !Hs || !masks_dev)))
+        return fail(DMSGM_ERR_INVALID_ARG, "invalid argument");
+    if (reinterpret_cast<uintptr_t>(frames_dev) % 16)
+        return fail(DMSGM_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(masks_dev) % 4)
+        return fail(DMSGM_ERR_INVALID_ARG, "masks must be 4-byte aligned");
+    for (long i = 0; i < 9L * n; ++i)
+        if (!std::isfinite(Hs[i])) return fail(DMSGM_ERR_INVALID_ARG, "homography %ld is not finite", i / 9);
+    if (n == 0) return DMSGM_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = launch_seq(h, frames_dev, n, Hs, masks_dev, s, h->flags_dev);
+    if (rc != DMSGM_ERR_UNSUPPORTED) return rc;
+    // the tiles do not fit the GPU at once: one launch per frame instead
+    clear_error();
+    const size_t fbytes = size_t(h->W) * h->H, mwords = size_t(h->H) * ((h->W + 31) / 32);
+    for (int t = 0; t < n; ++t) {
+        rc = process_one(h, frames_dev + t * fbytes, Hs + 9 * size_t(t), masks_dev + t * mwords, s);
+        if (rc) return rc;
+    }
+    return DMSGM_OK;
 }
 
 int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n, const double* Hs,

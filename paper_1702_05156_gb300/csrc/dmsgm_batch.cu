@@ -96,10 +96,9 @@ __device__ __forceinline__ void stage_item(const BatchParams<CAP>& p, int t, int
 __device__ __forceinline__ StreamArgs item_args(const BatchItem& it) {
     StreamArgs a;
     const int B = it.B;
-    const size_t N = size_t(it.W / B) * (it.H / B);
     const int s = it.prec == DMSGM_STATE_FP16 ? 2 : 4;
-    a.prev = state_buf(it.mem, N, s, it.parity);
-    a.next = state_buf(it.mem, N, s, it.parity ^ 1);
+    a.prev = state_buf(it.mem, it.W, it.H, B, s, it.parity);
+    a.next = state_buf(it.mem, it.W, it.H, B, s, it.parity ^ 1);
     a.mask = it.mask;
     a.W = it.W;
     a.H = it.H;

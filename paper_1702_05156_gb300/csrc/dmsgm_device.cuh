@@ -63,14 +63,24 @@ struct StateBuf {
 };
 
 // Device-memory layout of a handle: a 256-byte control block (status word
-// first), then the two buffers, every array 256-byte aligned.  s is the size
-// of one stored value (4: FP32, 2: FP16).
+// first), the per-tile progress counters of the multi-frame kernel (one int
+// per 256 x 8B tile, the smallest tile it uses), then the two state buffers;
+// every array 256-byte aligned.  s is the size of one stored value (4: FP32,
+// 2: FP16).
 __host__ __device__ __forceinline__ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 __host__ __device__ __forceinline__ size_t state_buf_bytes(size_t N, int s) {
     return 2 * align256(N * 2 * s) + align256(N * 2);
 }
-__host__ __device__ __forceinline__ StateBuf state_buf(char* mem, size_t N, int s, int which) {
-    char* p = mem + 256 + size_t(which) * state_buf_bytes(N, s);
+__host__ __device__ __forceinline__ size_t seq_flag_count(int W, int H, int B) {
+    return size_t((W + kTileW - 1) / kTileW) * size_t((H + 8 * B - 1) / (8 * B));
+}
+__host__ __device__ __forceinline__ size_t seq_flags_bytes(int W, int H, int B) {
+    return align256(4 * seq_flag_count(W, H, B));
+}
+__host__ __device__ __forceinline__ StateBuf state_buf(char* mem, int W, int H, int B, int s,
+                                                      int which) {
+    const size_t N = size_t(W / B) * (H / B);
+    char* p = mem + 256 + seq_flags_bytes(W, H, B) + size_t(which) * state_buf_bytes(N, s);
     StateBuf b;
     b.mu = p; p += align256(N * 2 * s);
     b.var = p; p += align256(N * 2 * s);
@@ -152,6 +162,27 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* t
         : "memory");
 }
 
+// 3-D tiled TMA load (x, y, z) -- z selects the frame of a sequence.
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* tmap, int x, int y,
+                                            int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Progress counters of the multi-frame kernel: release store / acquire load
+// at GPU scope.
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // 1-D bulk copy global -> shared (TMA engine, no tensor map).  Both addresses
 // 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_load_1d(void* smem_dst, const void* gsrc, uint32_t bytes,
@@ -177,12 +208,22 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 
 
 // ------------------------------------------------------------------ state I/O
-// Both models of a block, as (A, C) float pairs.
+// Both models of a block, as (A, C) float pairs.  COH = false: read-only
+// cache path (the previous buffer is not written during the launch);
+// COH = true: L2 only, for state that other CTAs of the same launch write.
+template <bool COH>
 __device__ __forceinline__ float2 ld2(const void* base, int k, float*) {
-    return __ldg(static_cast<const float2*>(base) + k);
+    const float2* p = static_cast<const float2*>(base) + k;
+    return COH ? __ldcg(p) : __ldg(p);
 }
+template <bool COH>
 __device__ __forceinline__ float2 ld2(const void* base, int k, __half*) {
-    return __half22float2(__ldg(static_cast<const __half2*>(base) + k));
+    const __half2* p = static_cast<const __half2*>(base) + k;
+    return __half22float2(COH ? __ldcg(p) : __ldg(p));
+}
+template <bool COH>
+__device__ __forceinline__ uint32_t ld_age(const uint16_t* base, int k) {
+    return COH ? __ldcg(base + k) : __ldg(base + k);
 }
 __device__ __forceinline__ void st2(void* base, int k, float2 v, float*) {
     static_cast<float2*>(base)[k] = v;
@@ -320,7 +361,7 @@ __device__ __forceinline__ void fill_origins(const StreamArgs& a, const Coef& k,
 // Motion compensation of block (bx, by): area-weighted mix of the previous
 // blocks that the back-projected BxB square overlaps (Sec. 2.4).  For the
 // affine form, o is the origin of the lane's half-warp, bx0 its first block.
-template <int B, typename T>
+template <int B, typename T, bool COH = false>
 __device__ __forceinline__ Comp compensate(const StreamArgs& a, const Coef& k, int bx, int by,
                                            int bx0, const Origin& o) {
     Comp r;
@@ -357,18 +398,18 @@ __device__ __forceinline__ Comp compensate(const StreamArgs& a, const Coef& k, i
         // interior: all four overlapped blocks exist and the weights sum to 1
         const int k0 = j0 * a.Gx + i0, k1 = k0 + a.Gx;
         const float2 W00 = dup2(w00), W10 = dup2(w10), W01 = dup2(w01), W11 = dup2(w11);
-        mu = __fmul2_rn(W00, ld2(a.prev.mu, k0, (T*)nullptr));
-        mu = __ffma2_rn(W10, ld2(a.prev.mu, k0 + 1, (T*)nullptr), mu);
-        mu = __ffma2_rn(W01, ld2(a.prev.mu, k1, (T*)nullptr), mu);
-        mu = __ffma2_rn(W11, ld2(a.prev.mu, k1 + 1, (T*)nullptr), mu);
-        var = __fmul2_rn(W00, ld2(a.prev.var, k0, (T*)nullptr));
-        var = __ffma2_rn(W10, ld2(a.prev.var, k0 + 1, (T*)nullptr), var);
-        var = __ffma2_rn(W01, ld2(a.prev.var, k1, (T*)nullptr), var);
-        var = __ffma2_rn(W11, ld2(a.prev.var, k1 + 1, (T*)nullptr), var);
-        ag = __fmul2_rn(W00, age2f(__ldg(a.prev.age + k0)));
-        ag = __ffma2_rn(W10, age2f(__ldg(a.prev.age + k0 + 1)), ag);
-        ag = __ffma2_rn(W01, age2f(__ldg(a.prev.age + k1)), ag);
-        ag = __ffma2_rn(W11, age2f(__ldg(a.prev.age + k1 + 1)), ag);
+        mu = __fmul2_rn(W00, ld2<COH>(a.prev.mu, k0, (T*)nullptr));
+        mu = __ffma2_rn(W10, ld2<COH>(a.prev.mu, k0 + 1, (T*)nullptr), mu);
+        mu = __ffma2_rn(W01, ld2<COH>(a.prev.mu, k1, (T*)nullptr), mu);
+        mu = __ffma2_rn(W11, ld2<COH>(a.prev.mu, k1 + 1, (T*)nullptr), mu);
+        var = __fmul2_rn(W00, ld2<COH>(a.prev.var, k0, (T*)nullptr));
+        var = __ffma2_rn(W10, ld2<COH>(a.prev.var, k0 + 1, (T*)nullptr), var);
+        var = __ffma2_rn(W01, ld2<COH>(a.prev.var, k1, (T*)nullptr), var);
+        var = __ffma2_rn(W11, ld2<COH>(a.prev.var, k1 + 1, (T*)nullptr), var);
+        ag = __fmul2_rn(W00, age2f(ld_age<COH>(a.prev.age, k0)));
+        ag = __ffma2_rn(W10, age2f(ld_age<COH>(a.prev.age, k0 + 1)), ag);
+        ag = __ffma2_rn(W01, age2f(ld_age<COH>(a.prev.age, k1)), ag);
+        ag = __ffma2_rn(W11, age2f(ld_age<COH>(a.prev.age, k1 + 1)), ag);
     } else {
         // border: drop out-of-grid blocks and renormalise the rest
         float wsum = 0.f;
@@ -381,9 +422,9 @@ __device__ __forceinline__ Comp compensate(const StreamArgs& a, const Coef& k, i
                 const int k = j * a.Gx + i;
                 const float2 W = dup2(w);
                 wsum += w;
-                mu = __ffma2_rn(W, ld2(a.prev.mu, k, (T*)nullptr), mu);
-                var = __ffma2_rn(W, ld2(a.prev.var, k, (T*)nullptr), var);
-                ag = __ffma2_rn(W, age2f(__ldg(a.prev.age + k)), ag);
+                mu = __ffma2_rn(W, ld2<COH>(a.prev.mu, k, (T*)nullptr), mu);
+                var = __ffma2_rn(W, ld2<COH>(a.prev.var, k, (T*)nullptr), var);
+                ag = __ffma2_rn(W, age2f(ld_age<COH>(a.prev.age, k)), ag);
             }
         }
         if (!(wsum >= kMinWeight)) return r;

@@ -28,6 +28,20 @@ void clear_error();
 
 constexpr int kTmapCache = 16;
 
+// Makes `dev` current for a scope and restores the previous device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 struct HostStage {              // device staging of dmsgm_process_host
     int chunk = 0;              // frames per chunk
     int slots = 0;
@@ -48,10 +62,12 @@ struct dmsgm_ctx {
     int device;
     int tile_rows;
     int use_pdl;
+    int seq_tile_rows;           // 0: automatic
     void* mem;                   // control block + two state buffers
     bool owns_mem;
     size_t state_bytes;
     int* status_dev;             // device status word (inside mem)
+    int* flags_dev;              // per-tile progress counters of the multi-frame kernel
     dmsgm::StateBuf buf[2];
     int parity;                  // buffer holding the current state
     bool initialized;
@@ -61,6 +77,11 @@ struct dmsgm_ctx {
         CUtensorMap map;
     } tmap[dmsgm::kTmapCache];
     int tmap_next;
+    struct {                     // 3-D tensor map of the last frame sequence
+        const void* ptr;
+        int frames, rows;
+        CUtensorMap map;
+    } seqmap;
     dmsgm::HostStage stage;
 };
 
@@ -76,6 +97,15 @@ void fill_args(const dmsgm_ctx* h, int affine, uint32_t* mask_dev, StreamArgs* a
 
 // Advance the handle's bookkeeping after a frame has been enqueued.
 void advance(dmsgm_ctx* h);
+
+// The driver's cuTensorMapEncodeTiled (NULL if unavailable).
+#include <cudaTypedefs.h>
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
+bool valid_dims_ex(int W, int H, int B);
+
+// T frames of one handle in persistent cooperative launches (dmsgm_seq.cu).
+int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* H3x3s,
+               uint32_t* masks_dev, cudaStream_t stream, int* flags);
 
 // Launch the batched persistent kernel (dmsgm_batch.cu).
 int launch_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,

@@ -49,12 +49,14 @@ class Dmsgm:
 
     def __init__(self, width: int, height: int, block: int = 4, theta_s: float = 2.0,
                  theta_d: float = 4.0, age_max: int = 30, precision: str = "fp32",
-                 tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None):
+                 tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None,
+                 seq_tile_rows: int = 0):
         prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
         opts = _lib.dmsgm_opts()
         opts.precision = prec
         opts.tile_rows = tile_rows
         opts.use_pdl = 1 if use_pdl else 0
+        opts.seq_tile_rows = seq_tile_rows
         self._state_mem = state_mem
         if state_mem is not None:
             opts.state_mem = state_mem.data_ptr()
@@ -77,6 +79,21 @@ class Dmsgm:
         assert tuple(mask.shape) == (self.height, mask_words(self.width))
         _lib.dmsgm_process(self._h, frame.data_ptr(), H, mask.data_ptr(), _stream_handle(stream))
         return mask
+
+    def process_seq(self, frames: torch.Tensor, Hs, masks: torch.Tensor | None = None,
+                    stream=None):
+        """Enqueue n consecutive frames (uint8 (n, H, W) on the GPU) in
+        persistent multi-frame launches; returns the masks (n, H, ceil(W/32))."""
+        assert frames.dtype == torch.uint8 and frames.is_cuda and frames.is_contiguous()
+        n = frames.shape[0]
+        assert tuple(frames.shape[1:]) == (self.height, self.width)
+        if masks is None:
+            masks = new_mask(self.height, self.width, frames.device, n=n)
+        assert masks.is_cuda and masks.dtype == torch.int32 and masks.is_contiguous()
+        assert tuple(masks.shape) == (n, self.height, mask_words(self.width))
+        _lib.dmsgm_process_seq(self._h, frames.data_ptr(), n, np.asarray(Hs), masks.data_ptr(),
+                               _stream_handle(stream))
+        return masks
 
     def process_host(self, frames: torch.Tensor, Hs, masks: torch.Tensor | None = None,
                      stream=None):

@@ -204,6 +204,10 @@ class Server:
             self.cv.notify_all()
         self._sched.join(timeout)
         self._comp.join(timeout)
+        with self.cv:   # retire whatever is still resident
+            for info in list(self.active.values()):
+                if not info.in_flight:
+                    self._release(info)
 
     def stats(self) -> dict:
         lat = np.array(self.latencies) * 1e3 if self.latencies else np.zeros(1)
