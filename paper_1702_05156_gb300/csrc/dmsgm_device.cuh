@@ -590,6 +590,7 @@ __device__ __forceinline__ void finish_tile(const StreamArgs& a, const uint8_t* 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
     const bool xin = x < a.W;
+    const bool xpad = !xin && x < a.mask_words * 32;         // padding bits of the last word
     const int bx = x / B;
     const size_t mrow = size_t(a.mask_words) * 4;            // mask bytes per row
     uint8_t* mcol = reinterpret_cast<uint8_t*>(a.mask) + (x >> 3);
@@ -627,6 +628,9 @@ __device__ __forceinline__ void finish_tile(const StreamArgs& a, const uint8_t* 
                 for (int i = 0; i < B; ++i)
                     m[i * mrow] = uint8_t((fg_nibble_hi(lw[i], tl) >> 28) |
                                           (fg_nibble_hi(rw[i], tr) >> 24));
+            } else if (xpad) {
+#pragma unroll
+                for (int i = 0; i < B; ++i) m[i * mrow] = 0;
             }
         } else {
             uint32_t all[2 * B];
@@ -646,6 +650,9 @@ __device__ __forceinline__ void finish_tile(const StreamArgs& a, const uint8_t* 
                 for (int i = 0; i < B; ++i)
                     m[i * mrow] = uint8_t((fg_nibble_hi(lw[i], t) >> 28) |
                                           (fg_nibble_hi(rw[i], t) >> 24));
+            } else if (xpad) {
+#pragma unroll
+                for (int i = 0; i < B; ++i) m[i * mrow] = 0;
             }
         }
     }

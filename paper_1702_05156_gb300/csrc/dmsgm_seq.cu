@@ -190,8 +190,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
             __threadfence();
             st_release_gpu(p.flags + blockIdx.x, k + 1);
         }
-        // off the critical path: the frame's mask bytes
-        if (xin) {
+        // off the critical path: the frame's mask bytes (lanes past the
+        // frame's right edge but inside the last mask word write zeros)
+        if (x < p.mask_words * 32) {
             const size_t mrow = size_t(p.mask_words) * 4;
             uint8_t* mcol = reinterpret_cast<uint8_t*>(a.mask) + (x >> 3);
 #pragma unroll
@@ -203,8 +204,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
                 const Thresh tr = BPL == 1 ? tl : bg_interval(muA[r][BPL - 1], thr[r][BPL - 1]);
 #pragma unroll
                 for (int i = 0; i < B; ++i)
-                    m[i * mrow] = uint8_t((fg_nibble_hi(lw[r][i], tl) >> 28) |
-                                          (fg_nibble_hi(rw[r][i], tr) >> 24));
+                    m[i * mrow] = xin ? uint8_t((fg_nibble_hi(lw[r][i], tl) >> 28) |
+                                                (fg_nibble_hi(rw[r][i], tr) >> 24))
+                                      : uint8_t(0);
             }
         }
         __syncthreads();   // this stage's pixels and origins are consumed
@@ -447,3 +449,4 @@ int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* Hs,
 }
 
 }  // namespace dmsgm
+

@@ -304,3 +304,24 @@ def test_batch_teacher_forced_vs_oracle(lib):
             rep.add(compare_step(p, m.get_state(), lib.unpack_mask(o, w), fr[t].cpu().numpy(),
                                  Hs[t], block=b))
     rep.assert_ok()
+
+
+@pytest.mark.parametrize("block", [4, 8])
+def test_mask_padding_bits_are_zero(lib, block):
+    """W % 32 == 16: the last word of each mask row has 16 bits past the
+    frame; every kernel writes them as 0 even into a dirty buffer."""
+    W, H = 48, 32
+    frames, Hs = make_stream(StreamSpec(W, H, 3, seed=12), device="cuda")
+    for mode in ("single", "batch", "seq"):
+        m = lib.Dmsgm(W, H, block)
+        masks = torch.full((3, H, lib.mask_words(W)), -1, dtype=torch.int32, device="cuda")
+        if mode == "seq":
+            m.process_seq(frames, Hs, masks)
+        for t in range(3):
+            if mode == "single":
+                m.process(frames[t], Hs[t], masks[t])
+            elif mode == "batch":
+                lib.process_batch([m], [frames[t]], Hs[t][None], [masks[t]])
+        w = masks.cpu().numpy().astype(np.uint32)
+        assert (w[..., -1] >> 16 == 0).all(), mode
+        m.close()
