@@ -159,6 +159,32 @@ int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9],
 int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double* H3x3s,
                       uint32_t* masks_dev, void* cuda_stream);
 
+/* dmsgm_process_seq for callers that may not allocate device memory -- for
+ * example an application whose device memory is all handed out by its own
+ * allocator or a fixed real-time budget, or one that must avoid the
+ * device-wide synchronisation a cudaMalloc or cudaFree can cause.  The paper
+ * has no counterpart; this is an integration convenience.
+ *
+ * Nothing is allocated and no handle is needed.  The caller passes the state
+ * memory (state_dev: state_bytes >= dmsgm_state_bytes(width, height, block,
+ * precision), 256-byte aligned, laid out as a handle's memory; its first
+ * word is the device status word, set nonzero if a wait runs out, never
+ * cleared here; its counter region is not used), *parity (0 or 1: the
+ * buffer holding the state, updated on return), first (1: start every block
+ * afresh, as after create/reset), and the frames, homographies and masks as
+ * in dmsgm_process_seq.  The multi-frame kernel's progress counters live in
+ * one static array of 4096 ints in the library: a frame needing more tiles
+ * is rejected with DMSGM_ERR_INVALID_ARG, and one whose tiles cannot all be
+ * resident on the GPU with DMSGM_ERR_UNSUPPORTED.  Every call on a device
+ * shares that array (each launch clears the counters it uses), so calls
+ * whose work may overlap on the GPU race: keep them on one stream.  The
+ * first call on a device looks up the array's device address; make that
+ * first call before any stream capture. */
+int dmsgm_process_seq_noalloc(int width, int height, int block, int precision, float theta_s,
+                              float theta_d, int age_max, void* state_dev, size_t state_bytes,
+                              int* parity, int first, const uint8_t* frames_dev, int n,
+                              const double* H3x3s, uint32_t* masks_dev, void* cuda_stream);
+
 /* n frames from HOST memory (frames_host: n*W*H bytes, pinned for overlap)
  * into host masks (masks_host: n*H*ceil(W/32) words), pipelined: host->device
  * copies, kernels and device->host copies of consecutive chunks overlap on

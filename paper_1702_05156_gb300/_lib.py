@@ -28,7 +28,8 @@ DMSGM_MAX_BATCH = 256
 
 # every symbol include/dmsgm.h declares
 EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm_create_ex",
-           "dmsgm_destroy", "dmsgm_process", "dmsgm_process_seq", "dmsgm_process_host", "dmsgm_process_batch",
+           "dmsgm_destroy", "dmsgm_process", "dmsgm_process_seq", "dmsgm_process_seq_noalloc",
+           "dmsgm_process_host", "dmsgm_process_batch",
            "dmsgm_process_batch_ex", "dmsgm_process_batch_host",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
            "dmsgm_status", "dmsgm_last_error", "dmsgm_version")
@@ -84,6 +85,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_destroy": (I, [P]),
             "dmsgm_process": (I, [P, P, P, P, P]),
             "dmsgm_process_seq": (I, [P, P, I, P, P, P]),
+            "dmsgm_process_seq_noalloc": (I, [I, I, I, I, F, F, I, P, S, P, I, P, I, P, P, P]),
             "dmsgm_process_host": (I, [P, P, I, P, P, P]),
             "dmsgm_process_batch": (I, [I, P, P, P, P, P]),
             "dmsgm_process_batch_ex": (I, [I, P, P, P, P, P, P]),
@@ -151,6 +153,17 @@ def dmsgm_process_seq(h, frames_ptr: int, n: int, Hs, masks_ptr: int, stream: in
     Hm = _h9(Hs)
     assert Hm.size == 9 * n
     _check(load_library().dmsgm_process_seq(h, frames_ptr, n, Hm.ctypes.data, masks_ptr, stream))
+
+
+def dmsgm_process_seq_noalloc(width, height, block, precision, theta_s, theta_d, age_max,
+                              state_ptr: int, state_bytes: int, parity: ctypes.c_int, first: int,
+                              frames_ptr: int, n: int, Hs, masks_ptr: int, stream: int = 0):
+    """No-allocation multi-frame call; `parity` (a ctypes.c_int) is updated."""
+    Hm = _h9(Hs)
+    assert Hm.size == 9 * n
+    _check(load_library().dmsgm_process_seq_noalloc(
+        width, height, block, precision, theta_s, theta_d, age_max, state_ptr, state_bytes,
+        ctypes.byref(parity), first, frames_ptr, n, Hm.ctypes.data, masks_ptr, stream))
 
 
 def dmsgm_process_host(h, frames_ptr: int, n: int, Hs, masks_ptr: int, stream: int = 0):

@@ -450,3 +450,97 @@ int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* Hs,
 
 }  // namespace dmsgm
 
+// ============================================================ no allocation
+// dmsgm_process_seq_noalloc: the multi-frame kernel for callers that may not
+// allocate device memory.  Its only scratch -- the per-tile progress
+// counters -- lives in this file-scope array instead of a handle's memory.
+// Every GPU that loads the library holds the array (16 KB) until the process
+// exits, and every call on a device shares it.
+namespace dmsgm {
+
+constexpr int kNoAllocCounters = 4096;
+static __device__ __align__(256) int g_noalloc_counters[kNoAllocCounters];
+
+// Device address of the array on the current device.  Host code must not
+// hand the symbol itself to a kernel (on the host it only stands in for the
+// device object), so the address is looked up once per device, with that
+// device current, and cached.
+static int noalloc_counters(int device, int** out) {
+    static std::mutex mu;
+    static int* addr[64] = {nullptr};
+    std::lock_guard<std::mutex> g(mu);
+    if (device < 0 || device >= 64) return fail(DMSGM_ERR_UNSUPPORTED, "device %d out of range", device);
+    if (!addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_counters);
+        if (e != cudaSuccess || !p)
+            return fail(DMSGM_ERR_CUDA, "cudaGetSymbolAddress of the counter array failed: %s",
+                        cudaGetErrorString(e));
+        addr[device] = static_cast<int*>(p);
+    }
+    *out = addr[device];
+    return DMSGM_OK;
+}
+
+}  // namespace dmsgm
+
+using namespace dmsgm;
+
+extern "C" int dmsgm_process_seq_noalloc(int W, int H, int B, int precision, float theta_s,
+                                         float theta_d, int age_max, void* state_dev,
+                                         size_t state_bytes, int* parity, int first,
+                                         const uint8_t* frames_dev, int n, const double* Hs,
+                                         uint32_t* masks_dev, void* stream) {
+    clear_error();
+    const size_t need = dmsgm_state_bytes(W, H, B, precision);
+    if (!need) return fail(DMSGM_ERR_INVALID_ARG, "invalid size %dx%d block %d or precision %d", W, H, B, precision);
+    if (!(std::isfinite(theta_s) && theta_s > 0) || !(std::isfinite(theta_d) && theta_d > 0))
+        return fail(DMSGM_ERR_INVALID_ARG, "theta_s and theta_d must be finite and > 0");
+    if (age_max < 1 || age_max > 255) return fail(DMSGM_ERR_INVALID_ARG, "age_max must be in [1, 255]");
+    if (!state_dev || state_bytes < need)
+        return fail(DMSGM_ERR_INVALID_ARG, "state_dev must hold %zu bytes", need);
+    if (reinterpret_cast<uintptr_t>(state_dev) % 256)
+        return fail(DMSGM_ERR_INVALID_ARG, "state_dev must be 256-byte aligned");
+    if (!parity || (*parity != 0 && *parity != 1)) return fail(DMSGM_ERR_INVALID_ARG, "parity must point to 0 or 1");
+    if (n < 0 || (n > 0 && (!frames_dev || !Hs || !masks_dev))) return fail(DMSGM_ERR_INVALID_ARG, "invalid argument");
+    if (reinterpret_cast<uintptr_t>(frames_dev) % 16 || reinterpret_cast<uintptr_t>(masks_dev) % 4)
+        return fail(DMSGM_ERR_INVALID_ARG, "frames must be 16-byte and masks 4-byte aligned");
+    for (long i = 0; i < 9L * n; ++i)
+        if (!std::isfinite(Hs[i])) return fail(DMSGM_ERR_INVALID_ARG, "homography %ld is not finite", i / 9);
+    if (n == 0) return DMSGM_OK;
+    int dev = 0;
+    DMSGM_CUDA_TRY(cudaGetDevice(&dev));
+    int* counters = nullptr;
+    int rc = noalloc_counters(dev, &counters);
+    if (rc) return rc;
+    // a handle description on the stack over the caller's memory
+    dmsgm_ctx h{};
+    h.W = W; h.H = H; h.B = B; h.Gx = W / B; h.Gy = H / B;
+    h.prec = precision; h.age_max = age_max;
+    h.theta_s = theta_s; h.theta_d = theta_d;
+    h.device = dev;
+    h.tile_rows = 32;
+    h.mem = state_dev;
+    h.owns_mem = false;
+    h.state_bytes = need;
+    const int s = precision == DMSGM_STATE_FP16 ? 2 : 4;
+    h.status_dev = static_cast<int*>(state_dev);
+    for (int b = 0; b < 2; ++b) h.buf[b] = state_buf(static_cast<char*>(state_dev), W, H, B, s, b);
+    h.parity = *parity;
+    h.initialized = !first;
+    // the counters this launch needs must fit the array
+    int sms = 0;
+    DMSGM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const SeqShape sh = pick_shape(&h, sms);
+    if (!sh.nw)
+        return fail(DMSGM_ERR_UNSUPPORTED, "the %dx%d frame's tiles cannot all be resident on this GPU", W, H);
+    const int th = sh.nw * sh.rpt * B;
+    const long tiles = long((W + kTileW - 1) / kTileW) * ((H + th - 1) / th);
+    if (tiles > kNoAllocCounters)
+        return fail(DMSGM_ERR_INVALID_ARG, "the frame needs %ld progress counters, the array holds %d",
+                    tiles, kNoAllocCounters);
+    rc = launch_seq(&h, frames_dev, n, Hs, masks_dev, static_cast<cudaStream_t>(stream), counters);
+    if (rc) return rc;
+    *parity = h.parity;
+    return DMSGM_OK;
+}
