@@ -135,6 +135,23 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(vals, device):
+    """Element-wise maximum of per-rank timings over all ranks (identity on
+    one rank).  The job is as slow as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_rate(pixels_per_rank, world, ms):
+    """Whole-job Mpix/s: every rank processes `pixels_per_rank` in at most
+    `ms` milliseconds (weak scaling: one stream replica per GPU)."""
+    return world * pixels_per_rank / (ms / 1e3) / 1e6
+
+
 def cpu_oracle_rate(frames_np, Hs, block, budget_s=12.0, min_frames=3):
     """Time the FP64 oracle, one thread, frame by frame from the first frame
     until the time budget is spent; returns (Mpix/s, frames, seconds)."""
@@ -251,13 +268,10 @@ def run_gpu(args):
         sampler.stop()
 
     # aggregate: max time over ranks
-    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = reduce_max([ms, e2e_ms], dev)
     npx = W * H
-    value = world * args.steps * T * npx / (ms / 1e3) / 1e6
-    e2e_val = world * e2e_steps * T * npx / (e2e_ms / 1e3) / 1e6
+    value = job_rate(args.steps * T * npx, world, ms)
+    e2e_val = job_rate(e2e_steps * T * npx, world, e2e_ms)
 
     if rank == 0:
         peak, peak_kind = load_peaks()

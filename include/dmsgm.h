@@ -254,6 +254,13 @@ int dmsgm_get_info(dmsgm_t h, dmsgm_info* out);
  * then cleared). */
 int dmsgm_status(dmsgm_t h);
 
+/* Diagnostic of the device-side failure path: enqueue a kernel that waits on
+ * a barrier nothing ever completes, bounded by timeout_ns (at most 1 s).
+ * The wait gives up, the kernel sets the handle's status word and returns,
+ * and the context stays usable; dmsgm_status() then reports
+ * DMSGM_ERR_TIMEOUT.  The paper has no counterpart. */
+int dmsgm_selftest_wait(dmsgm_t h, unsigned long long timeout_ns, void* cuda_stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dmsgm_last_error(void);
 

@@ -32,7 +32,7 @@ EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm
            "dmsgm_process_host", "dmsgm_process_batch",
            "dmsgm_process_batch_ex", "dmsgm_process_batch_host",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
-           "dmsgm_status", "dmsgm_last_error", "dmsgm_version")
+           "dmsgm_status", "dmsgm_selftest_wait", "dmsgm_last_error", "dmsgm_version")
 
 
 class dmsgm_opts(ctypes.Structure):
@@ -95,6 +95,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_reset": (I, [P]),
             "dmsgm_get_info": (I, [P, P]),
             "dmsgm_status": (I, [P]),
+            "dmsgm_selftest_wait": (I, [P, ctypes.c_ulonglong, P]),
             "dmsgm_last_error": (ctypes.c_char_p, []),
             "dmsgm_version": (ctypes.c_char_p, []),
         }
@@ -210,6 +211,10 @@ def dmsgm_get_info(h) -> dmsgm_info:
 
 def dmsgm_status(h) -> int:
     return load_library().dmsgm_status(h)
+
+
+def dmsgm_selftest_wait(h, timeout_ns: int, stream: int = 0):
+    _check(load_library().dmsgm_selftest_wait(h, timeout_ns, stream))
 
 
 def dmsgm_last_error() -> str:

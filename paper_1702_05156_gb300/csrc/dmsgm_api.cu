@@ -70,6 +70,19 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
     finish_tile<B, T, NW, RPT>(a, tile, tx0, ty0, comp);
 }
 
+// Diagnostic kernel: waits on a barrier that nothing completes, so the
+// bounded wait must give up after timeout_ns and report it.
+__global__ void dmsgm_selftest_wait_kernel(int* status, unsigned long long timeout_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, timeout_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+}
+
 template <int B, typename T, int NW, int RPT>
 static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, const Coef& k,
                                  int* status, cudaStream_t s, bool pdl) {
@@ -561,6 +574,18 @@ int dmsgm_process_batch_host(int n, const dmsgm_t* hs, const uint8_t* const* fra
         DMSGM_CUDA_TRY(cudaMemcpyAsync(masks_host[i], masks_dev[i],
                                        size_t(hs[i]->H) * ((hs[i]->W + 31) / 32) * 4,
                                        cudaMemcpyDeviceToHost, sd));
+    return DMSGM_OK;
+}
+
+int dmsgm_selftest_wait(dmsgm_t h, unsigned long long timeout_ns, void* stream) {
+    clear_error();
+    if (!h) return fail(DMSGM_ERR_INVALID_ARG, "NULL handle");
+    if (timeout_ns > 1000000000ull) return fail(DMSGM_ERR_INVALID_ARG, "timeout above 1 s");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", h->device);
+    dmsgm_selftest_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(h->status_dev,
+                                                                              timeout_ns);
+    DMSGM_CUDA_TRY(cudaGetLastError());
     return DMSGM_OK;
 }
 

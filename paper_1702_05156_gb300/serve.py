@@ -159,6 +159,7 @@ class Server:
         self.step_sizes = []
         self.latencies = []
         self.pixels = 0
+        self.failed = 0
         self.admit_log = []
         self._sched = threading.Thread(target=self._schedule_loop, daemon=True)
         self._comp = threading.Thread(target=self._complete_loop, daemon=True)
@@ -211,7 +212,7 @@ class Server:
 
     def stats(self) -> dict:
         lat = np.array(self.latencies) * 1e3 if self.latencies else np.zeros(1)
-        return {"frames": len(self.latencies), "steps": self.steps,
+        return {"frames": len(self.latencies), "steps": self.steps, "failed": self.failed,
                 "mean_batch": float(np.mean(self.step_sizes)) if self.step_sizes else 0.0,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "max_ms": float(lat.max()), "pixels": self.pixels}
@@ -256,7 +257,20 @@ class Server:
                     batch.append(s.queue.popleft())
                     s.in_flight += 1
                 self.in_flight_steps += 1
-            ev = self.engine.launch(batch)
+            try:
+                ev = self.engine.launch(batch)
+            except Exception as e:   # the step failed: its requests fail, the loop goes on
+                with self.cv:
+                    for r in batch:
+                        info = self.active.get(r.sid)
+                        if info is not None:
+                            info.in_flight -= 1
+                    self.in_flight_steps -= 1
+                    self.failed += len(batch)
+                    self.cv.notify_all()
+                for r in batch:
+                    r.future.set_exception(e)
+                continue
             with self.cv:
                 self.steps += 1
                 self.step_sizes.append(len(batch))
@@ -271,7 +285,11 @@ class Server:
                 if not self.done_q:
                     return
                 ev, batch = self.done_q.popleft()
-            self.engine.wait(ev)
+            err = None
+            try:
+                self.engine.wait(ev)
+            except Exception as e:
+                err = e
             t = time.perf_counter()
             with self.cv:
                 for r in batch:
@@ -285,7 +303,10 @@ class Server:
                 self.in_flight_steps -= 1
                 self.cv.notify_all()
             for r in batch:
-                r.future.set_result(getattr(r, "mask_host", None))
+                if err is None:
+                    r.future.set_result(getattr(r, "mask_host", None))
+                else:
+                    r.future.set_exception(err)
 
 
 def simulate(server: Server, n_streams: int, rate: float, fps: float, dur_lo: float,

@@ -325,3 +325,20 @@ def test_mask_padding_bits_are_zero(lib, block):
         w = masks.cpu().numpy().astype(np.uint32)
         assert (w[..., -1] >> 16 == 0).all(), mode
         m.close()
+
+
+def test_device_wait_timeout_reports_and_context_survives(lib):
+    """Failure detection without a fault: a kernel waits on a barrier nothing
+    completes, gives up after 2 ms, sets the status word; dmsgm_status
+    reports DMSGM_ERR_TIMEOUT once, then the handle works normally."""
+    from paper_1702_05156_gb300 import _lib
+    m = lib.Dmsgm(64, 32, 4)
+    assert m.status() == 0
+    _lib.dmsgm_selftest_wait(m.handle, 2_000_000, 0)
+    assert m.status() == _lib.DMSGM_ERR_TIMEOUT
+    assert "gave up" in _lib.dmsgm_last_error()
+    assert m.status() == 0
+    frame = torch.full((32, 64), 9, dtype=torch.uint8, device="cuda")
+    mask = m.process(frame, np.eye(3))
+    torch.cuda.synchronize()
+    assert int(mask.abs().sum()) == 0 and m.status() == 0

@@ -131,3 +131,38 @@ def test_rejects_oversized_and_unknown_streams():
     with pytest.raises(ValueError):
         srv.submit(7, _frame(0), np.eye(3))
     srv.shutdown()
+
+
+class FailingEngine(FakeEngine):
+    """Fails the launch of every step that contains stream 1's third frame."""
+
+    def launch(self, reqs):
+        if any(r.sid == 1 and int(r.frame[0, 0]) == 2 for r in reqs):
+            raise RuntimeError("injected launch failure")
+        return super().launch(reqs)
+
+
+def test_a_failed_step_fails_its_requests_and_the_loop_goes_on():
+    """Failure injected on the host: the step's futures carry the error,
+    other steps still complete, and the server shuts down cleanly."""
+    eng = FailingEngine()
+    srv = Server(eng, hbm_budget=10_000)
+    futs = {}
+    for sid in (0, 1):
+        srv.open_stream(sid, 8, 8)
+    for k in range(6):
+        for sid in (0, 1):
+            futs[(sid, k)] = srv.submit(sid, _frame(k), np.eye(3))
+    for sid in (0, 1):
+        srv.close_stream(sid)
+    failed = []
+    for key, f in futs.items():
+        try:
+            f.result(timeout=10)
+        except RuntimeError as e:
+            assert "injected" in str(e)
+            failed.append(key)
+    srv.shutdown()
+    assert (1, 2) in failed
+    assert len(failed) < len(futs)
+    assert srv.stats()["failed"] == len(failed)
