@@ -55,11 +55,6 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
     }
     fill_origins<B>(a, k, tx0, ty0, STRIPS, orig);
     __syncthreads();
-    // The pixels do not depend on the previous frame's kernel; the state does.
-    pdl_wait();
-    pdl_launch_dependents();
-    Comp comp[RPT][kLanePx / B];
-    compensate_tile<B, T, NW, RPT>(a, k, tx0, ty0, orig, comp);
     const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
     if (__syncthreads_or(!ok)) {
         // report, give the copy one more bounded chance to land, and leave
@@ -67,7 +62,20 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
         mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
         return;
     }
-    finish_tile<B, T, NW, RPT>(a, tile, tx0, ty0, comp);
+    // The pixels, their block statistics and the back-projections do not
+    // depend on the previous frame's kernel, so they run before its end;
+    // the state does.
+    constexpr int BPL = kLanePx / B;
+    const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
+    Stats st[RPT][BPL];
+    Proj pj[RPT][BPL];
+    tile_stats<B, NW, RPT>(tile, xin, st);
+    tile_project<B, NW, RPT>(a, k, tx0, ty0, orig, pj);
+    pdl_wait();
+    pdl_launch_dependents();
+    float muA[RPT][BPL], thr[RPT][BPL];
+    tile_update<B, T, NW, RPT, false>(a, tx0, ty0, pj, st, muA, thr);
+    tile_mask<B, NW, RPT>(a, tile, tx0, ty0, muA, thr);
 }
 
 // Diagnostic kernel: waits on a barrier that nothing completes, so the

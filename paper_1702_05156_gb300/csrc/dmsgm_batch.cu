@@ -116,14 +116,20 @@ __device__ __forceinline__ StreamArgs item_args(const BatchItem& it) {
 template <int B, typename T>
 __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origin* orig,
                                          const uint8_t* tile, uint64_t* bar, uint32_t parity) {
+    constexpr int BPL = kLanePx / B;
     const StreamArgs a = item_args(it);
     int tx0, ty0;
     item_origin(it, t, tx0, ty0);
-    Comp comp[1][kLanePx / B];
-    compensate_tile<B, T, kBatchWarps, 1>(a, it.coef, tx0, ty0, orig, comp);
+    Proj pj[1][BPL];
+    tile_project<B, kBatchWarps, 1>(a, it.coef, tx0, ty0, orig, pj);
     const bool ok = mbar_wait_bounded(bar, parity, 2000000000ull);
     if (__syncthreads_or(!ok)) return false;
-    finish_tile<B, T, kBatchWarps, 1>(a, tile, tx0, ty0, comp);
+    const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
+    Stats st[1][BPL];
+    tile_stats<B, kBatchWarps, 1>(tile, xin, st);
+    float muA[1][BPL], thr[1][BPL];
+    tile_update<B, T, kBatchWarps, 1, false>(a, tx0, ty0, pj, st, muA, thr);
+    tile_mask<B, kBatchWarps, 1>(a, tile, tx0, ty0, muA, thr);
     return true;
 }
 

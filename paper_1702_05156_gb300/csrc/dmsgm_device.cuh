@@ -26,6 +26,11 @@ constexpr float kVarFloor = 0.1f;    // appendix code: max(var, .1) in the match
 constexpr float kMinWeight = 1e-3f;  // in-grid weight below this: no source
 constexpr int kTileW = 256;          // pixels per tile row (one TMA box row)
 constexpr int kLanePx = 8;           // pixel columns a lane owns (one mask byte per row)
+// Adding kMagic = 1.5 * 2^23 to a float x with |x| < 2^22 leaves an integer
+// in the low mantissa bits (the ulp there is 1); with a directed rounding
+// mode the sum is kMagic + floor(x) or kMagic + ceil(x), exactly.
+constexpr float kMagic = 12582912.0f;
+constexpr int kMagicBits = 0x4B400000;
 
 // device status word bits
 constexpr int kStatusWaitTimeout = 1;
@@ -121,14 +126,19 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// One bounded wait for phase `parity`: the thread is suspended until the
+// phase completes or about kSuspendHintNs have passed (a hint to the
+// hardware), so a waiting warp issues almost nothing.
+constexpr uint32_t kSuspendHintNs = 20000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     return ok != 0;
 }
@@ -145,9 +155,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
                                                   uint64_t timeout_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
-    for (uint32_t it = 0;; ++it) {
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 63u && global_timer_ns() - t0 > timeout_ns) return false;
+        if (global_timer_ns() - t0 > timeout_ns) return false;
     }
 }
 
@@ -242,9 +252,11 @@ __device__ __forceinline__ float2 age2f(uint32_t a) {
 
 __device__ __forceinline__ float2 dup2(float w) { return make_float2(w, w); }
 
+// One Gaussian model.  The age is kept as a float holding a small exact
+// integer (0 .. 255), so the learning rate and the comparisons need no
+// int <-> float conversions.
 struct Model {
-    float mu, var;
-    int age;
+    float mu, var, age;
 };
 
 // Compensated (tilde) models of one block.  src == false: no source.
@@ -358,118 +370,173 @@ __device__ __forceinline__ void fill_origins(const StreamArgs& a, const Coef& k,
         orig[t] = affine_origin(k, (tx0 + 128 * (t & 1)) / B, ty0 / B + (t >> 1));
 }
 
-// Motion compensation of block (bx, by): area-weighted mix of the previous
-// blocks that the back-projected BxB square overlaps (Sec. 2.4).  For the
-// affine form, o is the origin of the lane's half-warp, bx0 its first block.
-template <int B, typename T, bool COH = false>
-__device__ __forceinline__ Comp compensate(const StreamArgs& a, const Coef& k, int bx, int by,
-                                           int bx0, const Origin& o) {
-    Comp r;
-    r.src = false;
-    r.A = Model{0.f, 0.f, 0};
-    r.C = r.A;
-    if (a.first) return r;
-    const float* c = k.c;
-    float fx, fy;
+// Back-projection of one block (Sec. 2.4): the previous-grid block (i0, j0)
+// at the top left of the overlapped 2x2 group and the fractional position
+// (fx, fy) of the back-projected square inside it.  ok == false: no source
+// (first frame, or the general form put the centre behind the camera or
+// far off the grid).  Depends on the homography only, not on the state.
+struct Proj {
     int i0, j0;
+    float fx, fy;
+    bool ok;
+};
+
+__device__ __forceinline__ Proj no_proj() { return Proj{0, 0, 0.f, 0.f, false}; }
+
+// For the affine form, o is the origin of the lane's half-warp and bx0 its
+// first block.
+template <int B>
+__device__ __forceinline__ Proj project(const StreamArgs& a, const Coef& k, int bx, int by,
+                                        int bx0, const Origin& o) {
+    if (a.first) return no_proj();
+    const float* c = k.c;
+    Proj p;
     if (a.affine) {
-        const float dl = float(bx - bx0);
-        const float wx = fmaf(c[1], dl, fmaf(c[0], dl, o.fx));
-        const float wy = fmaf(c[7], dl, fmaf(c[6], dl, o.fy));
-        const float flx = floorf(wx), fly = floorf(wy);
-        fx = wx - flx;
-        fy = wy - fly;
-        i0 = bx + o.nx + int(flx);
-        j0 = by + o.ny + int(fly);
+        // (x, y) side by side: w = o.f + (c_hi + c_lo) * dl, its floor and fraction
+        const float2 dl = dup2(float(bx - bx0));
+        const float2 w = __ffma2_rn(make_float2(c[1], c[7]), dl,
+                                    __ffma2_rn(make_float2(c[0], c[6]), dl, make_float2(o.fx, o.fy)));
+        const float2 m = __fadd2_rd(w, dup2(kMagic));                  // kMagic + floor(w)
+        const float2 f = __ffma2_rn(__fadd2_rn(m, dup2(-kMagic)), dup2(-1.0f), w);
+        p.fx = f.x;
+        p.fy = f.y;
+        p.i0 = bx + o.nx + (__float_as_int(m.x) - kMagicBits);
+        p.j0 = by + o.ny + (__float_as_int(m.y) - kMagicBits);
     } else {
         DF ex, ey;
-        if (!project_general(k, (bx + 0.5f) * B, (by + 0.5f) * B, ex, ey, 1.0f / B)) return r;
-        if (!(fabsf(ex.hi) < 1.0e7f) || !(fabsf(ey.hi) < 1.0e7f)) return r;  // NaN/inf/far: off grid
+        if (!project_general(k, (bx + 0.5f) * B, (by + 0.5f) * B, ex, ey, 1.0f / B))
+            return no_proj();
+        if (!(fabsf(ex.hi) < 1.0e7f) || !(fabsf(ey.hi) < 1.0e7f)) return no_proj();
         float flx, fly;
-        df_floor_frac(ex, flx, fx);
-        df_floor_frac(ey, fly, fy);
-        i0 = bx + int(flx);
-        j0 = by + int(fly);
+        df_floor_frac(ex, flx, p.fx);
+        df_floor_frac(ey, fly, p.fy);
+        p.i0 = bx + int(flx);
+        p.j0 = by + int(fly);
     }
-    const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy);
-    const float w01 = (1.f - fx) * fy, w11 = fx * fy;
-    float2 mu, var, ag;
-    if (i0 >= 0 && i0 + 1 < a.Gx && j0 >= 0 && j0 + 1 < a.Gy) {
-        // interior: all four overlapped blocks exist and the weights sum to 1
-        const int k0 = j0 * a.Gx + i0, k1 = k0 + a.Gx;
-        const float2 W00 = dup2(w00), W10 = dup2(w10), W01 = dup2(w01), W11 = dup2(w11);
-        mu = __fmul2_rn(W00, ld2<COH>(a.prev.mu, k0, (T*)nullptr));
-        mu = __ffma2_rn(W10, ld2<COH>(a.prev.mu, k0 + 1, (T*)nullptr), mu);
-        mu = __ffma2_rn(W01, ld2<COH>(a.prev.mu, k1, (T*)nullptr), mu);
-        mu = __ffma2_rn(W11, ld2<COH>(a.prev.mu, k1 + 1, (T*)nullptr), mu);
-        var = __fmul2_rn(W00, ld2<COH>(a.prev.var, k0, (T*)nullptr));
-        var = __ffma2_rn(W10, ld2<COH>(a.prev.var, k0 + 1, (T*)nullptr), var);
-        var = __ffma2_rn(W01, ld2<COH>(a.prev.var, k1, (T*)nullptr), var);
-        var = __ffma2_rn(W11, ld2<COH>(a.prev.var, k1 + 1, (T*)nullptr), var);
-        ag = __fmul2_rn(W00, age2f(ld_age<COH>(a.prev.age, k0)));
-        ag = __ffma2_rn(W10, age2f(ld_age<COH>(a.prev.age, k0 + 1)), ag);
-        ag = __ffma2_rn(W01, age2f(ld_age<COH>(a.prev.age, k1)), ag);
-        ag = __ffma2_rn(W11, age2f(ld_age<COH>(a.prev.age, k1 + 1)), ag);
-    } else {
-        // border: drop out-of-grid blocks and renormalise the rest
-        float wsum = 0.f;
-        mu = var = ag = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + (q & 1), j = j0 + (q >> 1);
-            const float w = q == 0 ? w00 : q == 1 ? w10 : q == 2 ? w01 : w11;
-            if (i >= 0 && i < a.Gx && j >= 0 && j < a.Gy) {
-                const int k = j * a.Gx + i;
-                const float2 W = dup2(w);
-                wsum += w;
-                mu = __ffma2_rn(W, ld2<COH>(a.prev.mu, k, (T*)nullptr), mu);
-                var = __ffma2_rn(W, ld2<COH>(a.prev.var, k, (T*)nullptr), var);
-                ag = __ffma2_rn(W, age2f(ld_age<COH>(a.prev.age, k)), ag);
-            }
-        }
-        if (!(wsum >= kMinWeight)) return r;
-        mu = make_float2(mu.x / wsum, mu.y / wsum);
-        var = make_float2(var.x / wsum, var.y / wsum);
-        ag = make_float2(ag.x / wsum, ag.y / wsum);
-    }
+    p.ok = true;
+    return p;
+}
+
+// Bilinear overlap areas of the four blocks (i0, j0), (i0+1, j0), (i0, j0+1),
+// (i0+1, j0+1).
+struct Weights {
+    float w00, w10, w01, w11;
+};
+__device__ __forceinline__ Weights overlap(const Proj& p) {
+    const float2 g = __ffma2_rn(make_float2(p.fx, p.fy), dup2(-1.0f), dup2(1.0f));   // 1 - f
+    const float2 top = __fmul2_rn(make_float2(g.x, p.fx), dup2(g.y));
+    const float2 bot = __fmul2_rn(make_float2(g.x, p.fx), dup2(p.fy));
+    return Weights{top.x, top.y, bot.x, bot.y};
+}
+
+// Compensated models from the mixed (A, C) pairs; the mixed age is rounded
+// half up: floor(age + 0.5).
+__device__ __forceinline__ Comp comp_from(float2 mu, float2 var, float2 ag) {
+    Comp r;
     r.src = true;
     r.A.mu = mu.x;
     r.C.mu = mu.y;
     r.A.var = var.x;
     r.C.var = var.y;
-    r.A.age = __float2int_rd(ag.x + 0.5f);   // mixed age, rounded half up
-    r.C.age = __float2int_rd(ag.y + 0.5f);
+    const float2 age = __fadd2_rn(__fadd2_rd(__fadd2_rn(ag, dup2(0.5f)), dup2(kMagic)), dup2(-kMagic));
+    r.A.age = age.x;
+    r.C.age = age.y;
     return r;
 }
 
+__device__ __forceinline__ Comp no_source() {
+    Comp r;
+    r.src = false;
+    r.A = Model{0.f, 0.f, 0.f};
+    r.C = r.A;
+    return r;
+}
+
+// Area-weighted mix of the four overlapped blocks whose top-left one is k0
+// (all four on the grid; the weights sum to 1).
+template <typename T, bool COH>
+__device__ __forceinline__ Comp mix4(const StreamArgs& a, int k0, const Weights& w) {
+    const int k1 = k0 + a.Gx;
+    const float2 W00 = dup2(w.w00), W10 = dup2(w.w10), W01 = dup2(w.w01), W11 = dup2(w.w11);
+    float2 mu, var, ag;
+    mu = __fmul2_rn(W00, ld2<COH>(a.prev.mu, k0, (T*)nullptr));
+    mu = __ffma2_rn(W10, ld2<COH>(a.prev.mu, k0 + 1, (T*)nullptr), mu);
+    mu = __ffma2_rn(W01, ld2<COH>(a.prev.mu, k1, (T*)nullptr), mu);
+    mu = __ffma2_rn(W11, ld2<COH>(a.prev.mu, k1 + 1, (T*)nullptr), mu);
+    var = __fmul2_rn(W00, ld2<COH>(a.prev.var, k0, (T*)nullptr));
+    var = __ffma2_rn(W10, ld2<COH>(a.prev.var, k0 + 1, (T*)nullptr), var);
+    var = __ffma2_rn(W01, ld2<COH>(a.prev.var, k1, (T*)nullptr), var);
+    var = __ffma2_rn(W11, ld2<COH>(a.prev.var, k1 + 1, (T*)nullptr), var);
+    ag = __fmul2_rn(W00, age2f(ld_age<COH>(a.prev.age, k0)));
+    ag = __ffma2_rn(W10, age2f(ld_age<COH>(a.prev.age, k0 + 1)), ag);
+    ag = __ffma2_rn(W01, age2f(ld_age<COH>(a.prev.age, k1)), ag);
+    ag = __ffma2_rn(W11, age2f(ld_age<COH>(a.prev.age, k1 + 1)), ag);
+    return comp_from(mu, var, ag);
+}
+
+// Motion compensation of one block (Sec. 2.4) from its projection: the
+// area-weighted mix of the previous blocks its back-projected square
+// overlaps.  At the grid border the blocks off the grid are dropped and the
+// remaining weights renormalised.
+template <typename T, bool COH>
+__device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p) {
+    if (!p.ok) return no_source();
+    const Weights w = overlap(p);
+    if (p.i0 >= 0 && p.i0 + 1 < a.Gx && p.j0 >= 0 && p.j0 + 1 < a.Gy)
+        return mix4<T, COH>(a, p.j0 * a.Gx + p.i0, w);
+    float wsum = 0.f;
+    float2 mu = make_float2(0.f, 0.f), var = mu, ag = mu;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = p.i0 + (q & 1), j = p.j0 + (q >> 1);
+        const float wq = q == 0 ? w.w00 : q == 1 ? w.w10 : q == 2 ? w.w01 : w.w11;
+        if (i >= 0 && i < a.Gx && j >= 0 && j < a.Gy) {
+            const int kk = j * a.Gx + i;
+            const float2 W = dup2(wq);
+            wsum += wq;
+            mu = __ffma2_rn(W, ld2<COH>(a.prev.mu, kk, (T*)nullptr), mu);
+            var = __ffma2_rn(W, ld2<COH>(a.prev.var, kk, (T*)nullptr), var);
+            ag = __ffma2_rn(W, age2f(ld_age<COH>(a.prev.age, kk)), ag);
+        }
+    }
+    if (!(wsum >= kMinWeight)) return no_source();
+    return comp_from(make_float2(mu.x / wsum, mu.y / wsum), make_float2(var.x / wsum, var.y / wsum),
+                     make_float2(ag.x / wsum, ag.y / wsum));
+}
+
 // ------------------------------------------------------------------ (b)
+// Block statistics: mean M_i and the extremes that give V_i (Sec. 2.2).
+struct Stats {
+    float M, mn, mx;
+};
+
 // Sec. 2.2 update with learning rate 1/(age~ + 1), written incrementally:
 // mu = mu~ + (M - mu~)/(age~+1), V = max_j (mu - I_j)^2 = max((mu-min)^2,
 // (max-mu)^2), var = var~ + (V - var~)/(age~+1), age + 1 below the cap.
-__device__ __forceinline__ void sgm_update(Model& m, float M, float mn, float mx, int age_max) {
-    const float rcp = __fdividef(1.0f, static_cast<float>(m.age) + 1.0f);   // ~2 ulp
-    const float mu = fmaf(M - m.mu, rcp, m.mu);
-    const float d0 = mu - mn, d1 = mx - mu;
+__device__ __forceinline__ void sgm_update(Model& m, const Stats& st, float age_max) {
+    const float rcp = __fdividef(1.0f, m.age + 1.0f);   // ~2 ulp
+    const float mu = fmaf(st.M - m.mu, rcp, m.mu);
+    const float d0 = mu - st.mn, d1 = st.mx - mu;
     const float V = fmaxf(d0 * d0, d1 * d1);
     m.var = fmaf(V - m.var, rcp, m.var);
     m.mu = mu;
-    m.age = (m.age < age_max) ? m.age + 1 : m.age;
+    m.age = (m.age < age_max) ? m.age + 1.0f : m.age;
 }
 
 // Match -> update -> reset -> swap (Sec. 2.3) from the compensated models.
-__device__ __forceinline__ void dual_mode_step(Comp& c, float M, float mn, float mx,
-                                               const StreamArgs& a) {
-    const Model reset{M, kVarInit, 1};
+__device__ __forceinline__ void dual_mode_step(Comp& c, const Stats& st, const StreamArgs& a) {
+    const Model reset{st.M, kVarInit, 1.0f};
     if (!c.src) {
         c.A = reset;
         c.C = reset;
         return;
     }
-    const float dA = M - c.A.mu, dC = M - c.C.mu;
+    const float age_max = static_cast<float>(a.age_max);
+    const float dA = st.M - c.A.mu, dC = st.M - c.C.mu;
     if (dA * dA < a.theta_s * fmaxf(c.A.var, kVarFloor)) {
-        sgm_update(c.A, M, mn, mx, a.age_max);
+        sgm_update(c.A, st, age_max);
     } else if (dC * dC < a.theta_s * fmaxf(c.C.var, kVarFloor)) {
-        sgm_update(c.C, M, mn, mx, a.age_max);
+        sgm_update(c.C, st, age_max);
     } else {
         c.C = reset;
     }
@@ -483,7 +550,7 @@ __device__ __forceinline__ void dual_mode_step(Comp& c, float M, float mn, float
 // 4-way dot products, min and max on 16-bit lanes (bytes 0/2 and 1/3 of each
 // word) with the 3-input DPX min/max instructions.
 template <int N>
-__device__ __forceinline__ void block_stats(const uint32_t* w, float& M, float& mn, float& mx) {
+__device__ __forceinline__ Stats block_stats(const uint32_t* w) {
     uint32_t s = 0, lo2 = 0x00FF00FFu, hi2 = 0u;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -492,77 +559,167 @@ __device__ __forceinline__ void block_stats(const uint32_t* w, float& M, float& 
         lo2 = __vimin3_u16x2(lo2, e, o);
         hi2 = __vimax3_u16x2(hi2, e, o);
     }
-    M = static_cast<float>(s) * (1.0f / (4 * N));   // exact: 4N is a power of two
-    mn = static_cast<float>(min(lo2 & 0xFFFFu, lo2 >> 16));
-    mx = static_cast<float>(max(hi2 & 0xFFFFu, hi2 >> 16));
+    Stats st;
+    // (2^23 + s) / (4N) - 2^23 / (4N): both steps exact (4N is a power of two)
+    st.M = fmaf(__int_as_float(0x4B000000 | s), 1.0f / (4 * N), -8388608.0f / (4 * N));
+    const uint32_t mn = __vimin3_u16x2(lo2, lo2 >> 16, lo2) & 0xFFFFu;
+    const uint32_t mx = __vimax3_u16x2(hi2, hi2 >> 16, hi2) & 0xFFFFu;
+    const float2 e = __fadd2_rn(make_float2(__int_as_float(0x4B000000 | mn), __int_as_float(0x4B000000 | mx)),
+                                dup2(-8388608.0f));   // exact small integers
+    st.mn = e.x;
+    st.mx = e.y;
+    return st;
 }
 
 // ------------------------------------------------------------------ (c)
 // The per-pixel test (I - mu)^2 > thr, evaluated in FP32, is monotone in
 // |I - mu|, so its background set is an interval [lo, hi] of intensities.
 // bg_interval finds that interval exactly (the FP32 test itself decides the
-// boundary integers) and fg_nibble then tests 4 pixels at once on bytes.
-__device__ __forceinline__ bool is_bg(float I, float mu, float thr) {
-    const float d = I - mu;
-    return d * d <= thr;
-}
-
+// boundary integers) and fg_bits then tests 4 pixels at once on bytes:
+// x > hi  <=>  x + (255 - hi) carries out of the byte, and
+// x < lo  <=>  (255 - x) + lo carries out of the byte.
 struct Thresh {
-    uint32_t c_gt;   // 255 - hi in every byte: x > hi  <=>  x + c_gt carries
-    uint32_t c_lt;   // lo in every byte:       x < lo  <=>  ~x + c_lt carries
-    uint32_t all;    // 0x80808080 when no intensity is background
+    uint32_t c_gt;   // 255 - hi in every byte
+    uint32_t c_lt;   // lo in every byte
 };
 
-__device__ __forceinline__ Thresh bg_interval(float mu, float thr) {
-    // s slightly below sqrt(thr) (the approximate rsqrt is within 3e-7), so
-    // every integer within s of mu is background and the true ends of the
-    // interval lie at most one step beyond floor(mu + s) / ceil(mu - s)
-    const float s = thr * rsqrtf(fmaxf(thr, 1.0e-30f)) * (1.0f - 1.0e-6f);
-    float hi = floorf(mu + s);
-    float lo = ceilf(mu - s);
-    hi += is_bg(hi + 1.f, mu, thr) ? 1.f : 0.f;
-    lo -= is_bg(lo - 1.f, mu, thr) ? 1.f : 0.f;
-    const int ih = min(max(__float2int_rd(hi), -1), 255);
-    const int il = min(max(__float2int_rd(lo), 0), 256);
+__device__ __forceinline__ Thresh thresh_of(int ih, int il) {
+    const int hi = min(ih, 255), lo = max(il, 0);
     Thresh t;
-    t.all = il > ih ? 0x80808080u : 0u;
-    t.c_gt = uint32_t(255 - max(ih, 0)) * 0x01010101u;
-    t.c_lt = uint32_t(min(il, 255)) * 0x01010101u;
+    if (lo > hi) {   // no intensity is background: both tests fire on every byte
+        t.c_gt = t.c_lt = 0xFFFFFFFFu;
+    } else {
+        t.c_gt = __byte_perm(uint32_t(255 - hi), 0u, 0x0000);
+        t.c_lt = __byte_perm(uint32_t(lo), 0u, 0x0000);
+    }
     return t;
 }
 
-// Per-byte carry out of x + c (bit 7 of every byte), no carries between bytes:
-// the majority of the two top bits and the carry into bit 7.
-__device__ __forceinline__ uint32_t carry8(uint32_t x, uint32_t c) {
-    const uint32_t s = (x & 0x7f7f7f7fu) + (c & 0x7f7f7f7fu);
-    return ((x & c) | ((x | c) & s)) & 0x80808080u;
+// Two models side by side (x and y lanes of the packed operations, each
+// rounded exactly like its scalar form).  s is slightly below sqrt(thr) (the
+// approximate rsqrt is within 3e-7), so every integer within s of mu is
+// background and the true ends of the interval lie at most one step beyond
+// floor(mu + s) / ceil(mu - s); s is capped where the interval already covers
+// every intensity.
+__device__ __forceinline__ void bg_interval2(float2 mu, float2 thr, Thresh& tx, Thresh& ty) {
+    const float2 rs = make_float2(rsqrtf(fmaxf(thr.x, 1.0e-30f)), rsqrtf(fmaxf(thr.y, 1.0e-30f)));
+    float2 s = __fmul2_rn(__fmul2_rn(thr, rs), dup2(1.0f - 1.0e-6f));
+    s = make_float2(fminf(s.x, 1024.0f), fminf(s.y, 1024.0f));
+    const float2 hm = __fadd2_rd(__fadd2_rn(mu, s), dup2(kMagic));                 // kMagic + floor(mu + s)
+    const float2 lm = __fadd2_ru(__ffma2_rn(s, dup2(-1.0f), mu), dup2(kMagic));    // kMagic + ceil(mu - s)
+    const float2 dh = __ffma2_rn(mu, dup2(-1.0f), __fadd2_rn(hm, dup2(-(kMagic - 1.0f))));  // (hi + 1) - mu
+    const float2 dl = __ffma2_rn(mu, dup2(-1.0f), __fadd2_rn(lm, dup2(-(kMagic + 1.0f))));  // (lo - 1) - mu
+    const float2 qh = __fmul2_rn(dh, dh), ql = __fmul2_rn(dl, dl);
+    tx = thresh_of(__float_as_int(hm.x) - kMagicBits + (qh.x <= thr.x ? 1 : 0),
+                   __float_as_int(lm.x) - kMagicBits - (ql.x <= thr.x ? 1 : 0));
+    ty = thresh_of(__float_as_int(hm.y) - kMagicBits + (qh.y <= thr.y ? 1 : 0),
+                   __float_as_int(lm.y) - kMagicBits - (ql.y <= thr.y ? 1 : 0));
 }
 
-// Foreground bits of the 4 pixels of w (byte j -> bit j), at bits 28..31.
-__device__ __forceinline__ uint32_t fg_nibble_hi(uint32_t w, const Thresh& t) {
-    const uint32_t f = carry8(w, t.c_gt) | carry8(~w, t.c_lt) | t.all;
-    // byte j's flag -> bit 28 + j; the cross terms of the product all land
-    // below bit 28 (on distinct bits, so nothing carries) and are masked off
-    return (((f >> 7) & 0x01010101u) * 0x10204080u) & 0xF0000000u;
+__device__ __forceinline__ Thresh bg_interval(float mu, float thr) {
+    Thresh t, u;
+    bg_interval2(make_float2(mu, mu), make_float2(thr, thr), t, u);
+    return t;
 }
 
-// Store a block's next state (both models).
+// Foreground flags of the 4 pixels of w: bit 7 of byte j <=> pixel j is
+// foreground.  A byte's carry out of x + c is the majority of the two top
+// bits and the carry into bit 7 (bit 7 of the 7-bit sum); ~x's low 7 bits
+// are 0x7f - (x & 0x7f), so both sums share x & 0x7f7f7f7f.
+__device__ __forceinline__ uint32_t fg_bits(uint32_t w, const Thresh& t) {
+    const uint32_t xm = w & 0x7f7f7f7fu;
+    const uint32_t s1 = xm + (t.c_gt & 0x7f7f7f7fu);
+    const uint32_t s2 = (0x7f7f7f7fu + (t.c_lt & 0x7f7f7f7fu)) - xm;
+    const uint32_t m1 = (w & t.c_gt) | ((w | t.c_gt) & s1);
+    const uint32_t m2 = (~w & t.c_lt) | ((~w | t.c_lt) & s2);
+    return (m1 | m2) & 0x80808080u;
+}
+
+// One mask byte from the flags of the left and right 4 pixels: the high word
+// of each product gathers the four flags (bits 7, 15, 23, 31) into bits
+// 0..3 (left) or 4..7 (right); every other partial product lands on its own
+// bit outside bits 32..39, so nothing carries into the byte.
+__device__ __forceinline__ uint32_t mask_byte(uint32_t fl, uint32_t fr) {
+    return __umulhi(fr, 0x20408100u) + __umulhi(fl, 0x02040810u);
+}
+
+// Store a block's next state (both models).  Ages are <= 255.
+__device__ __forceinline__ uint32_t age_pair(const Comp& c) {
+    // kMagic + age has the age in its low byte and a zero in byte 1
+    return __byte_perm(__float_as_uint(c.A.age + kMagic), __float_as_uint(c.C.age + kMagic),
+                       0x1140);
+}
 template <typename T>
 __device__ __forceinline__ void store_block(const StreamArgs& a, int k, const Comp& c) {
     st2(a.next.mu, k, make_float2(c.A.mu, c.C.mu), (T*)nullptr);
     st2(a.next.var, k, make_float2(c.A.var, c.C.var), (T*)nullptr);
-    a.next.age[k] = static_cast<uint16_t>(min(c.A.age, 255) | (min(c.C.age, 255) << 8));
+    a.next.age[k] = static_cast<uint16_t>(age_pair(c));
+}
+// Blocks k and k + 1 with k even: one 16-byte (FP32) or 8-byte (FP16) store
+// per array and one 4-byte store of the ages.
+__device__ __forceinline__ void st4(void* base, int k, float4 v, float*) {
+    reinterpret_cast<float4*>(base)[k >> 1] = v;
+}
+__device__ __forceinline__ void st4(void* base, int k, float4 v, __half*) {
+    const __half2 lo = __float22half2_rn(make_float2(v.x, v.y));
+    const __half2 hi = __float22half2_rn(make_float2(v.z, v.w));
+    reinterpret_cast<uint2*>(base)[k >> 1] =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+template <typename T>
+__device__ __forceinline__ void store_pair(const StreamArgs& a, int k, const Comp& c0,
+                                           const Comp& c1) {
+    st4(a.next.mu, k, make_float4(c0.A.mu, c0.C.mu, c1.A.mu, c1.C.mu), (T*)nullptr);
+    st4(a.next.var, k, make_float4(c0.A.var, c0.C.var, c1.A.var, c1.C.var), (T*)nullptr);
+    reinterpret_cast<uint32_t*>(a.next.age)[k >> 1] = __byte_perm(age_pair(c0), age_pair(c1), 0x5410);
 }
 
 // ------------------------------------------------------------------ tiles
 // Lane layout: warp w of the CTA takes strip rows w, w + NW, ...; lane l owns
 // pixel columns [tx0 + 8l, tx0 + 8l + 8) of its strip row, i.e. two 4x4
 // blocks (B = 4) or one 8x8 block (B = 8), and writes one mask byte per row.
-// A tile is kTileW x (NW * B * RPT) pixels.
-template <int B, typename T, int NW, int RPT>
-__device__ __forceinline__ void compensate_tile(const StreamArgs& a, const Coef& k, int tx0,
-                                                int ty0, const Origin* orig,
-                                                Comp (&comp)[RPT][kLanePx / B]) {
+// A tile is kTileW x (NW * B * RPT) pixels, its pixels in shared memory with
+// row pitch kTileW.  A step runs tile_stats and tile_project (frame and
+// homography only), then tile_update (reads the previous state, writes the
+// next) and tile_mask.
+template <int B>
+__device__ __forceinline__ uint2 tile_words(const uint8_t* tile, int row, int lane) {
+    return *reinterpret_cast<const uint2*>(tile + row * kTileW + kLanePx * lane);
+}
+
+template <int B, int NW, int RPT>
+__device__ __forceinline__ void tile_stats(const uint8_t* tile, bool xin,
+                                           Stats (&st)[RPT][kLanePx / B]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int s = warp + NW * r;
+        uint32_t lw[B], rw[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const uint2 v = xin ? tile_words<B>(tile, B * s + i, lane) : make_uint2(0u, 0u);
+            lw[i] = v.x;
+            rw[i] = v.y;
+        }
+        if (B == 4) {
+            st[r][0] = block_stats<4>(lw);
+            st[r][kLanePx / B - 1] = block_stats<4>(rw);
+        } else {
+            uint32_t all[2 * B];
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                all[2 * i] = lw[i];
+                all[2 * i + 1] = rw[i];
+            }
+            st[r][0] = block_stats<2 * B>(all);
+        }
+    }
+}
+
+template <int B, int NW, int RPT>
+__device__ __forceinline__ void tile_project(const StreamArgs& a, const Coef& k, int tx0,
+                                             int ty0, const Origin* orig,
+                                             Proj (&pj)[RPT][kLanePx / B]) {
     constexpr int BPL = kLanePx / B;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
@@ -575,85 +732,82 @@ __device__ __forceinline__ void compensate_tile(const StreamArgs& a, const Coef&
         const int by = ty0 / B + s;
         const bool in = x < a.W && by < a.Gy;
 #pragma unroll
-        for (int j = 0; j < BPL; ++j) {
-            if (in) comp[r][j] = compensate<B, T>(a, k, bx + j, by, bx0, orig[(s << 1) | half]);
-            else comp[r][j].src = false;
-        }
+        for (int j = 0; j < BPL; ++j)
+            pj[r][j] = in ? project<B>(a, k, bx + j, by, bx0, orig[(s << 1) | half]) : no_proj();
     }
 }
 
-// Finish a tile whose pixels are in shared memory (row pitch kTileW): block
-// statistics, the dual-mode update, the next state and the mask bytes.
-template <int B, typename T, int NW, int RPT>
-__device__ __forceinline__ void finish_tile(const StreamArgs& a, const uint8_t* tile, int tx0,
-                                            int ty0, Comp (&comp)[RPT][kLanePx / B]) {
+// Gather, update and store the state of the lane's blocks; returns per block
+// the final apparent mean and the mask threshold theta_d * var_A.
+template <int B, typename T, int NW, int RPT, bool COH>
+__device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty0,
+                                            const Proj (&pj)[RPT][kLanePx / B],
+                                            const Stats (&st)[RPT][kLanePx / B],
+                                            float (&muA)[RPT][kLanePx / B],
+                                            float (&thr)[RPT][kLanePx / B]) {
+    constexpr int BPL = kLanePx / B;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
     const bool xin = x < a.W;
-    const bool xpad = !xin && x < a.mask_words * 32;         // padding bits of the last word
     const int bx = x / B;
-    const size_t mrow = size_t(a.mask_words) * 4;            // mask bytes per row
-    uint8_t* mcol = reinterpret_cast<uint8_t*>(a.mask) + (x >> 3);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int s = warp + NW * r;
         const int by = ty0 / B + s;
-        if (by >= a.Gy) break;                                 // warp-uniform
-        uint32_t lw[B], rw[B];                                 // left / right 4 pixels per row
+        Comp c[BPL];
+#pragma unroll
+        for (int j = 0; j < BPL; ++j) {
+            c[j] = gather<T, COH>(a, pj[r][j]);
+            dual_mode_step(c[j], st[r][j], a);
+        }
+        if (xin && by < a.Gy) {
+            const int k = by * a.Gx + bx;
+            if (B == 4) store_pair<T>(a, k, c[0], c[BPL - 1]);
+            else store_block<T>(a, k, c[0]);
+        }
+#pragma unroll
+        for (int j = 0; j < BPL; ++j) {
+            muA[r][j] = c[j].A.mu;
+            thr[r][j] = a.theta_d * c[j].A.var;
+        }
+    }
+}
+
+// Mask bytes of the lane's pixel rows from the final apparent models
+// (lanes past the frame's right edge but inside the last mask word write
+// zeros, so the padding bits are defined).
+template <int B, int NW, int RPT>
+__device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* tile, int tx0,
+                                          int ty0, const float (&muA)[RPT][kLanePx / B],
+                                          const float (&thr)[RPT][kLanePx / B]) {
+    constexpr int BPL = kLanePx / B;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = tx0 + kLanePx * lane;
+    if (x >= a.mask_words * 32) return;
+    const bool xin = x < a.W;
+    const size_t mrow = size_t(a.mask_words) * 4;   // mask bytes per row
+    uint8_t* mcol = reinterpret_cast<uint8_t*>(a.mask) + (x >> 3);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int s = warp + NW * r;
+        if (ty0 / B + s >= a.Gy) break;   // warp-uniform
+        uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
+        if (!xin) {
+#pragma unroll
+            for (int i = 0; i < B; ++i) m[i * mrow] = 0;
+            continue;
+        }
+        Thresh tl, tr;
+        if (BPL == 1) {
+            tl = tr = bg_interval(muA[r][0], thr[r][0]);
+        } else {
+            bg_interval2(make_float2(muA[r][0], muA[r][BPL - 1]),
+                         make_float2(thr[r][0], thr[r][BPL - 1]), tl, tr);
+        }
 #pragma unroll
         for (int i = 0; i < B; ++i) {
-            const uint2 v = xin ? *reinterpret_cast<const uint2*>(tile + (B * s + i) * kTileW +
-                                                                  kLanePx * lane)
-                                : make_uint2(0u, 0u);
-            lw[i] = v.x;
-            rw[i] = v.y;
-        }
-        uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
-        const int k = by * a.Gx + bx;
-        if (B == 4) {
-            float M, mn, mx;
-            Comp cl = comp[r][0], cr = comp[r][kLanePx / B - 1];
-            block_stats<4>(lw, M, mn, mx);
-            dual_mode_step(cl, M, mn, mx, a);
-            block_stats<4>(rw, M, mn, mx);
-            dual_mode_step(cr, M, mn, mx, a);
-            if (xin) {
-                store_block<T>(a, k, cl);
-                store_block<T>(a, k + 1, cr);
-            }
-            const Thresh tl = bg_interval(cl.A.mu, a.theta_d * cl.A.var);
-            const Thresh tr = bg_interval(cr.A.mu, a.theta_d * cr.A.var);
-            if (xin) {
-#pragma unroll
-                for (int i = 0; i < B; ++i)
-                    m[i * mrow] = uint8_t((fg_nibble_hi(lw[i], tl) >> 28) |
-                                          (fg_nibble_hi(rw[i], tr) >> 24));
-            } else if (xpad) {
-#pragma unroll
-                for (int i = 0; i < B; ++i) m[i * mrow] = 0;
-            }
-        } else {
-            uint32_t all[2 * B];
-#pragma unroll
-            for (int i = 0; i < B; ++i) {
-                all[2 * i] = lw[i];
-                all[2 * i + 1] = rw[i];
-            }
-            float M, mn, mx;
-            Comp c = comp[r][0];
-            block_stats<2 * B>(all, M, mn, mx);
-            dual_mode_step(c, M, mn, mx, a);
-            if (xin) store_block<T>(a, k, c);
-            const Thresh t = bg_interval(c.A.mu, a.theta_d * c.A.var);
-            if (xin) {
-#pragma unroll
-                for (int i = 0; i < B; ++i)
-                    m[i * mrow] = uint8_t((fg_nibble_hi(lw[i], t) >> 28) |
-                                          (fg_nibble_hi(rw[i], t) >> 24));
-            } else if (xpad) {
-#pragma unroll
-                for (int i = 0; i < B; ++i) m[i * mrow] = 0;
-            }
+            const uint2 v = tile_words<B>(tile, B * s + i, lane);
+            m[i * mrow] = uint8_t(mask_byte(fg_bits(v.x, tl), fg_bits(v.y, tr)));
         }
     }
 }

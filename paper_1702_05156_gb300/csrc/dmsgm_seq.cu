@@ -73,12 +73,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
 
     const int tix = blockIdx.x % p.tiles_x, tiy = blockIdx.x / p.tiles_x;
     const int tx0 = tix * kTileW, ty0 = tiy * TILE_H;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x = tx0 + kLanePx * lane;
-    const bool xin = x < p.W;
-    const int bx = x / B;
-    const int half = lane >> 4;
-    const int bx0 = (tx0 + 128 * half) / B;
+    const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < p.W;
     constexpr uint32_t kTileBytes = TILE_H * kTileW;
 
     StreamArgs a;
@@ -121,33 +116,16 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
             origins(k + 1, orig[st ^ 1]);
         }
         bool ok = mbar_wait_bounded(&bar[st], (k >> 1) & 1, kSeqTimeoutNs);
-        // block statistics need only this frame's pixels
-        uint32_t lw[RPT][B], rw[RPT][B];
-        float M[RPT][BPL], mn[RPT][BPL], mx[RPT][BPL];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int s = warp + NW * r;
-#pragma unroll
-            for (int i = 0; i < B; ++i) {
-                const uint2 v = (ok && xin) ? *reinterpret_cast<const uint2*>(
-                                                  tile[st] + (B * s + i) * kTileW + kLanePx * lane)
-                                            : make_uint2(0u, 0u);
-                lw[r][i] = v.x;
-                rw[r][i] = v.y;
-            }
-            if (B == 4) {
-                block_stats<4>(lw[r], M[r][0], mn[r][0], mx[r][0]);
-                block_stats<4>(rw[r], M[r][BPL - 1], mn[r][BPL - 1], mx[r][BPL - 1]);
-            } else {
-                uint32_t all[2 * B];
-#pragma unroll
-                for (int i = 0; i < B; ++i) {
-                    all[2 * i] = lw[r][i];
-                    all[2 * i + 1] = rw[r][i];
-                }
-                block_stats<2 * B>(all, M[r][0], mn[r][0], mx[r][0]);
-            }
-        }
+        a.prev = p.buf[(p.p0 + k) & 1];
+        a.next = p.buf[(p.p0 + k + 1) & 1];
+        a.first = (k == 0) ? p.first : 0;
+        a.affine = p.affine[k];
+        a.mask = p.masks + k * p.frame_words;
+        // the frame's block statistics and back-projections need no other tile
+        Stats sts[RPT][BPL];
+        Proj pj[RPT][BPL];
+        tile_stats<B, NW, RPT>(tile[st], ok && xin, sts);
+        tile_project<B, NW, RPT>(a, p.coef[k], tx0, ty0, orig[st], pj);
         // wait until every neighbour tile has published frame k-1
         if (k > 0) {
             for (int q = threadIdx.x; q < nn; q += NW * 32) {
@@ -162,53 +140,16 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
             if (k + 1 < p.T) mbar_wait_bounded(&bar[st ^ 1], ((k + 1) >> 1) & 1, kSeqTimeoutNs);
             return;
         }
-        a.prev = p.buf[(p.p0 + k) & 1];
-        a.next = p.buf[(p.p0 + k + 1) & 1];
-        a.first = (k == 0) ? p.first : 0;
-        a.affine = p.affine[k];
-        a.mask = p.masks + k * p.frame_words;
         // critical path: gather, mix, update, store the state
         float muA[RPT][BPL], thr[RPT][BPL];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int s = warp + NW * r;
-            const int by = ty0 / B + s;
-            const bool in = xin && by < p.Gy;
-#pragma unroll
-            for (int j = 0; j < BPL; ++j) {
-                Comp c;
-                if (in) c = compensate<B, T, true>(a, p.coef[k], bx + j, by, bx0, orig[st][(s << 1) | half]);
-                else c.src = false;
-                dual_mode_step(c, M[r][j], mn[r][j], mx[r][j], a);
-                if (in) store_block<T>(a, by * p.Gx + bx + j, c);
-                muA[r][j] = c.A.mu;
-                thr[r][j] = a.theta_d * c.A.var;
-            }
-        }
+        tile_update<B, T, NW, RPT, true>(a, tx0, ty0, pj, sts, muA, thr);
         __syncthreads();
         if (threadIdx.x == 0) {   // publish: this tile's frame-k state is visible
             __threadfence();
             st_release_gpu(p.flags + blockIdx.x, k + 1);
         }
-        // off the critical path: the frame's mask bytes (lanes past the
-        // frame's right edge but inside the last mask word write zeros)
-        if (x < p.mask_words * 32) {
-            const size_t mrow = size_t(p.mask_words) * 4;
-            uint8_t* mcol = reinterpret_cast<uint8_t*>(a.mask) + (x >> 3);
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const int s = warp + NW * r;
-                if (ty0 / B + s >= p.Gy) break;
-                uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
-                const Thresh tl = bg_interval(muA[r][0], thr[r][0]);
-                const Thresh tr = BPL == 1 ? tl : bg_interval(muA[r][BPL - 1], thr[r][BPL - 1]);
-#pragma unroll
-                for (int i = 0; i < B; ++i)
-                    m[i * mrow] = xin ? uint8_t((fg_nibble_hi(lw[r][i], tl) >> 28) |
-                                                (fg_nibble_hi(rw[r][i], tr) >> 24))
-                                      : uint8_t(0);
-            }
-        }
+        // off the critical path: the frame's mask bytes
+        tile_mask<B, NW, RPT>(a, tile[st], tx0, ty0, muA, thr);
         __syncthreads();   // this stage's pixels and origins are consumed
     }
 }
