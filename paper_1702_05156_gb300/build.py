@@ -31,12 +31,15 @@ def _sources():
 
 
 def _fingerprint() -> str:
+    """Hash of the kernel sources, the public headers and the compile flags.
+    Paths enter relative to the repository root, so the same sources give the
+    same fingerprint wherever the repository sits."""
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h"))):
         with open(p, "rb") as f:
-            h.update(p.encode())
+            h.update(os.path.relpath(p, ROOT).encode())
             h.update(f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + [f for f in FLAGS if f not in (INCLUDE, CSRC)]).encode())
     return h.hexdigest()
 
 
