@@ -88,7 +88,18 @@ typedef struct {
                            times the block size / 2 (32, 64, 128, 256 rows
                            for block 4; 64, 128, 256 for block 8); 0 = the
                            built-in choice                                    */
+    int kernel;         /* frame-step kernel of dmsgm_process and
+                           dmsgm_process_host: DMSGM_KERNEL_AUTO (0),
+                           DMSGM_KERNEL_TILE (one CTA per tile) or
+                           DMSGM_KERNEL_PIPE (resident CTAs that stream the
+                           tiles, staging each tile's pixels and previous-
+                           state box in shared memory by TMA; frames in the
+                           general projective form, and sizes whose state
+                           rows are not 16-byte multiples, use the per-tile
+                           kernel).  Results are identical.                  */
 } dmsgm_opts;
+
+enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1, DMSGM_KERNEL_PIPE = 2 };
 
 /* Read-only description of a handle. */
 typedef struct {
@@ -101,6 +112,10 @@ typedef struct {
     size_t host_state_bytes;     /* bytes of the packed image of get/set_state */
     int tile_rows;               /* rows per CTA tile in use                 */
     int device;                  /* CUDA device of the handle                */
+    int kernel;                  /* frame-step kernel setting (DMSGM_KERNEL_*) */
+    int last_kernel;             /* kernel of the last dmsgm_process step:
+                                    DMSGM_KERNEL_TILE or DMSGM_KERNEL_PIPE;
+                                    0 before the first                        */
 } dmsgm_info;
 
 /* Device bytes a handle needs for its state: a 256-byte control block, one

@@ -24,6 +24,9 @@ DMSGM_ERR_DEVICE_STATUS = -5
 DMSGM_ERR_UNSUPPORTED = -6
 DMSGM_STATE_FP32 = 0
 DMSGM_STATE_FP16 = 1
+DMSGM_KERNEL_AUTO = 0
+DMSGM_KERNEL_TILE = 1
+DMSGM_KERNEL_PIPE = 2
 DMSGM_MAX_BATCH = 256
 
 # every symbol include/dmsgm.h declares
@@ -38,7 +41,8 @@ EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm
 class dmsgm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("state_mem", ctypes.c_void_p),
                 ("state_bytes", ctypes.c_size_t), ("tile_rows", ctypes.c_int),
-                ("use_pdl", ctypes.c_int), ("seq_tile_rows", ctypes.c_int)]
+                ("use_pdl", ctypes.c_int), ("seq_tile_rows", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 class dmsgm_batch_opts(ctypes.Structure):
@@ -52,7 +56,8 @@ class dmsgm_info(ctypes.Structure):
                 ("theta_d", ctypes.c_float), ("initialized", ctypes.c_int),
                 ("parity", ctypes.c_int), ("frames", ctypes.c_ulonglong),
                 ("state_bytes", ctypes.c_size_t), ("host_state_bytes", ctypes.c_size_t),
-                ("tile_rows", ctypes.c_int), ("device", ctypes.c_int)]
+                ("tile_rows", ctypes.c_int), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("last_kernel", ctypes.c_int)]
 
 
 class DmsgmError(RuntimeError):

@@ -31,13 +31,13 @@ void clear_error() { g_err[0] = 0; }
 // ------------------------------------------------------------------ kernel
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // 2 s: only a broken copy gets here
 
-// 8x8 blocks: 32 registers (full occupancy) measured faster despite a small
-// spill; 4x4 blocks keep the compiler's choice.
-template <int B, int NW>
-constexpr int step_min_blocks() { return B == 8 ? 64 / NW : 1; }
+// 8x8 blocks, one strip row per warp: 32 registers (full occupancy); two
+// rows per warp: 64.  4x4 blocks keep the compiler's choice.
+template <int B, int NW, int RPT>
+constexpr int step_min_blocks() { return B == 8 ? (RPT == 1 ? 64 : 32) / NW : 1; }
 
 template <int B, typename T, int NW, int RPT>
-__global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
+__global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
     dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, const Coef k,
                       int* status) {
     constexpr int STRIPS = NW * RPT;          // strip rows per tile
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW>()))
     pdl_launch_dependents();
     float muA[RPT][BPL], thr[RPT][BPL];
     tile_update<B, T, NW, RPT, false>(a, tx0, ty0, pj, st, muA, thr);
-    tile_mask<B, NW, RPT>(a, tile, tx0, ty0, muA, thr);
+    tile_mask<B, NW, RPT>(a, tile, tx0, ty0, st, muA, thr);
 }
 
 // Diagnostic kernel: waits on a barrier that nothing completes, so the
@@ -108,19 +108,61 @@ static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, c
     return cudaLaunchKernelEx(&cfg, dmsgm_step_kernel<B, T, NW, RPT>, tmap, a, k, status);
 }
 
-// tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1), (8, 2)}
-static cudaError_t launch_step(int B, int prec, int tile_rows, const CUtensorMap& tmap,
-                               const StreamArgs& a, const Coef& k, int* status, cudaStream_t s,
-                               bool pdl) {
-    const int q = tile_rows / B;   // 4, 8 or 16
-#define DMSGM_CASE(BB, TT, QQ, NWW, RR) \
-    if (B == BB && q == QQ) return launch_step_t<BB, TT, NWW, RR>(tmap, a, k, status, s, pdl);
-    if (prec == DMSGM_STATE_FP32) {
-        DMSGM_CASE(4, float, 4, 4, 1) DMSGM_CASE(4, float, 8, 8, 1) DMSGM_CASE(4, float, 16, 8, 2)
-        DMSGM_CASE(8, float, 4, 4, 1) DMSGM_CASE(8, float, 8, 8, 1) DMSGM_CASE(8, float, 16, 8, 2)
+// How many CTAs of one per-tile kernel shape the GPU holds at once.
+template <int B, typename T, int NW, int RPT>
+static int step_capacity(int device) {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    std::lock_guard<std::mutex> g(mu);
+    if (device < 0 || device >= 64) return 0;
+    if (!cache[device]) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_step_kernel<B, T, NW, RPT>,
+                                                          NW * 32, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cache[device] = per_sm * sms;
+    }
+    return cache[device];
+}
+
+// Strip rows per warp for tile_rows = 8 B: 8 warps x 1 row when the frame's
+// CTAs fit the GPU at once; otherwise 4 warps x 2 rows, which holds the
+// frame in fewer resident warps (a single wave at 3840 x 2160) instead of
+// leaving a partial second wave.
+template <int B, typename T>
+static int step_rpt_q8(const dmsgm_ctx* h) {
+    const int ctas = ((h->W + kTileW - 1) / kTileW) * ((h->H + 8 * B - 1) / (8 * B));
+    const int cap = step_capacity<B, T, 8, 1>(h->device);
+    return (cap > 0 && ctas > cap) ? 2 : 1;
+}
+
+// tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1) or (4, 2), (8, 2)}
+static cudaError_t launch_step(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
+                               const Coef& k, cudaStream_t s) {
+    const int B = h->B, q = h->tile_rows / B;   // 4, 8 or 16
+    const bool f16 = h->prec == DMSGM_STATE_FP16;
+    const bool pdl = h->use_pdl != 0;
+    if (q == 8 && h->step_rpt == 0)
+        h->step_rpt = B == 4 ? (f16 ? step_rpt_q8<4, __half>(h) : step_rpt_q8<4, float>(h))
+                             : (f16 ? step_rpt_q8<8, __half>(h) : step_rpt_q8<8, float>(h));
+    const int rpt = q == 8 ? h->step_rpt : (q == 16 ? 2 : 1);
+    int* st = h->status_dev;
+#define DMSGM_CASE(BB, TT, QQ, NWW, RR)                                         \
+    if (B == BB && q == QQ && rpt == RR)                                       \
+        return launch_step_t<BB, TT, NWW, RR>(tmap, a, k, st, s, pdl);
+    if (!f16) {
+        DMSGM_CASE(4, float, 4, 4, 1) DMSGM_CASE(4, float, 8, 8, 1) DMSGM_CASE(4, float, 8, 4, 2)
+        DMSGM_CASE(4, float, 16, 8, 2)
+        DMSGM_CASE(8, float, 4, 4, 1) DMSGM_CASE(8, float, 8, 8, 1) DMSGM_CASE(8, float, 8, 4, 2)
+        DMSGM_CASE(8, float, 16, 8, 2)
     } else {
-        DMSGM_CASE(4, __half, 4, 4, 1) DMSGM_CASE(4, __half, 8, 8, 1) DMSGM_CASE(4, __half, 16, 8, 2)
-        DMSGM_CASE(8, __half, 4, 4, 1) DMSGM_CASE(8, __half, 8, 8, 1) DMSGM_CASE(8, __half, 16, 8, 2)
+        DMSGM_CASE(4, __half, 4, 4, 1) DMSGM_CASE(4, __half, 8, 8, 1) DMSGM_CASE(4, __half, 8, 4, 2)
+        DMSGM_CASE(4, __half, 16, 8, 2)
+        DMSGM_CASE(8, __half, 4, 4, 1) DMSGM_CASE(8, __half, 8, 8, 1) DMSGM_CASE(8, __half, 8, 4, 2)
+        DMSGM_CASE(8, __half, 16, 8, 2)
     }
 #undef DMSGM_CASE
     return cudaErrorInvalidValue;
@@ -259,9 +301,17 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
     if (rc) return rc;
     StreamArgs a;
     fill_args(h, affine, mask_dev, &a);
-    cudaError_t e = launch_step(h->B, h->prec, h->tile_rows, *tm, a, c, h->status_dev, s,
-                                h->use_pdl != 0);
-    if (e != cudaSuccess) return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    bool launched = false;
+    if (h->kernel != DMSGM_KERNEL_TILE) {
+        rc = launch_pipe(h, *tm, a, c, s, h->kernel == DMSGM_KERNEL_AUTO, &launched);
+        if (rc) return rc;
+    }
+    if (!launched) {
+        cudaError_t e = launch_step(h, *tm, a, c, s);
+        if (e != cudaSuccess)
+            return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    }
+    h->last_kernel = launched ? DMSGM_KERNEL_PIPE : DMSGM_KERNEL_TILE;
     advance(h);
     return DMSGM_OK;
 }
@@ -379,6 +429,11 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
         return fail(DMSGM_ERR_INVALID_ARG, "seq_tile_rows %d invalid", opts.seq_tile_rows);
     }
     h->seq_tile_rows = opts.seq_tile_rows;
+    if (opts.kernel < DMSGM_KERNEL_AUTO || opts.kernel > DMSGM_KERNEL_PIPE) {
+        delete h;
+        return fail(DMSGM_ERR_INVALID_ARG, "unknown kernel %d", opts.kernel);
+    }
+    h->kernel = opts.kernel;
     h->state_bytes = need;
     if (opts.state_mem) {
         h->mem = opts.state_mem;
@@ -659,6 +714,8 @@ int dmsgm_get_info(dmsgm_t h, dmsgm_info* o) {
     o->host_state_bytes = dmsgm_host_state_bytes(h->W, h->H, h->B, h->prec);
     o->tile_rows = h->tile_rows;
     o->device = h->device;
+    o->kernel = h->kernel;
+    o->last_kernel = h->last_kernel;
     return DMSGM_OK;
 }
 

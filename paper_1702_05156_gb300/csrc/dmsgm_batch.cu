@@ -129,7 +129,7 @@ __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origi
     tile_stats<B, kBatchWarps, 1>(tile, xin, st);
     float muA[1][BPL], thr[1][BPL];
     tile_update<B, T, kBatchWarps, 1, false>(a, tx0, ty0, pj, st, muA, thr);
-    tile_mask<B, kBatchWarps, 1>(a, tile, tx0, ty0, muA, thr);
+    tile_mask<B, kBatchWarps, 1>(a, tile, tx0, ty0, st, muA, thr);
     return true;
 }
 

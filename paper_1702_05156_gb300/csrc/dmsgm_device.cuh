@@ -452,38 +452,58 @@ __device__ __forceinline__ Comp no_source() {
     return r;
 }
 
+// Where a gather reads the previous state.  at(i, j) is the index of grid
+// block (i, j), pitch the index step from one grid row to the next.
+// GlobalSrc: the previous state buffer in global memory.
+template <typename T, bool COH>
+struct GlobalSrc {
+    const void* mu;
+    const void* var;
+    const uint16_t* age;
+    int pitch;
+    __device__ __forceinline__ int at(int i, int j) const { return j * pitch + i; }
+    __device__ __forceinline__ float2 ld_mu(int k) const { return ld2<COH>(mu, k, (T*)nullptr); }
+    __device__ __forceinline__ float2 ld_var(int k) const { return ld2<COH>(var, k, (T*)nullptr); }
+    __device__ __forceinline__ uint32_t ld_ag(int k) const { return ld_age<COH>(age, k); }
+};
+template <typename T, bool COH>
+__device__ __forceinline__ GlobalSrc<T, COH> global_src(const StreamArgs& a) {
+    return GlobalSrc<T, COH>{a.prev.mu, a.prev.var, a.prev.age, a.Gx};
+}
+
 // Area-weighted mix of the four overlapped blocks whose top-left one is k0
 // (all four on the grid; the weights sum to 1).
-template <typename T, bool COH>
-__device__ __forceinline__ Comp mix4(const StreamArgs& a, int k0, const Weights& w) {
-    const int k1 = k0 + a.Gx;
+template <typename Src>
+__device__ __forceinline__ Comp mix4(const Src& src, int k0, const Weights& w) {
+    const int k1 = k0 + src.pitch;
     const float2 W00 = dup2(w.w00), W10 = dup2(w.w10), W01 = dup2(w.w01), W11 = dup2(w.w11);
     float2 mu, var, ag;
-    mu = __fmul2_rn(W00, ld2<COH>(a.prev.mu, k0, (T*)nullptr));
-    mu = __ffma2_rn(W10, ld2<COH>(a.prev.mu, k0 + 1, (T*)nullptr), mu);
-    mu = __ffma2_rn(W01, ld2<COH>(a.prev.mu, k1, (T*)nullptr), mu);
-    mu = __ffma2_rn(W11, ld2<COH>(a.prev.mu, k1 + 1, (T*)nullptr), mu);
-    var = __fmul2_rn(W00, ld2<COH>(a.prev.var, k0, (T*)nullptr));
-    var = __ffma2_rn(W10, ld2<COH>(a.prev.var, k0 + 1, (T*)nullptr), var);
-    var = __ffma2_rn(W01, ld2<COH>(a.prev.var, k1, (T*)nullptr), var);
-    var = __ffma2_rn(W11, ld2<COH>(a.prev.var, k1 + 1, (T*)nullptr), var);
-    ag = __fmul2_rn(W00, age2f(ld_age<COH>(a.prev.age, k0)));
-    ag = __ffma2_rn(W10, age2f(ld_age<COH>(a.prev.age, k0 + 1)), ag);
-    ag = __ffma2_rn(W01, age2f(ld_age<COH>(a.prev.age, k1)), ag);
-    ag = __ffma2_rn(W11, age2f(ld_age<COH>(a.prev.age, k1 + 1)), ag);
+    mu = __fmul2_rn(W00, src.ld_mu(k0));
+    mu = __ffma2_rn(W10, src.ld_mu(k0 + 1), mu);
+    mu = __ffma2_rn(W01, src.ld_mu(k1), mu);
+    mu = __ffma2_rn(W11, src.ld_mu(k1 + 1), mu);
+    var = __fmul2_rn(W00, src.ld_var(k0));
+    var = __ffma2_rn(W10, src.ld_var(k0 + 1), var);
+    var = __ffma2_rn(W01, src.ld_var(k1), var);
+    var = __ffma2_rn(W11, src.ld_var(k1 + 1), var);
+    ag = __fmul2_rn(W00, age2f(src.ld_ag(k0)));
+    ag = __ffma2_rn(W10, age2f(src.ld_ag(k0 + 1)), ag);
+    ag = __ffma2_rn(W01, age2f(src.ld_ag(k1)), ag);
+    ag = __ffma2_rn(W11, age2f(src.ld_ag(k1 + 1)), ag);
     return comp_from(mu, var, ag);
 }
 
 // Motion compensation of one block (Sec. 2.4) from its projection: the
 // area-weighted mix of the previous blocks its back-projected square
 // overlaps.  At the grid border the blocks off the grid are dropped and the
-// remaining weights renormalised.
-template <typename T, bool COH>
-__device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p) {
+// remaining weights renormalised.  src must hold the blocks (i0 .. i0+1,
+// j0 .. j0+1) that lie on the grid.
+template <typename Src>
+__device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p, const Src& src) {
     if (!p.ok) return no_source();
     const Weights w = overlap(p);
     if (p.i0 >= 0 && p.i0 + 1 < a.Gx && p.j0 >= 0 && p.j0 + 1 < a.Gy)
-        return mix4<T, COH>(a, p.j0 * a.Gx + p.i0, w);
+        return mix4(src, src.at(p.i0, p.j0), w);
     float wsum = 0.f;
     float2 mu = make_float2(0.f, 0.f), var = mu, ag = mu;
 #pragma unroll
@@ -491,17 +511,21 @@ __device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p) {
         const int i = p.i0 + (q & 1), j = p.j0 + (q >> 1);
         const float wq = q == 0 ? w.w00 : q == 1 ? w.w10 : q == 2 ? w.w01 : w.w11;
         if (i >= 0 && i < a.Gx && j >= 0 && j < a.Gy) {
-            const int kk = j * a.Gx + i;
+            const int kk = src.at(i, j);
             const float2 W = dup2(wq);
             wsum += wq;
-            mu = __ffma2_rn(W, ld2<COH>(a.prev.mu, kk, (T*)nullptr), mu);
-            var = __ffma2_rn(W, ld2<COH>(a.prev.var, kk, (T*)nullptr), var);
-            ag = __ffma2_rn(W, age2f(ld_age<COH>(a.prev.age, kk)), ag);
+            mu = __ffma2_rn(W, src.ld_mu(kk), mu);
+            var = __ffma2_rn(W, src.ld_var(kk), var);
+            ag = __ffma2_rn(W, age2f(src.ld_ag(kk)), ag);
         }
     }
     if (!(wsum >= kMinWeight)) return no_source();
     return comp_from(make_float2(mu.x / wsum, mu.y / wsum), make_float2(var.x / wsum, var.y / wsum),
                      make_float2(ag.x / wsum, ag.y / wsum));
+}
+template <typename T, bool COH>
+__device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p) {
+    return gather(a, p, global_src<T, COH>(a));
 }
 
 // ------------------------------------------------------------------ (b)
@@ -737,14 +761,16 @@ __device__ __forceinline__ void tile_project(const StreamArgs& a, const Coef& k,
     }
 }
 
-// Gather, update and store the state of the lane's blocks; returns per block
-// the final apparent mean and the mask threshold theta_d * var_A.
-template <int B, typename T, int NW, int RPT, bool COH>
-__device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty0,
-                                            const Proj (&pj)[RPT][kLanePx / B],
-                                            const Stats (&st)[RPT][kLanePx / B],
-                                            float (&muA)[RPT][kLanePx / B],
-                                            float (&thr)[RPT][kLanePx / B]) {
+// Gather (gather_fn: Proj -> Comp), update and store the state of the lane's
+// blocks; returns per block the final apparent mean and the mask threshold
+// theta_d * var_A.
+template <int B, typename T, int NW, int RPT, typename GatherFn>
+__device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, int ty0,
+                                                 const Proj (&pj)[RPT][kLanePx / B],
+                                                 const Stats (&st)[RPT][kLanePx / B],
+                                                 float (&muA)[RPT][kLanePx / B],
+                                                 float (&thr)[RPT][kLanePx / B],
+                                                 const GatherFn& gather_fn) {
     constexpr int BPL = kLanePx / B;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
@@ -757,7 +783,7 @@ __device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty
         Comp c[BPL];
 #pragma unroll
         for (int j = 0; j < BPL; ++j) {
-            c[j] = gather<T, COH>(a, pj[r][j]);
+            c[j] = gather_fn(pj[r][j]);
             dual_mode_step(c[j], st[r][j], a);
         }
         if (xin && by < a.Gy) {
@@ -773,17 +799,39 @@ __device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty
     }
 }
 
-// Mask bytes of the lane's pixel rows from the final apparent models
-// (lanes past the frame's right edge but inside the last mask word write
-// zeros, so the padding bits are defined).
+template <int B, typename T, int NW, int RPT, bool COH>
+__device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty0,
+                                            const Proj (&pj)[RPT][kLanePx / B],
+                                            const Stats (&st)[RPT][kLanePx / B],
+                                            float (&muA)[RPT][kLanePx / B],
+                                            float (&thr)[RPT][kLanePx / B]) {
+    const GlobalSrc<T, COH> src = global_src<T, COH>(a);
+    tile_update_with<B, T, NW, RPT>(a, tx0, ty0, pj, st, muA, thr,
+                                    [&](const Proj& p) { return gather(a, p, src); });
+}
+
+// Both extremes of a block's pixels pass the background test: then every
+// pixel does, since the background set of the FP32 test is an interval of
+// intensities containing [mn, mx].  Same operations as the per-pixel test.
+__device__ __forceinline__ bool block_all_bg(const Stats& st, float mu, float thr) {
+    const float2 d = __fadd2_rn(make_float2(st.mn, st.mx), dup2(-mu));
+    const float2 q = __fmul2_rn(d, d);
+    return q.x <= thr && q.y <= thr;
+}
+
+// Mask bytes of the lane's pixel rows from the final apparent models.  A
+// warp whose blocks are all background writes zero bytes without the
+// per-pixel test.  Lanes past the frame's right edge but inside the last
+// mask word write zeros, so the padding bits are defined.
 template <int B, int NW, int RPT>
 __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* tile, int tx0,
-                                          int ty0, const float (&muA)[RPT][kLanePx / B],
+                                          int ty0, const Stats (&st)[RPT][kLanePx / B],
+                                          const float (&muA)[RPT][kLanePx / B],
                                           const float (&thr)[RPT][kLanePx / B]) {
     constexpr int BPL = kLanePx / B;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
-    if (x >= a.mask_words * 32) return;
+    const bool active = x < a.mask_words * 32;      // owns a byte of the mask row
     const bool xin = x < a.W;
     const size_t mrow = size_t(a.mask_words) * 4;   // mask bytes per row
     uint8_t* mcol = reinterpret_cast<uint8_t*>(a.mask) + (x >> 3);
@@ -792,7 +840,19 @@ __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* ti
         const int s = warp + NW * r;
         if (ty0 / B + s >= a.Gy) break;   // warp-uniform
         uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
-        if (!xin) {
+        bool flat = true;   // lanes outside the frame count as flat
+        if (xin) {
+#pragma unroll
+            for (int j = 0; j < BPL; ++j) flat = flat && block_all_bg(st[r][j], muA[r][j], thr[r][j]);
+        }
+        if (__all_sync(0xffffffffu, flat) || !xin) {
+            if (active) {
+#pragma unroll
+                for (int i = 0; i < B; ++i) m[i * mrow] = 0;
+            }
+            continue;
+        }
+        if (flat) {
 #pragma unroll
             for (int i = 0; i < B; ++i) m[i * mrow] = 0;
             continue;

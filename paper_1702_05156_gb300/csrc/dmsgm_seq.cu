@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
             st_release_gpu(p.flags + blockIdx.x, k + 1);
         }
         // off the critical path: the frame's mask bytes
-        tile_mask<B, NW, RPT>(a, tile[st], tx0, ty0, muA, thr);
+        tile_mask<B, NW, RPT>(a, tile[st], tx0, ty0, sts, muA, thr);
         __syncthreads();   // this stage's pixels and origins are consumed
     }
 }

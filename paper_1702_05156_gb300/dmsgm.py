@@ -13,7 +13,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DMSGM_STATE_FP16, DMSGM_STATE_FP32
+from ._lib import (DMSGM_KERNEL_AUTO, DMSGM_KERNEL_PIPE, DMSGM_KERNEL_TILE, DMSGM_STATE_FP16,
+                   DMSGM_STATE_FP32)
 
 
 def mask_words(width: int) -> int:
@@ -50,13 +51,15 @@ class Dmsgm:
     def __init__(self, width: int, height: int, block: int = 4, theta_s: float = 2.0,
                  theta_d: float = 4.0, age_max: int = 30, precision: str = "fp32",
                  tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None,
-                 seq_tile_rows: int = 0):
+                 seq_tile_rows: int = 0, kernel: str = "auto"):
         prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
         opts = _lib.dmsgm_opts()
         opts.precision = prec
         opts.tile_rows = tile_rows
         opts.use_pdl = 1 if use_pdl else 0
         opts.seq_tile_rows = seq_tile_rows
+        opts.kernel = {"auto": DMSGM_KERNEL_AUTO, "tile": DMSGM_KERNEL_TILE,
+                       "pipe": DMSGM_KERNEL_PIPE}[kernel]
         self._state_mem = state_mem
         if state_mem is not None:
             opts.state_mem = state_mem.data_ptr()
