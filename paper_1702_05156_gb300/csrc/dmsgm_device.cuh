@@ -776,16 +776,21 @@ __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, i
     const int x = tx0 + kLanePx * lane;
     const bool xin = x < a.W;
     const int bx = x / B;
+    // all strip rows' gathers first: the loads of a later row cannot move
+    // above an earlier row's state stores on their own (the compiler does not
+    // know that the two buffers are distinct)
+    Comp cc[RPT][BPL];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int j = 0; j < BPL; ++j) cc[r][j] = gather_fn(pj[r][j]);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int s = warp + NW * r;
         const int by = ty0 / B + s;
-        Comp c[BPL];
+        Comp (&c)[BPL] = cc[r];
 #pragma unroll
-        for (int j = 0; j < BPL; ++j) {
-            c[j] = gather_fn(pj[r][j]);
-            dual_mode_step(c[j], st[r][j], a);
-        }
+        for (int j = 0; j < BPL; ++j) dual_mode_step(c[j], st[r][j], a);
         if (xin && by < a.Gy) {
             const int k = by * a.Gx + bx;
             if (B == 4) store_pair<T>(a, k, c[0], c[BPL - 1]);
