@@ -37,11 +37,16 @@
  *   R9 strict '<' in the match tests, strict '>' in the swap and the mask;
  *   R10 a block with no source (first frame, Z <= 0, non-finite projection,
  *      or in-grid weight below 1e-3) resets both models to (M, 255, 1) and
- *      skips the match step.
+ *      skips the match step;
+ *   R11 sides that are not multiples of B: the grid has ceil(W/B) x ceil(H/B)
+ *      blocks with the nominal geometry (centres, back-projected squares,
+ *      mixing); a block cut by the right or bottom edge takes M_i, its
+ *      extremes and V_i over its pixels inside the frame, and only those
+ *      pixels get mask values.
  *
  * Pixel (x, y) has its centre at (x + 0.5, y + 0.5).  Block (bx, by) covers
- * pixels [bx*B, (bx+1)*B) x [by*B, (by+1)*B); its centre is
- * ((bx + 0.5) * B, (by + 0.5) * B).
+ * pixels [bx*B, (bx+1)*B) x [by*B, (by+1)*B) clipped to the frame; its centre
+ * is ((bx + 0.5) * B, (by + 0.5) * B).
  *
  * Build:  gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so
  *         dmsgm_oracle.c -lm
@@ -88,14 +93,14 @@ typedef struct { double mu, var; int age; } model_t;
  *   age   = age~ + 1, not beyond age_max (appendix: increment only below cap)
  */
 static model_t sgm_update(model_t m, double M, const unsigned char* frame, int W,
-                          int x0, int y0, int B, int age_max)
+                          int x0, int y0, int x1, int y1, int age_max)
 {
     model_t out;
     double a = (double)m.age;
     out.mu = a / (a + 1.0) * m.mu + 1.0 / (a + 1.0) * M;
     double V = 0.0;
-    for (int y = y0; y < y0 + B; ++y)
-        for (int x = x0; x < x0 + B; ++x) {
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
             double d = out.mu - (double)frame[(size_t)y * W + x];
             if (d * d > V) V = d * d;
         }
@@ -123,6 +128,7 @@ static model_t sgm_reset(double M)
  * diag      NULL or Gx*Gy*ORACLE_DIAG doubles.
  *
  * Returns 0, or -1 on invalid sizes.  Inputs and outputs must not alias.
+ * The grid is Gx x Gy = ceil(W/B) x ceil(H/B) blocks (R11).
  */
 int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max,
                 int first, const unsigned char* frame, const double* Hm,
@@ -132,24 +138,26 @@ int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max
                 double* muC_out, double* varC_out, int* ageC_out,
                 unsigned char* mask_out, double* diag)
 {
-    if (W <= 0 || H <= 0 || B <= 0 || W % B != 0 || H % B != 0) return -1;
-    const int Gx = W / B, Gy = H / B;
+    if (W <= 0 || H <= 0 || B <= 0) return -1;
+    const int Gx = (W + B - 1) / B, Gy = (H + B - 1) / B;
 
     for (int by = 0; by < Gy; ++by) {
         for (int bx = 0; bx < Gx; ++bx) {
             const size_t k = (size_t)by * Gx + bx;
             const int x0 = bx * B, y0 = by * B;
+            const int x1 = x0 + B < W ? x0 + B : W;    /* R11: clipped to the frame */
+            const int y1 = y0 + B < H ? y0 + B : H;
 
             /* Sec. 2.2 eq. for M_i: mean of the block's pixels. */
             double S = 0.0, mn = 255.0, mx = 0.0;
-            for (int y = y0; y < y0 + B; ++y)
-                for (int x = x0; x < x0 + B; ++x) {
+            for (int y = y0; y < y1; ++y)
+                for (int x = x0; x < x1; ++x) {
                     double I = (double)frame[(size_t)y * W + x];
                     S += I;
                     if (I < mn) mn = I;
                     if (I > mx) mx = I;
                 }
-            const double M = S / ((double)B * (double)B);
+            const double M = S / ((double)(x1 - x0) * (double)(y1 - y0));
 
             /* Sec. 2.4 + R6/R8/R10: compensate the previous models by mixing
              * the blocks that the back-projected square overlaps. */
@@ -221,10 +229,10 @@ int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max
             } else {
                 const double dA = M - A.mu, dC = M - C.mu;
                 if (dA * dA < theta_s * fmax(A.var, VAR_FLOOR)) {
-                    A = sgm_update(A, M, frame, W, x0, y0, B, age_max);
+                    A = sgm_update(A, M, frame, W, x0, y0, x1, y1, age_max);
                     branch = 0;
                 } else if (dC * dC < theta_s * fmax(C.var, VAR_FLOOR)) {
-                    C = sgm_update(C, M, frame, W, x0, y0, B, age_max);
+                    C = sgm_update(C, M, frame, W, x0, y0, x1, y1, age_max);
                     branch = 1;
                 } else {
                     C = sgm_reset(M);
@@ -240,8 +248,8 @@ int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max
             muC_out[k] = C.mu; varC_out[k] = C.var; ageC_out[k] = C.age;
 
             /* Per-pixel foreground test with the final apparent model. */
-            for (int y = y0; y < y0 + B; ++y)
-                for (int x = x0; x < x0 + B; ++x) {
+            for (int y = y0; y < y1; ++y)
+                for (int x = x0; x < x1; ++x) {
                     double d = (double)frame[(size_t)y * W + x] - A.mu;
                     mask_out[(size_t)y * W + x] = (d * d > theta_d * A.var) ? 1 : 0;
                 }
@@ -276,8 +284,9 @@ int oracle_run(int W, int H, int B, double theta_s, double theta_d, int age_max,
                double* tmu_C, double* tvar_C, int* tage_C,
                unsigned char* masks)
 {
-    if (W <= 0 || H <= 0 || B <= 0 || W % B != 0 || H % B != 0 || T < 0) return -1;
-    const size_t npx = (size_t)W * H, nb = (size_t)(W / B) * (H / B);
+    if (W <= 0 || H <= 0 || B <= 0 || T < 0) return -1;
+    const size_t npx = (size_t)W * H;
+    const size_t nb = (size_t)((W + B - 1) / B) * (size_t)((H + B - 1) / B);
     for (int t = 0; t < T; ++t) {
         int rc = oracle_step(W, H, B, theta_s, theta_d, age_max, t == 0,
                              frames + (size_t)t * npx, Hs + (size_t)t * 9,

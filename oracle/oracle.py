@@ -99,9 +99,9 @@ def oracle_step(frame: np.ndarray, H: np.ndarray, prev: OracleState | None, *,
     lib = _load()
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     h, w = frame.shape
-    if w % block or h % block:
-        raise ValueError("frame size must be a multiple of the block size")
-    gy, gx = h // block, w // block
+    if block < 1:
+        raise ValueError("block size must be >= 1")
+    gy, gx = -(-h // block), -(-w // block)   # ceil: edge blocks are clipped (R11)
     Hm = np.ascontiguousarray(H, dtype=np.float64).reshape(9)
     first = prev is None
     if first:
@@ -128,7 +128,7 @@ def oracle_run(frames: np.ndarray, Hs: np.ndarray, *, block: int,
     lib = _load()
     frames = np.ascontiguousarray(frames, dtype=np.uint8)
     T, h, w = frames.shape
-    gy, gx = h // block, w // block
+    gy, gx = -(-h // block), -(-w // block)
     Hs = np.ascontiguousarray(Hs, dtype=np.float64).reshape(T, 9)
     st = OracleState.empty(gy, gx)
     tmp = OracleState.empty(gy, gx)

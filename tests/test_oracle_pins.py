@@ -50,7 +50,7 @@ def test_hand_computed_8x8_sequence():
 
 
 # ---------------------------------------------------------------- closed forms
-@pytest.mark.parametrize("block", [1, 4, 8])
+@pytest.mark.parametrize("block", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("c", [0, 37, 255])
 def test_constant_frame_identity_closed_form(block, c):
     """Identity H and a constant frame c: mu == c, var_n = 255/n while the
@@ -125,7 +125,7 @@ def _shift_blocks(a, k, l, fill):
     return out
 
 
-@pytest.mark.parametrize("block", [1, 4, 8])
+@pytest.mark.parametrize("block", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("k,l", [(1, 0), (0, 1), (-2, 3), (3, -1), (0, 0)])
 def test_whole_block_translation_is_an_exact_shift(block, k, l):
     """Content moving by (k*B, l*B) px: the compensated state of block
@@ -378,7 +378,87 @@ def test_variance_sample_min_max_identity():
 
 def test_invalid_sizes_rejected():
     with pytest.raises(ValueError):
-        oracle_step(np.zeros((6, 8), np.uint8), np.eye(3), None, block=4)
+        oracle_step(np.zeros((6, 8), np.uint8), np.eye(3), None, block=0)
+
+
+# ---------------------------------------------------------------- per-pixel model
+def test_hand_computed_per_pixel_sequence():
+    """Block 1 is the paper's own per-pixel model (M_i = I, V_i = (mu - I)^2).
+    Five hand-computed frames (tests/golden/hand_b1.json) take one pixel
+    through an apparent match, a candidate reset, a candidate match, a
+    refused swap at equal ages (strict '>') and a swap; the other pixel is a
+    constant control."""
+    with open(os.path.join(GOLDEN, "hand_b1.json")) as f:
+        g = json.load(f)
+    st = None
+    for fr in g["frames"]:
+        img = np.array(fr["pixels"], dtype=np.uint8)
+        st, mask = oracle_step(img, np.eye(3), st, block=1, theta_s=g["theta_s"],
+                               theta_d=g["theta_d"], age_max=g["age_max"])
+        e = fr["expect"]
+        for name in ("muA", "varA", "muC", "varC"):
+            exp = np.array([_q(v) for v in e[name]]).reshape(img.shape)
+            np.testing.assert_allclose(getattr(st, name), exp, rtol=1e-13, atol=0, err_msg=name)
+        for name in ("ageA", "ageC"):
+            np.testing.assert_array_equal(getattr(st, name), np.array(e[name]).reshape(img.shape))
+        np.testing.assert_array_equal(mask, np.array(e["mask"], dtype=np.uint8).reshape(img.shape))
+
+
+# ---------------------------------------------------------------- clipped edge blocks (R11)
+@pytest.mark.parametrize("W,H,block", [(10, 7, 4), (13, 10, 4), (16, 20, 16), (9, 5, 2), (17, 9, 8)])
+def test_clipped_blocks_first_frame_brute_force(W, H, block):
+    """Sides that are not multiples of B: the grid is ceil(W/B) x ceil(H/B);
+    each block's M, min and max are those of its pixels inside the frame
+    (brute force over the clipped slice), and on the first frame the mask is
+    the per-pixel test against the reset model (M, 255)."""
+    rng = np.random.default_rng(W * 31 + H)
+    img = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    st, mask, dg = oracle_step(img, np.eye(3), None, block=block, diag=True)
+    gy, gx = -(-H // block), -(-W // block)
+    assert st.muA.shape == (gy, gx)
+    Mpix = np.zeros((H, W))
+    for by in range(gy):
+        for bx in range(gx):
+            sl = img[by * block:(by + 1) * block, bx * block:(bx + 1) * block].astype(np.float64)
+            assert dg[by, bx, DIAG["M"]] == sl.mean()
+            assert dg[by, bx, DIAG["MIN"]] == sl.min() and dg[by, bx, DIAG["MAX"]] == sl.max()
+            assert st.muA[by, bx] == sl.mean() and st.varA[by, bx] == 255
+            Mpix[by * block:(by + 1) * block, bx * block:(bx + 1) * block] = sl.mean()
+    np.testing.assert_array_equal(mask, ((img - Mpix) ** 2 > 4.0 * 255).astype(np.uint8))
+
+
+@pytest.mark.parametrize("W,H,block", [(10, 7, 4), (18, 21, 8), (16, 9, 16)])
+@pytest.mark.parametrize("c", [3, 200])
+def test_clipped_blocks_constant_closed_form(W, H, block, c):
+    """A constant frame follows the full-block closed form in every block,
+    clipped ones included: their mean over the pixels inside the frame is
+    exactly c and their V is 0."""
+    img = np.full((H, W), c, dtype=np.uint8)
+    st = None
+    for n in range(1, 35):
+        st, mask = oracle_step(img, np.eye(3), st, block=block)
+        np.testing.assert_allclose(st.muA, c, rtol=0, atol=1e-12)
+        exp_var = 255.0 / n if n <= 30 else (255.0 / 30) * (30.0 / 31.0) ** (n - 30)
+        np.testing.assert_allclose(st.varA, exp_var, rtol=1e-12)
+        assert (st.ageA == min(n, 30)).all() and mask.sum() == 0
+
+
+@pytest.mark.parametrize("W,H,block", [(13, 10, 4), (21, 19, 8), (9, 7, 2)])
+def test_identity_motion_crop_invariance(W, H, block):
+    """With the identity homography no block mixes with another, so the
+    whole blocks of a clipped frame evolve exactly as the same pixels cropped
+    to a multiple of the block size."""
+    rng = np.random.default_rng(block + W)
+    frames = np.clip(rng.normal(120, 25, (6, H, W)), 0, 255).astype(np.uint8)
+    frames[3:, : H // 2] = 30
+    gx, gy = W // block, H // block
+    st = sc = None
+    for t in range(6):
+        st, m = oracle_step(frames[t], np.eye(3), st, block=block)
+        sc, mc = oracle_step(frames[t, : gy * block, : gx * block], np.eye(3), sc, block=block)
+        for n in ("muA", "varA", "ageA", "muC", "varC", "ageC"):
+            assert np.array_equal(getattr(st, n)[:gy, :gx], getattr(sc, n)), n
+        assert np.array_equal(m[: gy * block, : gx * block], mc)
 
 
 def test_run_equals_repeated_steps():
@@ -393,3 +473,20 @@ def test_run_equals_repeated_steps():
         np.testing.assert_array_equal(m, masks[t])
     for n in ("muA", "varA", "ageA", "muC", "varC", "ageC"):
         np.testing.assert_array_equal(getattr(st, n), getattr(st_run, n))
+
+
+def test_clipped_block_variance_sees_only_its_pixels():
+    """Right-edge blocks of a 10-px-wide frame (B = 4) hold 2 columns. Those
+    columns are constant while the rest of the frame is random, so their V
+    is 0 and their variance follows the closed form; a V loop over all B
+    columns would wrap into the next row's random pixels."""
+    W, H, B = 10, 8, 4
+    rng = np.random.default_rng(4)
+    st = None
+    for n in range(1, 8):
+        img = rng.integers(0, 256, (H, W), dtype=np.uint8)
+        img[:, 8:] = 77
+        st, mask = oracle_step(img, np.eye(3), st, block=B)
+        np.testing.assert_allclose(st.muA[:, 2], 77, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(st.varA[:, 2], 255.0 / n, rtol=1e-12)
+        assert (st.ageA[:, 2] == n).all() and mask[:, 8:].sum() == 0
