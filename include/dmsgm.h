@@ -17,10 +17,15 @@
  *
  * Conventions
  *   - Frames are W x H uint8, row-major, pitch W bytes, device memory,
- *     16-byte aligned base.  W % 16 == 0, W % block == 0, H % block == 0.
- *   - block is 4 or 8 on the GPU.  Block (bx, by) covers pixels
- *     [bx*B, (bx+1)*B) x [by*B, (by+1)*B); pixel (x, y) has its centre at
- *     (x + 0.5, y + 0.5).
+ *     16-byte aligned base.  W % 16 == 0 (so W is a multiple of every
+ *     block size); H is any height.
+ *   - block is 1, 2, 4, 8 or 16 (1 is the paper's per-pixel model).  The
+ *     grid is Gx x Gy = W/B x ceil(H/B) blocks; block (bx, by) covers pixels
+ *     [bx*B, (bx+1)*B) x [by*B, (by+1)*B) clipped to the frame: a bottom
+ *     block row cut by the frame edge takes its mean, extremes and variance
+ *     sample over its pixels inside the frame, while its centre and
+ *     back-projected square keep the nominal B x B geometry.  Pixel (x, y)
+ *     has its centre at (x + 0.5, y + 0.5).
  *   - The homography is a host double[9], row-major, and maps CURRENT
  *     pixel-centre coordinates to PREVIOUS ones.  It is reduced on the host
  *     (FP64) to FP32 displacement coefficients; the GPU does no FP64 work.
@@ -78,7 +83,8 @@ typedef struct {
                            outlive the handle.  NULL: the handle allocates.   */
     size_t state_bytes; /* size of state_mem                                  */
     int tile_rows;      /* rows of pixels per CTA tile: 4, 8 or 16 times the
-                           block size; 0 = built-in choice (32)              */
+                           block size, at most 256; 0 = built-in choice (8
+                           for block 1, 16 for 2, 32 for 4 and 8, 64 for 16) */
     int use_pdl;        /* 1: programmatic dependent launch -- a frame's
                            pixel load overlaps the previous kernel's tail, so
                            the frame must not be written by the kernel that
@@ -136,7 +142,7 @@ size_t dmsgm_host_state_bytes(int width, int height, int block, int precision);
  * theta_s is the match
  * threshold of Sec. 2.3, theta_d the foreground threshold, age_max the age
  * cap of Sec. 2.2 (30 in the paper).  Validation: width, height > 0;
- * block in {4, 8}; width % 16 == 0; width and height multiples of block;
+ * block in {1, 2, 4, 8, 16}; width % 16 == 0; width and height <= 2^20;
  * theta_s, theta_d finite and > 0; 1 <= age_max <= 255. */
 int dmsgm_create(int width, int height, int block, float theta_s, float theta_d,
                  int age_max, dmsgm_t* out);
@@ -168,9 +174,10 @@ int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9],
  * the dependency radius of the frames' homographies have published frame t
  * (per-tile progress counters in the handle's memory, Sec. 2.4 fixes that
  * radius); the launch is cooperative and every wait is bounded (a timeout
- * sets the status word).  Results equal n calls of dmsgm_process.  If the
- * tiles cannot all be resident at once, the call falls back to one launch
- * per frame.  Asynchronous on cuda_stream. */
+ * sets the status word).  Results equal n calls of dmsgm_process.  The
+ * kernel is built for blocks 4 and 8 on whole block rows; for other sizes,
+ * or if the tiles cannot all be resident at once, the call falls back to
+ * one launch per frame.  Asynchronous on cuda_stream. */
 int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double* H3x3s,
                       uint32_t* masks_dev, void* cuda_stream);
 
@@ -190,7 +197,8 @@ int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double*
  * in dmsgm_process_seq.  The multi-frame kernel's progress counters live in
  * one static array of 4096 ints in the library: a frame needing more tiles
  * is rejected with DMSGM_ERR_INVALID_ARG, and one whose tiles cannot all be
- * resident on the GPU with DMSGM_ERR_UNSUPPORTED.  Every call on a device
+ * resident on the GPU, or whose block is not 4 or 8 or whose height is not
+ * a multiple of the block, with DMSGM_ERR_UNSUPPORTED.  Every call on a device
  * shares that array (each launch clears the counters it uses), so calls
  * whose work may overlap on the GPU race: keep them on one stream.  The
  * first call on a device looks up the array's device address; make that
@@ -213,7 +221,8 @@ int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n,
 /* n handles, one frame each, in ONE persistent kernel launch over a
  * (stream, tile) work list (handles may differ in size, block and
  * precision; all on one device; no handle twice; width and height at most
- * 65535).  frames_dev[i], masks_dev[i] and H3x3s[9*i..] are handle i's
+ * 65535; block 4 or 8 with the height a multiple of it, else
+ * DMSGM_ERR_UNSUPPORTED).  frames_dev[i], masks_dev[i] and H3x3s[9*i..] are handle i's
  * arguments as in dmsgm_process.  1 <= n <= DMSGM_MAX_BATCH (n == 0 is a
  * no-op).  The per-stream descriptors travel in the launch's parameters:
  * the call allocates nothing and copies nothing to the device, and a stream

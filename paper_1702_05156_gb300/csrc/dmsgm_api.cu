@@ -65,11 +65,11 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
     // The pixels, their block statistics and the back-projections do not
     // depend on the previous frame's kernel, so they run before its end;
     // the state does.
-    constexpr int BPL = kLanePx / B;
+    constexpr int BPL = kLaneBlocks<B>;
     const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
     Stats st[RPT][BPL];
     Proj pj[RPT][BPL];
-    tile_stats<B, NW, RPT>(tile, xin, st);
+    tile_stats<B, NW, RPT>(a, tile, ty0, xin, st);
     tile_project<B, NW, RPT>(a, k, tx0, ty0, orig, pj);
     pdl_wait();
     pdl_launch_dependents();
@@ -145,34 +145,42 @@ static cudaError_t launch_step(dmsgm_ctx* h, const CUtensorMap& tmap, const Stre
     const int B = h->B, q = h->tile_rows / B;   // 4, 8 or 16
     const bool f16 = h->prec == DMSGM_STATE_FP16;
     const bool pdl = h->use_pdl != 0;
-    if (q == 8 && h->step_rpt == 0)
-        h->step_rpt = B == 4 ? (f16 ? step_rpt_q8<4, __half>(h) : step_rpt_q8<4, float>(h))
-                             : (f16 ? step_rpt_q8<8, __half>(h) : step_rpt_q8<8, float>(h));
+    if (q == 8 && h->step_rpt == 0) {
+#define DMSGM_RPT(BB) \
+        if (B == BB) h->step_rpt = f16 ? step_rpt_q8<BB, __half>(h) : step_rpt_q8<BB, float>(h);
+        DMSGM_RPT(1) DMSGM_RPT(2) DMSGM_RPT(4) DMSGM_RPT(8) DMSGM_RPT(16)
+#undef DMSGM_RPT
+    }
     const int rpt = q == 8 ? h->step_rpt : (q == 16 ? 2 : 1);
     int* st = h->status_dev;
 #define DMSGM_CASE(BB, TT, QQ, NWW, RR)                                         \
     if (B == BB && q == QQ && rpt == RR)                                       \
         return launch_step_t<BB, TT, NWW, RR>(tmap, a, k, st, s, pdl);
+#define DMSGM_SHAPES(BB, TT)                                                    \
+    DMSGM_CASE(BB, TT, 4, 4, 1) DMSGM_CASE(BB, TT, 8, 8, 1) DMSGM_CASE(BB, TT, 8, 4, 2) \
+    DMSGM_CASE(BB, TT, 16, 8, 2)
     if (!f16) {
-        DMSGM_CASE(4, float, 4, 4, 1) DMSGM_CASE(4, float, 8, 8, 1) DMSGM_CASE(4, float, 8, 4, 2)
-        DMSGM_CASE(4, float, 16, 8, 2)
-        DMSGM_CASE(8, float, 4, 4, 1) DMSGM_CASE(8, float, 8, 8, 1) DMSGM_CASE(8, float, 8, 4, 2)
-        DMSGM_CASE(8, float, 16, 8, 2)
+        DMSGM_SHAPES(1, float) DMSGM_SHAPES(2, float) DMSGM_SHAPES(4, float)
+        DMSGM_SHAPES(8, float) DMSGM_SHAPES(16, float)
     } else {
-        DMSGM_CASE(4, __half, 4, 4, 1) DMSGM_CASE(4, __half, 8, 8, 1) DMSGM_CASE(4, __half, 8, 4, 2)
-        DMSGM_CASE(4, __half, 16, 8, 2)
-        DMSGM_CASE(8, __half, 4, 4, 1) DMSGM_CASE(8, __half, 8, 8, 1) DMSGM_CASE(8, __half, 8, 4, 2)
-        DMSGM_CASE(8, __half, 16, 8, 2)
+        DMSGM_SHAPES(1, __half) DMSGM_SHAPES(2, __half) DMSGM_SHAPES(4, __half)
+        DMSGM_SHAPES(8, __half) DMSGM_SHAPES(16, __half)
     }
+#undef DMSGM_SHAPES
 #undef DMSGM_CASE
     return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ helpers
+// Block 1, 2, 4, 8 or 16; W a multiple of 16 (TMA row pitch; so also of
+// the block); any H (a bottom block row may be cut by the frame edge).
 static bool valid_dims(int W, int H, int B) {
-    return W > 0 && H > 0 && (B == 4 || B == 8) && W % 16 == 0 && W % B == 0 && H % B == 0 &&
+    return W > 0 && H > 0 && (B == 1 || B == 2 || B == 4 || B == 8 || B == 16) && W % 16 == 0 &&
            W <= (1 << 20) && H <= (1 << 20);
 }
+
+// Tile height when dmsgm_opts.tile_rows is 0.
+static int default_tile_rows(int B) { return B == 1 ? 8 : B == 2 ? 16 : B == 16 ? 64 : 32; }
 
 static size_t buf_bytes(size_t N, int prec) {
     return state_buf_bytes(N, prec == DMSGM_STATE_FP16 ? 2 : 4);
@@ -372,13 +380,13 @@ const char* dmsgm_version(void) { return "dmsgm-gb300 0.1 (sm_103a)"; }
 
 size_t dmsgm_state_bytes(int W, int H, int B, int prec) {
     if (!valid_dims(W, H, B) || (prec != DMSGM_STATE_FP32 && prec != DMSGM_STATE_FP16)) return 0;
-    const size_t N = size_t(W / B) * (H / B);
+    const size_t N = size_t(W / B) * grid_rows(H, B);
     return 256 + seq_flags_bytes(W, H, B) + 2 * buf_bytes(N, prec);
 }
 
 size_t dmsgm_host_state_bytes(int W, int H, int B, int prec) {
     if (!valid_dims(W, H, B) || (prec != DMSGM_STATE_FP32 && prec != DMSGM_STATE_FP16)) return 0;
-    const size_t N = size_t(W / B) * (H / B);
+    const size_t N = size_t(W / B) * grid_rows(H, B);
     return N * (4 * (prec == DMSGM_STATE_FP16 ? 2 : 4) + 2);
 }
 
@@ -393,8 +401,8 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     *out = nullptr;
     if (!valid_dims(W, H, B))
         return fail(DMSGM_ERR_INVALID_ARG,
-                    "invalid size %dx%d block %d (need block 4 or 8, W%%16==0, W and H "
-                    "multiples of block, <= 2^20)", W, H, B);
+                    "invalid size %dx%d block %d (need block 1, 2, 4, 8 or 16, W%%16==0, "
+                    "W and H <= 2^20)", W, H, B);
     if (!(std::isfinite(ts) && ts > 0) || !(std::isfinite(td) && td > 0))
         return fail(DMSGM_ERR_INVALID_ARG, "theta_s and theta_d must be finite and > 0");
     if (age_max < 1 || age_max > 255) return fail(DMSGM_ERR_INVALID_ARG, "age_max must be in [1, 255]");
@@ -402,9 +410,10 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     if (o) opts = *o;
     if (opts.precision != DMSGM_STATE_FP32 && opts.precision != DMSGM_STATE_FP16)
         return fail(DMSGM_ERR_INVALID_ARG, "unknown precision %d", opts.precision);
-    const int tile_rows = opts.tile_rows ? opts.tile_rows : 32;
-    if (!(tile_rows == 4 * B || tile_rows == 8 * B || tile_rows == 16 * B))
-        return fail(DMSGM_ERR_INVALID_ARG, "tile_rows %d must be 4, 8 or 16 times the block", tile_rows);
+    const int tile_rows = opts.tile_rows ? opts.tile_rows : default_tile_rows(B);
+    if (!(tile_rows == 4 * B || tile_rows == 8 * B || tile_rows == 16 * B) || tile_rows > 256)
+        return fail(DMSGM_ERR_INVALID_ARG, "tile_rows %d must be 4, 8 or 16 times the block and <= 256",
+                    tile_rows);
     const size_t need = dmsgm_state_bytes(W, H, B, opts.precision);
     if (opts.state_mem) {
         if (opts.state_bytes < need)
@@ -416,7 +425,7 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     DMSGM_CUDA_TRY(cudaGetDevice(&dev));
     dmsgm_ctx* h = new (std::nothrow) dmsgm_ctx();
     if (!h) return fail(DMSGM_ERR_OOM, "host allocation failed");
-    h->W = W; h->H = H; h->B = B; h->Gx = W / B; h->Gy = H / B;
+    h->W = W; h->H = H; h->B = B; h->Gx = W / B; h->Gy = grid_rows(H, B);
     h->prec = opts.precision;
     h->age_max = age_max;
     h->theta_s = ts; h->theta_d = td;

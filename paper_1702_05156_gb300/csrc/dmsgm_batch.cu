@@ -103,7 +103,7 @@ __device__ __forceinline__ StreamArgs item_args(const BatchItem& it) {
     a.W = it.W;
     a.H = it.H;
     a.Gx = it.W / B;
-    a.Gy = it.H / B;
+    a.Gy = grid_rows(it.H, B);
     a.mask_words = (it.W + 31) / 32;
     a.first = it.first;
     a.affine = it.affine;
@@ -116,7 +116,7 @@ __device__ __forceinline__ StreamArgs item_args(const BatchItem& it) {
 template <int B, typename T>
 __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origin* orig,
                                          const uint8_t* tile, uint64_t* bar, uint32_t parity) {
-    constexpr int BPL = kLanePx / B;
+    constexpr int BPL = kLaneBlocks<B>;
     const StreamArgs a = item_args(it);
     int tx0, ty0;
     item_origin(it, t, tx0, ty0);
@@ -126,7 +126,7 @@ __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origi
     if (__syncthreads_or(!ok)) return false;
     const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
     Stats st[1][BPL];
-    tile_stats<B, kBatchWarps, 1>(tile, xin, st);
+    tile_stats<B, kBatchWarps, 1>(a, tile, ty0, xin, st);
     float muA[1][BPL], thr[1][BPL];
     tile_update<B, T, kBatchWarps, 1, false>(a, tx0, ty0, pj, st, muA, thr);
     tile_mask<B, kBatchWarps, 1>(a, tile, tx0, ty0, st, muA, thr);
@@ -218,6 +218,9 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
         const dmsgm_ctx* h = hs[i];
         if (h->W > 65535 || h->H > 65535)
             return fail(DMSGM_ERR_INVALID_ARG, "batched streams must be at most 65535 px wide/high");
+        if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0))
+            return fail(DMSGM_ERR_UNSUPPORTED,
+                        "batched streams take blocks 4 and 8 on whole block rows (stream %d)", i);
         BatchItem& it = p.item[i];
         it.frame = frames[i];
         it.mask = masks[i];

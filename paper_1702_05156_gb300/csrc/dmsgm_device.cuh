@@ -26,6 +26,14 @@ constexpr float kVarFloor = 0.1f;    // appendix code: max(var, .1) in the match
 constexpr float kMinWeight = 1e-3f;  // in-grid weight below this: no source
 constexpr int kTileW = 256;          // pixels per tile row (one TMA box row)
 constexpr int kLanePx = 8;           // pixel columns a lane owns (one mask byte per row)
+
+// Blocks a lane owns: 8 / B for B <= 8; for B = 16 a pair of lanes shares one.
+template <int B>
+constexpr int kLaneBlocks = B <= 8 ? 8 / B : 1;
+
+// Grid rows: ceil(H / B); a bottom block row cut by the frame edge holds
+// H - (Gy - 1) * B pixel rows.
+__host__ __device__ __forceinline__ int grid_rows(int H, int B) { return (H + B - 1) / B; }
 // Adding kMagic = 1.5 * 2^23 to a float x with |x| < 2^22 leaves an integer
 // in the low mantissa bits (the ulp there is 1); with a directed rounding
 // mode the sum is kMagic + floor(x) or kMagic + ceil(x), exactly.
@@ -84,7 +92,7 @@ __host__ __device__ __forceinline__ size_t seq_flags_bytes(int W, int H, int B) 
 }
 __host__ __device__ __forceinline__ StateBuf state_buf(char* mem, int W, int H, int B, int s,
                                                       int which) {
-    const size_t N = size_t(W / B) * (H / B);
+    const size_t N = size_t(W / B) * grid_rows(H, B);
     char* p = mem + 256 + seq_flags_bytes(W, H, B) + size_t(which) * state_buf_bytes(N, s);
     StateBuf b;
     b.mu = p; p += align256(N * 2 * s);
@@ -595,6 +603,51 @@ __device__ __forceinline__ Stats block_stats(const uint32_t* w) {
     return st;
 }
 
+// Statistics from an exact byte sum over n pixels and 16-bit-lane min / max
+// words; nfull is the pixel count of an unclipped block (a power of two).
+// NFULL > 0: a whole block of NFULL pixels (a power of two), whose mean
+// (2^23 + s) / NFULL - 2^23 / NFULL is exact in both steps; NFULL = 0: a
+// block cut by the frame edge, n pixels, approximate divide (within 2 ulp).
+template <int NFULL>
+__device__ __forceinline__ Stats stats_from(uint32_t s, uint32_t lo2, uint32_t hi2, int n = 0) {
+    Stats st;
+    const float m = __int_as_float(0x4B000000 | s);   // 2^23 + s, exact: s < 2^23
+    if constexpr (NFULL > 0) st.M = fmaf(m, 1.0f / NFULL, -8388608.0f / NFULL);
+    else st.M = __fdividef(m - 8388608.0f, float(max(n, 1)));
+    const uint32_t mn = __vimin3_u16x2(lo2, lo2 >> 16, lo2) & 0xFFFFu;
+    const uint32_t mx = __vimax3_u16x2(hi2, hi2 >> 16, hi2) & 0xFFFFu;
+    const float2 e = __fadd2_rn(make_float2(__int_as_float(0x4B000000 | mn), __int_as_float(0x4B000000 | mx)),
+                                dup2(-8388608.0f));
+    st.mn = e.x;
+    st.mx = e.y;
+    return st;
+}
+
+// Exact byte sum and 16-bit-lane min / max of words w[0 .. nv) of N; the
+// words from nv on (rows below a cut frame edge) are left out.  With nv = N
+// known at the call the selects fold away.
+template <int N>
+__device__ __forceinline__ void raw_stats(const uint32_t* w, int nv, uint32_t& s, uint32_t& lo,
+                                          uint32_t& hi) {
+    s = 0;
+    lo = 0x00FF00FFu;
+    hi = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const bool in = i < nv;
+        const uint32_t x = in ? w[i] : 0u;
+        s = __dp4a(x, 0x01010101u, s);
+        const uint32_t e = x & 0x00FF00FFu, o = (x >> 8) & 0x00FF00FFu;
+        lo = __vimin3_u16x2(lo, in ? e : 0x00FF00FFu, in ? o : 0x00FF00FFu);
+        hi = __vimax3_u16x2(hi, e, o);   // a left-out word is 0 and never raises the max
+    }
+}
+
+// Byte j of w as an exact float (the byte becomes the low mantissa byte of 2^23 + j).
+__device__ __forceinline__ float byte_f(uint32_t w, int j) {
+    return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7540 + j)) - 8388608.0f;
+}
+
 // ------------------------------------------------------------------ (c)
 // The per-pixel test (I - mu)^2 > thr, evaluated in FP32, is monotone in
 // |I - mu|, so its background set is an interval [lo, hi] of intensities.
@@ -711,31 +764,103 @@ __device__ __forceinline__ uint2 tile_words(const uint8_t* tile, int row, int la
     return *reinterpret_cast<const uint2*>(tile + row * kTileW + kLanePx * lane);
 }
 
+// Pixel rows of the lane's strip row s that lie inside the frame (B unless
+// the frame's bottom edge cuts the block row; 0 past the grid).
+template <int B>
+__device__ __forceinline__ int strip_rows(const StreamArgs& a, int ty0, int s) {
+    return max(0, min(B, a.H - ty0 - B * s));
+}
+
+// Block statistics of the lane's blocks (Sec. 2.2 M_i, and the extremes for
+// V_i), over the pixels inside the frame.
 template <int B, int NW, int RPT>
-__device__ __forceinline__ void tile_stats(const uint8_t* tile, bool xin,
-                                           Stats (&st)[RPT][kLanePx / B]) {
+__device__ __forceinline__ void tile_stats(const StreamArgs& a, const uint8_t* tile, int ty0,
+                                           bool xin, Stats (&st)[RPT][kLaneBlocks<B>]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int s = warp + NW * r;
-        uint32_t lw[B], rw[B];
+        const int vr = strip_rows<B>(a, ty0, s);
+        if constexpr (B == 1) {
+            // one pixel per block: M = min = max = the pixel
+            const uint2 v = xin ? tile_words<B>(tile, s, lane) : make_uint2(0u, 0u);
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const uint2 v = xin ? tile_words<B>(tile, B * s + i, lane) : make_uint2(0u, 0u);
-            lw[i] = v.x;
-            rw[i] = v.y;
-        }
-        if (B == 4) {
-            st[r][0] = block_stats<4>(lw);
-            st[r][kLanePx / B - 1] = block_stats<4>(rw);
+            for (int j = 0; j < 8; ++j) {
+                const float f = byte_f(j < 4 ? v.x : v.y, j & 3);
+                st[r][j] = Stats{f, f, f};
+            }
+        } else if constexpr (B == 2) {
+            // blocks 2h, 2h+1 are bytes (0, 1) and (2, 3) of word h of both rows;
+            // the 16-bit lanes of the min / max words hold one block each
+            uint32_t sum[4] = {0, 0, 0, 0}, lo[2] = {0x00FF00FFu, 0x00FF00FFu}, hi[2] = {0, 0};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i >= vr) break;
+                const uint2 v = xin ? tile_words<B>(tile, B * s + i, lane) : make_uint2(0u, 0u);
+                const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    sum[2 * h] = __dp4a(w[h], 0x00000101u, sum[2 * h]);
+                    sum[2 * h + 1] = __dp4a(w[h], 0x01010000u, sum[2 * h + 1]);
+                    const uint32_t e = w[h] & 0x00FF00FFu, o = (w[h] >> 8) & 0x00FF00FFu;
+                    lo[h] = __vimin3_u16x2(lo[h], e, o);
+                    hi[h] = __vimax3_u16x2(hi[h], e, o);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                // block 2h in the low 16-bit lane, block 2h+1 in the high one
+                const uint32_t l0 = lo[h] | 0x00FF0000u, h0 = hi[h] & 0xFFFFu;
+                const uint32_t l1 = (lo[h] >> 16) | 0x00FF0000u, h1 = hi[h] >> 16;
+                if (vr == 2) {
+                    st[r][2 * h] = stats_from<4>(sum[2 * h], l0, h0);
+                    st[r][2 * h + 1] = stats_from<4>(sum[2 * h + 1], l1, h1);
+                } else {
+                    st[r][2 * h] = stats_from<0>(sum[2 * h], l0, h0, 2 * vr);
+                    st[r][2 * h + 1] = stats_from<0>(sum[2 * h + 1], l1, h1, 2 * vr);
+                }
+            }
         } else {
-            uint32_t all[2 * B];
+            uint32_t lw[B], rw[B];
 #pragma unroll
             for (int i = 0; i < B; ++i) {
-                all[2 * i] = lw[i];
-                all[2 * i + 1] = rw[i];
+                const uint2 v = xin ? tile_words<B>(tile, B * s + i, lane) : make_uint2(0u, 0u);
+                lw[i] = v.x;
+                rw[i] = v.y;
             }
-            st[r][0] = block_stats<2 * B>(all);
+            if constexpr (B == 4) {
+                uint32_t sl, ll, hl, sr, lr, hr;
+                if (vr == B) {
+                    raw_stats<4>(lw, 4, sl, ll, hl);
+                    raw_stats<4>(rw, 4, sr, lr, hr);
+                    st[r][0] = stats_from<16>(sl, ll, hl);
+                    st[r][1] = stats_from<16>(sr, lr, hr);
+                } else {   // the bottom block row, cut by the frame edge
+                    raw_stats<4>(lw, vr, sl, ll, hl);
+                    raw_stats<4>(rw, vr, sr, lr, hr);
+                    st[r][0] = stats_from<0>(sl, ll, hl, 4 * vr);
+                    st[r][1] = stats_from<0>(sr, lr, hr, 4 * vr);
+                }
+            } else {
+                // B = 8: the lane's 8 columns are the whole block; B = 16: half
+                // of it, and the lane pair (l, l ^ 1) combines its halves
+                uint32_t all[2 * B];
+#pragma unroll
+                for (int i = 0; i < B; ++i) {
+                    all[2 * i] = lw[i];
+                    all[2 * i + 1] = rw[i];
+                }
+                uint32_t sm, lo, hi;
+                const bool whole = vr == B;   // warp-uniform
+                if (whole) raw_stats<2 * B>(all, 2 * B, sm, lo, hi);
+                else raw_stats<2 * B>(all, 2 * vr, sm, lo, hi);
+                if constexpr (B == 16) {
+                    sm += __shfl_xor_sync(0xffffffffu, sm, 1);
+                    lo = __vimin3_u16x2(lo, __shfl_xor_sync(0xffffffffu, lo, 1), lo);
+                    hi = __vimax3_u16x2(hi, __shfl_xor_sync(0xffffffffu, hi, 1), hi);
+                }
+                st[r][0] = whole ? stats_from<B * B>(sm, lo, hi) : stats_from<0>(sm, lo, hi, B * vr);
+            }
         }
     }
 }
@@ -743,8 +868,8 @@ __device__ __forceinline__ void tile_stats(const uint8_t* tile, bool xin,
 template <int B, int NW, int RPT>
 __device__ __forceinline__ void tile_project(const StreamArgs& a, const Coef& k, int tx0,
                                              int ty0, const Origin* orig,
-                                             Proj (&pj)[RPT][kLanePx / B]) {
-    constexpr int BPL = kLanePx / B;
+                                             Proj (&pj)[RPT][kLaneBlocks<B>]) {
+    constexpr int BPL = kLaneBlocks<B>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
     const int bx = x / B;
@@ -766,12 +891,12 @@ __device__ __forceinline__ void tile_project(const StreamArgs& a, const Coef& k,
 // theta_d * var_A.
 template <int B, typename T, int NW, int RPT, typename GatherFn>
 __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, int ty0,
-                                                 const Proj (&pj)[RPT][kLanePx / B],
-                                                 const Stats (&st)[RPT][kLanePx / B],
-                                                 float (&muA)[RPT][kLanePx / B],
-                                                 float (&thr)[RPT][kLanePx / B],
+                                                 const Proj (&pj)[RPT][kLaneBlocks<B>],
+                                                 const Stats (&st)[RPT][kLaneBlocks<B>],
+                                                 float (&muA)[RPT][kLaneBlocks<B>],
+                                                 float (&thr)[RPT][kLaneBlocks<B>],
                                                  const GatherFn& gather_fn) {
-    constexpr int BPL = kLanePx / B;
+    constexpr int BPL = kLaneBlocks<B>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
     const bool xin = x < a.W;
@@ -792,9 +917,15 @@ __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, i
 #pragma unroll
         for (int j = 0; j < BPL; ++j) dual_mode_step(c[j], st[r][j], a);
         if (xin && by < a.Gy) {
-            const int k = by * a.Gx + bx;
-            if (B == 4) store_pair<T>(a, k, c[0], c[BPL - 1]);
-            else store_block<T>(a, k, c[0]);
+            const int k = by * a.Gx + bx;   // even for B <= 4: pairs are 16-byte aligned
+            if constexpr (B <= 4) {
+#pragma unroll
+                for (int j = 0; j < BPL; j += 2) store_pair<T>(a, k + j, c[j], c[j + 1]);
+            } else if constexpr (B == 8) {
+                store_block<T>(a, k, c[0]);
+            } else {
+                if ((lane & 1) == 0) store_block<T>(a, k, c[0]);   // one lane of the pair
+            }
         }
 #pragma unroll
         for (int j = 0; j < BPL; ++j) {
@@ -806,10 +937,10 @@ __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, i
 
 template <int B, typename T, int NW, int RPT, bool COH>
 __device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty0,
-                                            const Proj (&pj)[RPT][kLanePx / B],
-                                            const Stats (&st)[RPT][kLanePx / B],
-                                            float (&muA)[RPT][kLanePx / B],
-                                            float (&thr)[RPT][kLanePx / B]) {
+                                            const Proj (&pj)[RPT][kLaneBlocks<B>],
+                                            const Stats (&st)[RPT][kLaneBlocks<B>],
+                                            float (&muA)[RPT][kLaneBlocks<B>],
+                                            float (&thr)[RPT][kLaneBlocks<B>]) {
     const GlobalSrc<T, COH> src = global_src<T, COH>(a);
     tile_update_with<B, T, NW, RPT>(a, tx0, ty0, pj, st, muA, thr,
                                     [&](const Proj& p) { return gather(a, p, src); });
@@ -827,13 +958,14 @@ __device__ __forceinline__ bool block_all_bg(const Stats& st, float mu, float th
 // Mask bytes of the lane's pixel rows from the final apparent models.  A
 // warp whose blocks are all background writes zero bytes without the
 // per-pixel test.  Lanes past the frame's right edge but inside the last
-// mask word write zeros, so the padding bits are defined.
+// mask word write zeros, so the padding bits are defined; rows past the
+// frame's bottom edge are not written.
 template <int B, int NW, int RPT>
 __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* tile, int tx0,
-                                          int ty0, const Stats (&st)[RPT][kLanePx / B],
-                                          const float (&muA)[RPT][kLanePx / B],
-                                          const float (&thr)[RPT][kLanePx / B]) {
-    constexpr int BPL = kLanePx / B;
+                                          int ty0, const Stats (&st)[RPT][kLaneBlocks<B>],
+                                          const float (&muA)[RPT][kLaneBlocks<B>],
+                                          const float (&thr)[RPT][kLaneBlocks<B>]) {
+    constexpr int BPL = kLaneBlocks<B>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
     const bool active = x < a.mask_words * 32;      // owns a byte of the mask row
@@ -844,35 +976,59 @@ __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* ti
     for (int r = 0; r < RPT; ++r) {
         const int s = warp + NW * r;
         if (ty0 / B + s >= a.Gy) break;   // warp-uniform
+        const int vr = strip_rows<B>(a, ty0, s);
         uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
         bool flat = true;   // lanes outside the frame count as flat
         if (xin) {
 #pragma unroll
             for (int j = 0; j < BPL; ++j) flat = flat && block_all_bg(st[r][j], muA[r][j], thr[r][j]);
         }
-        if (__all_sync(0xffffffffu, flat) || !xin) {
-            if (active) {
+        // rows of this strip to write: all B (the loops unroll without a
+        // guard), or the rows above a frame edge that cuts the block row
+        auto rows = [&](auto body) {
+            if (vr == B) {
 #pragma unroll
-                for (int i = 0; i < B; ++i) m[i * mrow] = 0;
+                for (int i = 0; i < B; ++i) body(i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (i < vr) body(i);
             }
+        };
+        if (__all_sync(0xffffffffu, flat) || !xin || flat) {
+            if (active) rows([&](int i) { m[i * mrow] = 0; });
             continue;
         }
-        if (flat) {
+        if constexpr (B <= 2) {
+            // small blocks: the per-pixel FP32 test itself, two pixels per
+            // packed operation; pixel p belongs to block p / B
+            rows([&](int i) {
+                const uint2 v = tile_words<B>(tile, B * s + i, lane);
+                uint32_t byte = 0;
 #pragma unroll
-            for (int i = 0; i < B; ++i) m[i * mrow] = 0;
-            continue;
-        }
-        Thresh tl, tr;
-        if (BPL == 1) {
-            tl = tr = bg_interval(muA[r][0], thr[r][0]);
+                for (int p = 0; p < 8; p += 2) {
+                    const uint32_t w = p < 4 ? v.x : v.y;
+                    const int j0 = p / B, j1 = (p + 1) / B;
+                    const float2 d = __fadd2_rn(make_float2(byte_f(w, p & 3), byte_f(w, (p + 1) & 3)),
+                                                make_float2(-muA[r][j0], -muA[r][j1]));
+                    const float2 q = __fmul2_rn(d, d);
+                    byte |= (q.x > thr[r][j0] ? 1u : 0u) << p;
+                    byte |= (q.y > thr[r][j1] ? 1u : 0u) << (p + 1);
+                }
+                m[i * mrow] = uint8_t(byte);
+            });
         } else {
-            bg_interval2(make_float2(muA[r][0], muA[r][BPL - 1]),
-                         make_float2(thr[r][0], thr[r][BPL - 1]), tl, tr);
-        }
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const uint2 v = tile_words<B>(tile, B * s + i, lane);
-            m[i * mrow] = uint8_t(mask_byte(fg_bits(v.x, tl), fg_bits(v.y, tr)));
+            Thresh tl, tr;
+            if (BPL == 1) {
+                tl = tr = bg_interval(muA[r][0], thr[r][0]);
+            } else {
+                bg_interval2(make_float2(muA[r][0], muA[r][BPL - 1]),
+                             make_float2(thr[r][0], thr[r][BPL - 1]), tl, tr);
+            }
+            rows([&](int i) {
+                const uint2 v = tile_words<B>(tile, B * s + i, lane);
+                m[i * mrow] = uint8_t(mask_byte(fg_bits(v.x, tl), fg_bits(v.y, tr)));
+            });
         }
     }
 }

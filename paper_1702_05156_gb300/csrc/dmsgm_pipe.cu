@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
                       const Coef k, int tiles_x, int n_tiles, int* status) {
     using G = PipeGeom<B, NW>;
     using S = PipeSmem<B, T, NW>;
-    constexpr int BPL = kLanePx / B;
+    constexpr int BPL = kLaneBlocks<B>;
     constexpr uint32_t kFrameBytes = G::kTileH * kTileW;
     constexpr uint32_t kStateBytes = G::kBoxH * G::kBoxW * (2 * sizeof(Pair<T>) + 2);
     extern __shared__ __align__(128) uint8_t dsm[];
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         return;
     }
     ph ^= 1;
-    tile_stats<B, NW, 1>(sm.frame[0], tx0 + kLanePx * lane < a.W, st);
+    tile_stats<B, NW, 1>(a, sm.frame[0], ty0, tx0 + kLanePx * lane < a.W, st);
     tile_project<B, NW, 1>(a, k, tx0, ty0, sm.orig[0], pj);
     pdl_wait();
     pdl_launch_dependents();
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         }
         ph ^= 1u << (s ^ 1);
         tile_xy(nxt, tx0, ty0);
-        tile_stats<B, NW, 1>(sm.frame[s ^ 1], tx0 + kLanePx * lane < a.W, st);
+        tile_stats<B, NW, 1>(a, sm.frame[s ^ 1], ty0, tx0 + kLanePx * lane < a.W, st);
         tile_project<B, NW, 1>(a, k, tx0, ty0, sm.orig[s ^ 1], pj);
     }
 }
@@ -310,6 +310,7 @@ int launch_pipe(dmsgm_ctx* h, const CUtensorMap& fmap, const StreamArgs& a, cons
                 cudaStream_t s, bool automatic, bool* launched) {
     *launched = false;
     if (!a.first && !a.affine) return DMSGM_OK;   // general projective form: per-tile kernel
+    if (h->H % h->B) return DMSGM_OK;              // a cut bottom block row: per-tile kernel
     const int q = h->tile_rows / h->B;
     const bool f16 = h->prec == DMSGM_STATE_FP16;
 #define DMSGM_PIPE(BB, TT, NWW) return launch_pipe_t<BB, TT, NWW>(h, fmap, a, c, s, automatic, launched);

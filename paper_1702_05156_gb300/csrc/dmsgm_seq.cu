@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
     dmsgm_seq_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SeqParams p) {
     constexpr int STRIPS = NW * RPT;
     constexpr int TILE_H = STRIPS * B;
-    constexpr int BPL = kLanePx / B;
+    constexpr int BPL = kLaneBlocks<B>;
     static_assert(TILE_H <= 256, "TMA box rows");
     extern __shared__ __align__(128) uint8_t dyn_smem[];   // two pixel stages
     uint8_t* tile[2] = {dyn_smem, dyn_smem + TILE_H * kTileW};
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
         // the frame's block statistics and back-projections need no other tile
         Stats sts[RPT][BPL];
         Proj pj[RPT][BPL];
-        tile_stats<B, NW, RPT>(tile[st], ok && xin, sts);
+        tile_stats<B, NW, RPT>(a, tile[st], ty0, ok && xin, sts);
         tile_project<B, NW, RPT>(a, p.coef[k], tx0, ty0, orig[st], pj);
         // wait until every neighbour tile has published frame k-1
         if (k > 0) {
@@ -239,6 +239,8 @@ static int capacity(const dmsgm_ctx* h, int nw, int rpt) {
 // most that fit the GPU at all; {0, 0} if none fits.
 static SeqShape pick_shape(const dmsgm_ctx* h, int sms) {
     static const SeqShape shapes[] = {{8, 1}, {16, 1}, {16, 2}, {16, 4}};
+    // built for blocks 4 and 8 on whole block rows
+    if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0)) return SeqShape{0, 0};
     if (h->seq_tile_rows) {   // asked for: use it if the tiles fit the GPU at once
         for (const SeqShape& sh : shapes) {
             if (sh.nw * sh.rpt * h->B != h->seq_tile_rows) continue;
@@ -456,7 +458,7 @@ extern "C" int dmsgm_process_seq_noalloc(int W, int H, int B, int precision, flo
     if (rc) return rc;
     // a handle description on the stack over the caller's memory
     dmsgm_ctx h{};
-    h.W = W; h.H = H; h.B = B; h.Gx = W / B; h.Gy = H / B;
+    h.W = W; h.H = H; h.B = B; h.Gx = W / B; h.Gy = grid_rows(H, B);
     h.prec = precision; h.age_max = age_max;
     h.theta_s = theta_s; h.theta_d = theta_d;
     h.device = dev;
@@ -472,6 +474,8 @@ extern "C" int dmsgm_process_seq_noalloc(int W, int H, int B, int precision, flo
     // the counters this launch needs must fit the array
     int sms = 0;
     DMSGM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (!((B == 4 || B == 8) && H % B == 0))
+        return fail(DMSGM_ERR_UNSUPPORTED, "the multi-frame kernel takes blocks 4 and 8 on whole block rows");
     const SeqShape sh = pick_shape(&h, sms);
     if (!sh.nw)
         return fail(DMSGM_ERR_UNSUPPORTED, "the %dx%d frame's tiles cannot all be resident on this GPU", W, H);

@@ -119,13 +119,14 @@ def compare_step(prev: dict | None, got: dict, got_mask_bits: np.ndarray, frame:
             idx = np.argwhere(bad)[0]
             r.notes.append(f"{name}{tuple(idx)} gpu={g[tuple(idx)]!r} oracle={o[tuple(idx)]!r}")
     # mask
-    pix_keep = np.kron(keep, np.ones((block, block), bool))
+    hh, ww = frame.shape   # a block row cut by the frame edge: crop the expansion
+    pix_keep = np.kron(keep, np.ones((block, block), bool))[:hh, :ww]
     mism = (got_mask_bits != omask) & pix_keep
     r.pixels = int(pix_keep.sum())
     r.mask_mismatch = int(mism.sum())
     if r.mask_mismatch:
-        muA = np.kron(ost.muA, np.ones((block, block)))
-        varA = np.kron(ost.varA, np.ones((block, block)))
+        muA = np.kron(ost.muA, np.ones((block, block)))[:hh, :ww]
+        varA = np.kron(ost.varA, np.ones((block, block)))[:hh, :ww]
         f = frame.astype(np.float64)
         thr = theta_d * varA
         band = np.abs((f - muA) ** 2 - thr) <= 1e-4 * thr

@@ -50,14 +50,21 @@ def test_version_and_sizes(L):
     assert L.dmsgm_host_state_bytes(3840, 2160, 8, 1) == 480 * 270 * 10
     assert L.dmsgm_state_bytes(100, 100, 4, 0) == 0       # W % 16 != 0
     assert L.dmsgm_state_bytes(320, 240, 5, 0) == 0       # block 5
-    assert L.dmsgm_state_bytes(320, 242, 4, 0) == 0       # H % B != 0
+    assert L.dmsgm_state_bytes(320, 240, 32, 0) == 0      # block 32
     assert L.dmsgm_state_bytes(320, 240, 4, 7) == 0       # precision
+    # a bottom block row cut by the frame edge counts as a block row:
+    # 320 x 242 at B = 4 is 80 x 61 blocks; block 1 is one block per pixel
+    assert L.dmsgm_host_state_bytes(320, 242, 4, 0) == 80 * 61 * 18
+    assert L.dmsgm_host_state_bytes(320, 250, 16, 1) == 20 * 16 * 10
+    assert L.dmsgm_host_state_bytes(64, 3, 1, 0) == 64 * 3 * 18
+    assert L.dmsgm_host_state_bytes(64, 5, 2, 0) == 32 * 3 * 18
 
 
 @pytest.mark.parametrize("args", [
     (100, 240, 4, 2.0, 4.0, 30),     # W % 16
     (320, 240, 5, 2.0, 4.0, 30),     # block
-    (320, 244, 8, 2.0, 4.0, 30),     # H % B
+    (320, 240, 32, 2.0, 4.0, 30),    # block
+    (320, 240, 0, 2.0, 4.0, 30),     # block
     (0, 240, 4, 2.0, 4.0, 30),
     (320, 240, 4, 0.0, 4.0, 30),     # theta_s
     (320, 240, 4, 2.0, float("nan"), 30),
