@@ -42,7 +42,10 @@
  *      blocks with the nominal geometry (centres, back-projected squares,
  *      mixing); a block cut by the right or bottom edge takes M_i, its
  *      extremes and V_i over its pixels inside the frame, and only those
- *      pixels get mask values.
+ *      pixels get mask values;
+ *   R12 (option, off by default) Yi et al.'s mixture variance: the mixed
+ *      variance also carries the spread of the mixed means,
+ *      var~ = sum_k w_k (var_k + (mu_k - mu~)^2) / sum_k w_k.
  *
  * Pixel (x, y) has its centre at (x + 0.5, y + 0.5).  Block (bx, by) covers
  * pixels [bx*B, (bx+1)*B) x [by*B, (by+1)*B) clipped to the frame; its centre
@@ -128,10 +131,11 @@ static model_t sgm_reset(double M)
  * diag      NULL or Gx*Gy*ORACLE_DIAG doubles.
  *
  * Returns 0, or -1 on invalid sizes.  Inputs and outputs must not alias.
- * The grid is Gx x Gy = ceil(W/B) x ceil(H/B) blocks (R11).
+ * The grid is Gx x Gy = ceil(W/B) x ceil(H/B) blocks (R11).  mix_spread
+ * (oracle_step_ex only) switches on R12.
  */
-int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max,
-                int first, const unsigned char* frame, const double* Hm,
+int oracle_step_ex(int W, int H, int B, double theta_s, double theta_d, int age_max,
+                   int mix_spread, int first, const unsigned char* frame, const double* Hm,
                 const double* muA_in, const double* varA_in, const int* ageA_in,
                 const double* muC_in, const double* varC_in, const int* ageC_in,
                 double* muA_out, double* varA_out, int* ageA_out,
@@ -201,7 +205,20 @@ int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max
                             sC_age += wgt * ageC_in[n];
                         }
                     if (!(wsum >= MIN_WEIGHT)) nosrc = 1;
-                    else {
+                    else if (mix_spread) {
+                        /* R12: second pass, the spread of the mixed means */
+                        const double mA = sA_mu / wsum, mC = sC_mu / wsum;
+                        for (int dj = 0; dj < 2; ++dj)
+                            for (int di = 0; di < 2; ++di) {
+                                const double ii = i0 + di, jj = j0 + dj;
+                                const double wgt = (di ? fx : 1.0 - fx) * (dj ? fy : 1.0 - fy);
+                                if (ii < 0 || ii >= Gx || jj < 0 || jj >= Gy) continue;
+                                const size_t n = (size_t)jj * Gx + (size_t)ii;
+                                sA_var += wgt * (muA_in[n] - mA) * (muA_in[n] - mA);
+                                sC_var += wgt * (muC_in[n] - mC) * (muC_in[n] - mC);
+                            }
+                    }
+                    if (!nosrc) {
                         A.mu = sA_mu / wsum;
                         A.var = sA_var / wsum;
                         xageA = sA_age / wsum;
@@ -268,6 +285,20 @@ int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max
     return 0;
 }
 
+int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max,
+                int first, const unsigned char* frame, const double* Hm,
+                const double* muA_in, const double* varA_in, const int* ageA_in,
+                const double* muC_in, const double* varC_in, const int* ageC_in,
+                double* muA_out, double* varA_out, int* ageA_out,
+                double* muC_out, double* varC_out, int* ageC_out,
+                unsigned char* mask_out, double* diag)
+{
+    return oracle_step_ex(W, H, B, theta_s, theta_d, age_max, 0, first, frame, Hm,
+                          muA_in, varA_in, ageA_in, muC_in, varC_in, ageC_in,
+                          muA_out, varA_out, ageA_out, muC_out, varC_out, ageC_out,
+                          mask_out, diag);
+}
+
 /*
  * oracle_run -- T frames in a row, free-running, from an empty state.
  * frames: T*W*H bytes; Hs: T*9 doubles (Hs[0] is ignored: first frame).
@@ -276,7 +307,8 @@ int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max
  * the caller passes in (st_* ping buffers) so that this file allocates
  * nothing.
  */
-int oracle_run(int W, int H, int B, double theta_s, double theta_d, int age_max, int T,
+int oracle_run_ex(int W, int H, int B, double theta_s, double theta_d, int age_max,
+                  int mix_spread, int T,
                const unsigned char* frames, const double* Hs,
                double* muA, double* varA, int* ageA,
                double* muC, double* varC, int* ageC,
@@ -288,7 +320,7 @@ int oracle_run(int W, int H, int B, double theta_s, double theta_d, int age_max,
     const size_t npx = (size_t)W * H;
     const size_t nb = (size_t)((W + B - 1) / B) * (size_t)((H + B - 1) / B);
     for (int t = 0; t < T; ++t) {
-        int rc = oracle_step(W, H, B, theta_s, theta_d, age_max, t == 0,
+        int rc = oracle_step_ex(W, H, B, theta_s, theta_d, age_max, mix_spread, t == 0,
                              frames + (size_t)t * npx, Hs + (size_t)t * 9,
                              muA, varA, ageA, muC, varC, ageC,
                              tmu_A, tvar_A, tage_A, tmu_C, tvar_C, tage_C,
@@ -302,4 +334,17 @@ int oracle_run(int W, int H, int B, double theta_s, double theta_d, int age_max,
         memcpy(ageC, tage_C, nb * sizeof(int));
     }
     return 0;
+}
+
+int oracle_run(int W, int H, int B, double theta_s, double theta_d, int age_max, int T,
+               const unsigned char* frames, const double* Hs,
+               double* muA, double* varA, int* ageA,
+               double* muC, double* varC, int* ageC,
+               double* tmu_A, double* tvar_A, int* tage_A,
+               double* tmu_C, double* tvar_C, int* tage_C,
+               unsigned char* masks)
+{
+    return oracle_run_ex(W, H, B, theta_s, theta_d, age_max, 0, T, frames, Hs,
+                         muA, varA, ageA, muC, varC, ageC,
+                         tmu_A, tvar_A, tage_A, tmu_C, tvar_C, tage_C, masks);
 }

@@ -55,6 +55,12 @@ def _load():
             lib.oracle_run.restype = ctypes.c_int
             lib.oracle_run.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
                 ctypes.c_int, ctypes.c_int] + [P] * 15
+            lib.oracle_step_ex.restype = ctypes.c_int
+            lib.oracle_step_ex.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
+                ctypes.c_int] * 3 + [P] * 16
+            lib.oracle_run_ex.restype = ctypes.c_int
+            lib.oracle_run_ex.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
+                ctypes.c_int] * 3 + [P] * 15
             lib.oracle_diag_stride.restype = ctypes.c_int
             assert lib.oracle_diag_stride() == len(DIAG)
             _lib = lib
@@ -90,7 +96,7 @@ def _ptr(a: np.ndarray):
 
 def oracle_step(frame: np.ndarray, H: np.ndarray, prev: OracleState | None, *,
                 block: int, theta_s: float = 2.0, theta_d: float = 4.0,
-                age_max: int = 30, diag: bool = False):
+                age_max: int = 30, diag: bool = False, mix_spread: bool = False):
     """One frame.  ``prev=None`` means the first frame of a stream.
 
     Returns ``(state, mask)`` or ``(state, mask, diag)``; ``mask`` is uint8
@@ -109,8 +115,9 @@ def oracle_step(frame: np.ndarray, H: np.ndarray, prev: OracleState | None, *,
     nxt = OracleState.empty(gy, gx)
     mask = np.zeros((h, w), dtype=np.uint8)
     dg = np.zeros((gy, gx, len(DIAG)), dtype=np.float64) if diag else None
-    rc = lib.oracle_step(
-        w, h, block, float(theta_s), float(theta_d), int(age_max), int(first),
+    rc = lib.oracle_step_ex(
+        w, h, block, float(theta_s), float(theta_d), int(age_max), int(bool(mix_spread)),
+        int(first),
         _ptr(frame), _ptr(Hm),
         _ptr(prev.muA), _ptr(prev.varA), _ptr(prev.ageA),
         _ptr(prev.muC), _ptr(prev.varC), _ptr(prev.ageC),
@@ -123,7 +130,8 @@ def oracle_step(frame: np.ndarray, H: np.ndarray, prev: OracleState | None, *,
 
 
 def oracle_run(frames: np.ndarray, Hs: np.ndarray, *, block: int,
-               theta_s: float = 2.0, theta_d: float = 4.0, age_max: int = 30):
+               theta_s: float = 2.0, theta_d: float = 4.0, age_max: int = 30,
+               mix_spread: bool = False):
     """T frames free-running from an empty state; returns (state, masks[T,H,W])."""
     lib = _load()
     frames = np.ascontiguousarray(frames, dtype=np.uint8)
@@ -133,8 +141,8 @@ def oracle_run(frames: np.ndarray, Hs: np.ndarray, *, block: int,
     st = OracleState.empty(gy, gx)
     tmp = OracleState.empty(gy, gx)
     masks = np.zeros((T, h, w), dtype=np.uint8)
-    rc = lib.oracle_run(
-        w, h, block, float(theta_s), float(theta_d), int(age_max), T,
+    rc = lib.oracle_run_ex(
+        w, h, block, float(theta_s), float(theta_d), int(age_max), int(bool(mix_spread)), T,
         _ptr(frames), _ptr(Hs),
         _ptr(st.muA), _ptr(st.varA), _ptr(st.ageA),
         _ptr(st.muC), _ptr(st.varC), _ptr(st.ageC),

@@ -490,3 +490,61 @@ def test_clipped_block_variance_sees_only_its_pixels():
         np.testing.assert_allclose(st.muA[:, 2], 77, rtol=0, atol=1e-12)
         np.testing.assert_allclose(st.varA[:, 2], 255.0 / n, rtol=1e-12)
         assert (st.ageA[:, 2] == n).all() and mask[:, 8:].sum() == 0
+
+
+# ---------------------------------------------------------------- mixture spread (R12)
+def test_spread_half_half_hand_value():
+    """A half-block shift mixes two blocks with weights 1/2: the compensated
+    variance is the mean of their variances plus the spread of their means,
+    (v1 + v2)/2 + ((m1 - m2)/2)^2 (the variance of an equal two-component
+    mixture), and the mean is unchanged by the option."""
+    B, gx, gy = 4, 3, 1
+    prev = state_from_arrays(np.array([[10.0, 50.0, 90.0]]), np.array([[4.0, 9.0, 16.0]]),
+                             np.full((1, 3), 5), np.array([[20.0, 30.0, 40.0]]),
+                             np.array([[1.0, 1.0, 1.0]]), np.full((1, 3), 2))
+    img = np.full((gy * B, gx * B), 60, np.uint8)
+    Hm = translation(B / 2, 0)   # block 1 draws half from block 0, half from block 1
+    _, _, d0 = oracle_step(img, Hm, prev, block=B, diag=True)
+    _, _, d1 = oracle_step(img, Hm, prev, block=B, diag=True, mix_spread=True)
+    assert d0[0, 1, DIAG["MU_A"]] == d1[0, 1, DIAG["MU_A"]] == 30.0
+    assert d0[0, 1, DIAG["VAR_A"]] == (4.0 + 9.0) / 2
+    assert d1[0, 1, DIAG["VAR_A"]] == (4.0 + 9.0) / 2 + 20.0 ** 2
+    assert d1[0, 1, DIAG["VAR_C"]] == 1.0 + 5.0 ** 2
+
+
+@pytest.mark.parametrize("k,l", [(1, 0), (-2, 1), (0, 0)])
+def test_spread_vanishes_on_whole_block_shifts(k, l):
+    """All weight on one block: no spread, so the option changes nothing."""
+    gx, gy, B = 9, 6, 4
+    prev = state_from_arrays(*random_state(gy, gx, 30, seed=3))
+    rng = np.random.default_rng(7)
+    img = rng.integers(0, 256, (gy * B, gx * B), dtype=np.uint8)
+    a = oracle_step(img, translation(k * B, l * B), prev, block=B)
+    b = oracle_step(img, translation(k * B, l * B), prev, block=B, mix_spread=True)
+    for n in ("muA", "varA", "ageA", "muC", "varC", "ageC"):
+        assert np.array_equal(getattr(a[0], n), getattr(b[0], n)), n
+    assert np.array_equal(a[1], b[1])
+
+
+def test_spread_is_the_mixture_variance_by_sampling_weights():
+    """For a fractional shift the spread term equals the weighted variance
+    of the four source means about their weighted mean, computed here by
+    brute force over a 1000x1000 sub-cell count of the overlap (the same
+    counting as the weight pin), so no formula of the oracle is retyped."""
+    B = 4
+    prev = state_from_arrays(np.array([[10.0, 70.0], [40.0, 100.0]]), np.zeros((2, 2)),
+                             np.full((2, 2), 3), np.zeros((2, 2)), np.zeros((2, 2)),
+                             np.full((2, 2), 1))
+    img = np.zeros((8, 8), np.uint8)
+    dx, dy = 0.3, 0.8                       # block units
+    Hm = translation(-dx * B, -dy * B)      # block (0, 0) back-projects to [dx, dx+1) x [dy, dy+1)
+    _, _, d = oracle_step(img, Hm, prev, block=B, diag=True, mix_spread=True)
+    # brute force: the back-projected square of block (0, 0) covers [dx, dx+1) x [dy, dy+1)
+    n = 1000
+    c = (np.arange(n) + 0.5) / n
+    xs, ys = dx + c, dy + c
+    ix, iy = np.floor(xs).astype(int), np.floor(ys).astype(int)
+    vals = prev.muA[np.clip(iy, 0, 1)[:, None], np.clip(ix, 0, 1)[None, :]]
+    inside = ((iy < 2)[:, None] & (ix < 2)[None, :])
+    v = vals[inside]
+    np.testing.assert_allclose(d[0, 0, DIAG["VAR_A"]], v.var(), rtol=1e-3)
