@@ -103,6 +103,11 @@ typedef struct {
                            general projective form, and sizes whose state
                            rows are not 16-byte multiples, use the per-tile
                            kernel).  Results are identical.                  */
+    int mix_spread;     /* 1: Yi et al.'s mixture variance -- the compensated
+                           variance also carries the spread of the mixed
+                           means, sum_k w_k (var_k + (mu_k - mu~)^2) / sum w;
+                           0 (default): the variances alone (Sec. 2.4).  Not
+                           available through dmsgm_process_seq_noalloc.      */
 } dmsgm_opts;
 
 enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1, DMSGM_KERNEL_PIPE = 2 };
@@ -122,6 +127,7 @@ typedef struct {
     int last_kernel;             /* kernel of the last dmsgm_process step:
                                     DMSGM_KERNEL_TILE or DMSGM_KERNEL_PIPE;
                                     0 before the first                        */
+    int mix_spread;              /* dmsgm_opts.mix_spread in use              */
 } dmsgm_info;
 
 /* Device bytes a handle needs for its state: a 256-byte control block, one

@@ -42,7 +42,7 @@ class dmsgm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("state_mem", ctypes.c_void_p),
                 ("state_bytes", ctypes.c_size_t), ("tile_rows", ctypes.c_int),
                 ("use_pdl", ctypes.c_int), ("seq_tile_rows", ctypes.c_int),
-                ("kernel", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("mix_spread", ctypes.c_int)]
 
 
 class dmsgm_batch_opts(ctypes.Structure):
@@ -57,7 +57,7 @@ class dmsgm_info(ctypes.Structure):
                 ("parity", ctypes.c_int), ("frames", ctypes.c_ulonglong),
                 ("state_bytes", ctypes.c_size_t), ("host_state_bytes", ctypes.c_size_t),
                 ("tile_rows", ctypes.c_int), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("last_kernel", ctypes.c_int)]
+                ("last_kernel", ctypes.c_int), ("mix_spread", ctypes.c_int)]
 
 
 class DmsgmError(RuntimeError):

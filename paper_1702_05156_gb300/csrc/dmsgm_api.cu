@@ -29,55 +29,6 @@ int fail(int code, const char* fmt, ...) {
 void clear_error() { g_err[0] = 0; }
 
 // ------------------------------------------------------------------ kernel
-constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // 2 s: only a broken copy gets here
-
-// 8x8 blocks, one strip row per warp: 32 registers (full occupancy); two
-// rows per warp: 64.  4x4 blocks keep the compiler's choice.
-template <int B, int NW, int RPT>
-constexpr int step_min_blocks() { return B == 8 ? (RPT == 1 ? 64 : 32) / NW : 1; }
-
-template <int B, typename T, int NW, int RPT>
-__global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
-    dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, const Coef k,
-                      int* status) {
-    constexpr int STRIPS = NW * RPT;          // strip rows per tile
-    constexpr int TILE_H = STRIPS * B;
-    __shared__ __align__(128) uint8_t tile[TILE_H * kTileW];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ Origin orig[2 * STRIPS];
-    const int tx0 = blockIdx.x * kTileW;
-    const int ty0 = blockIdx.y * TILE_H;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        mbar_arrive_expect_tx(&bar, TILE_H * kTileW);
-        tma_load_2d(tile, &tmap, tx0, ty0, &bar);
-    }
-    fill_origins<B>(a, k, tx0, ty0, STRIPS, orig);
-    __syncthreads();
-    const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
-    if (__syncthreads_or(!ok)) {
-        // report, give the copy one more bounded chance to land, and leave
-        if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
-        mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
-        return;
-    }
-    // The pixels, their block statistics and the back-projections do not
-    // depend on the previous frame's kernel, so they run before its end;
-    // the state does.
-    constexpr int BPL = kLaneBlocks<B>;
-    const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
-    Stats st[RPT][BPL];
-    Proj pj[RPT][BPL];
-    tile_stats<B, NW, RPT>(a, tile, ty0, xin, st);
-    tile_project<B, NW, RPT>(a, k, tx0, ty0, orig, pj);
-    pdl_wait();
-    pdl_launch_dependents();
-    float muA[RPT][BPL], thr[RPT][BPL];
-    tile_update<B, T, NW, RPT, false>(a, tx0, ty0, pj, st, muA, thr);
-    tile_mask<B, NW, RPT>(a, tile, tx0, ty0, st, muA, thr);
-}
-
 // Diagnostic kernel: waits on a barrier that nothing completes, so the
 // bounded wait must give up after timeout_ns and report it.
 __global__ void dmsgm_selftest_wait_kernel(int* status, unsigned long long timeout_ns) {
@@ -91,84 +42,17 @@ __global__ void dmsgm_selftest_wait_kernel(int* status, unsigned long long timeo
     if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
 }
 
-template <int B, typename T, int NW, int RPT>
-static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, const Coef& k,
-                                 int* status, cudaStream_t s, bool pdl) {
-    constexpr int TILE_H = NW * RPT * B;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
-    cfg.blockDim = dim3(NW * 32, 1, 1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, dmsgm_step_kernel<B, T, NW, RPT>, tmap, a, k, status);
-}
-
-// How many CTAs of one per-tile kernel shape the GPU holds at once.
-template <int B, typename T, int NW, int RPT>
-static int step_capacity(int device) {
-    static std::mutex mu;
-    static int cache[64] = {0};
-    std::lock_guard<std::mutex> g(mu);
-    if (device < 0 || device >= 64) return 0;
-    if (!cache[device]) {
-        int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_step_kernel<B, T, NW, RPT>,
-                                                          NW * 32, 0) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
-        }
-        cache[device] = per_sm * sms;
-    }
-    return cache[device];
-}
-
-// Strip rows per warp for tile_rows = 8 B: 8 warps x 1 row when the frame's
-// CTAs fit the GPU at once; otherwise 4 warps x 2 rows, which holds the
-// frame in fewer resident warps (a single wave at 3840 x 2160) instead of
-// leaving a partial second wave.
-template <int B, typename T>
-static int step_rpt_q8(const dmsgm_ctx* h) {
-    const int ctas = ((h->W + kTileW - 1) / kTileW) * ((h->H + 8 * B - 1) / (8 * B));
-    const int cap = step_capacity<B, T, 8, 1>(h->device);
-    return (cap > 0 && ctas > cap) ? 2 : 1;
-}
-
-// tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1) or (4, 2), (8, 2)}
+// The per-tile kernel of the handle's block size (dmsgm_step.cuh).
 static cudaError_t launch_step(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
                                const Coef& k, cudaStream_t s) {
-    const int B = h->B, q = h->tile_rows / B;   // 4, 8 or 16
-    const bool f16 = h->prec == DMSGM_STATE_FP16;
-    const bool pdl = h->use_pdl != 0;
-    if (q == 8 && h->step_rpt == 0) {
-#define DMSGM_RPT(BB) \
-        if (B == BB) h->step_rpt = f16 ? step_rpt_q8<BB, __half>(h) : step_rpt_q8<BB, float>(h);
-        DMSGM_RPT(1) DMSGM_RPT(2) DMSGM_RPT(4) DMSGM_RPT(8) DMSGM_RPT(16)
-#undef DMSGM_RPT
+    switch (h->B) {
+        case 1: return launch_step_block<1>(h, tmap, a, k, s);
+        case 2: return launch_step_block<2>(h, tmap, a, k, s);
+        case 4: return launch_step_block<4>(h, tmap, a, k, s);
+        case 8: return launch_step_block<8>(h, tmap, a, k, s);
+        case 16: return launch_step_block<16>(h, tmap, a, k, s);
+        default: return cudaErrorInvalidValue;
     }
-    const int rpt = q == 8 ? h->step_rpt : (q == 16 ? 2 : 1);
-    int* st = h->status_dev;
-#define DMSGM_CASE(BB, TT, QQ, NWW, RR)                                         \
-    if (B == BB && q == QQ && rpt == RR)                                       \
-        return launch_step_t<BB, TT, NWW, RR>(tmap, a, k, st, s, pdl);
-#define DMSGM_SHAPES(BB, TT)                                                    \
-    DMSGM_CASE(BB, TT, 4, 4, 1) DMSGM_CASE(BB, TT, 8, 8, 1) DMSGM_CASE(BB, TT, 8, 4, 2) \
-    DMSGM_CASE(BB, TT, 16, 8, 2)
-    if (!f16) {
-        DMSGM_SHAPES(1, float) DMSGM_SHAPES(2, float) DMSGM_SHAPES(4, float)
-        DMSGM_SHAPES(8, float) DMSGM_SHAPES(16, float)
-    } else {
-        DMSGM_SHAPES(1, __half) DMSGM_SHAPES(2, __half) DMSGM_SHAPES(4, __half)
-        DMSGM_SHAPES(8, __half) DMSGM_SHAPES(16, __half)
-    }
-#undef DMSGM_SHAPES
-#undef DMSGM_CASE
-    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ helpers
@@ -290,6 +174,7 @@ void fill_args(const dmsgm_ctx* h, int affine, uint32_t* mask_dev, StreamArgs* a
     a->age_max = h->age_max;
     a->theta_s = h->theta_s;
     a->theta_d = h->theta_d;
+    a->spread = h->mix_spread;
 }
 
 void advance(dmsgm_ctx* h) {
@@ -443,6 +328,7 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
         return fail(DMSGM_ERR_INVALID_ARG, "unknown kernel %d", opts.kernel);
     }
     h->kernel = opts.kernel;
+    h->mix_spread = opts.mix_spread ? 1 : 0;
     h->state_bytes = need;
     if (opts.state_mem) {
         h->mem = opts.state_mem;
@@ -725,6 +611,7 @@ int dmsgm_get_info(dmsgm_t h, dmsgm_info* o) {
     o->device = h->device;
     o->kernel = h->kernel;
     o->last_kernel = h->last_kernel;
+    o->mix_spread = h->mix_spread;
     return DMSGM_OK;
 }
 

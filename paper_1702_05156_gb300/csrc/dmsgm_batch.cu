@@ -26,7 +26,7 @@ struct BatchItem {
     char* mem;           // the handle's device memory (control block + buffers)
     Coef coef;
     uint16_t W, H;
-    uint8_t B, prec, first, parity, affine, age_max;
+    uint8_t B, prec, first, parity, affine, age_max, spread, unused;
     float theta_s, theta_d;
     int tile_begin;      // first work-list index of this stream
 };
@@ -110,10 +110,11 @@ __device__ __forceinline__ StreamArgs item_args(const BatchItem& it) {
     a.age_max = it.age_max;
     a.theta_s = it.theta_s;
     a.theta_d = it.theta_d;
+    a.spread = it.spread;
     return a;
 }
 
-template <int B, typename T>
+template <int B, typename T, bool SPREAD>
 __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origin* orig,
                                          const uint8_t* tile, uint64_t* bar, uint32_t parity) {
     constexpr int BPL = kLaneBlocks<B>;
@@ -128,12 +129,14 @@ __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origi
     Stats st[1][BPL];
     tile_stats<B, kBatchWarps, 1>(a, tile, ty0, xin, st);
     float muA[1][BPL], thr[1][BPL];
-    tile_update<B, T, kBatchWarps, 1, false>(a, tx0, ty0, pj, st, muA, thr);
+    tile_update<B, T, kBatchWarps, 1, false, SPREAD>(a, tx0, ty0, pj, st, muA, thr);
     tile_mask<B, kBatchWarps, 1>(a, tile, tx0, ty0, st, muA, thr);
     return true;
 }
 
-template <int CAP>
+// SPREAD: built to honour the streams' mixture-variance option (each item
+// still follows its own flag); without it the option's code is compiled out.
+template <int CAP, bool SPREAD>
 __global__ void __launch_bounds__(kBatchWarps * 32, 4)
     dmsgm_batch_kernel(const __grid_constant__ BatchParams<CAP> p) {
     __shared__ __align__(128) uint8_t tile[2][kStageRows * kTileW];
@@ -163,10 +166,10 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4)
         const int kind = (it.B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
         bool ok;
         switch (kind) {
-            case 0: ok = run_item<4, float>(it, t, orig[st], tile[st], &bar[st], par); break;
-            case 1: ok = run_item<4, __half>(it, t, orig[st], tile[st], &bar[st], par); break;
-            case 2: ok = run_item<8, float>(it, t, orig[st], tile[st], &bar[st], par); break;
-            default: ok = run_item<8, __half>(it, t, orig[st], tile[st], &bar[st], par); break;
+            case 0: ok = run_item<4, float, SPREAD>(it, t, orig[st], tile[st], &bar[st], par); break;
+            case 1: ok = run_item<4, __half, SPREAD>(it, t, orig[st], tile[st], &bar[st], par); break;
+            case 2: ok = run_item<8, float, SPREAD>(it, t, orig[st], tile[st], &bar[st], par); break;
+            default: ok = run_item<8, __half, SPREAD>(it, t, orig[st], tile[st], &bar[st], par); break;
         }
         if (!ok) {
             // report on the stream's status word; let in-flight copies land
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4)
     }
 }
 
-template <int CAP>
+template <int CAP, bool SPREAD>
 static cudaError_t launch_t(const BatchParams<CAP>& p, int ctas, cudaStream_t s, bool pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas, 1, 1);
@@ -188,7 +191,7 @@ static cudaError_t launch_t(const BatchParams<CAP>& p, int ctas, cudaStream_t s,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, dmsgm_batch_kernel<CAP>, p);
+    return cudaLaunchKernelEx(&cfg, dmsgm_batch_kernel<CAP, SPREAD>, p);
 }
 
 template <int CAP>
@@ -199,7 +202,7 @@ static int resident_ctas(int device) {
     if (device < 0 || device >= 64) return 1;
     if (!cache[device]) {
         int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_batch_kernel<CAP>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_batch_kernel<CAP, false>,
                                                           kBatchWarps * 32, 0) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
             return 1;
@@ -214,6 +217,7 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
     if (o.reserved != 0) return fail(DMSGM_ERR_INVALID_ARG, "dmsgm_batch_opts.reserved must be 0");
     static thread_local BatchParams<CAP> p;   // ~CAP*120 bytes: keep it off the stack
     int total = 0;
+    bool spread = false;
     for (int i = 0; i < n; ++i) {
         const dmsgm_ctx* h = hs[i];
         if (h->W > 65535 || h->H > 65535)
@@ -238,6 +242,9 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
         it.theta_s = h->theta_s;
         it.theta_d = h->theta_d;
         it.age_max = uint8_t(h->age_max);
+        it.spread = uint8_t(h->mix_spread);
+        spread = spread || h->mix_spread;
+        it.unused = 0;
         it.tile_begin = total;
         const int th = kBatchWarps * h->B;
         total += ((h->W + kTileW - 1) / kTileW) * ((h->H + th - 1) / th);
@@ -248,7 +255,8 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
     // one another, so more than fit at once is fine: one item each at most)
     int ctas = o.ctas > 0 ? o.ctas : resident_ctas<CAP>(hs[0]->device);
     ctas = std::max(1, std::min(ctas, total));
-    cudaError_t e = launch_t<CAP>(p, ctas, s, o.use_pdl > 0);
+    cudaError_t e = spread ? launch_t<CAP, true>(p, ctas, s, o.use_pdl > 0)
+                           : launch_t<CAP, false>(p, ctas, s, o.use_pdl > 0);
     if (e != cudaSuccess)
         return fail(DMSGM_ERR_CUDA, "batch kernel launch failed: %s", cudaGetErrorString(e));
     for (int i = 0; i < n; ++i) advance(hs[i]);

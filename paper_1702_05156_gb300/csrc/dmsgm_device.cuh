@@ -111,6 +111,7 @@ struct StreamArgs {
     int affine;         // 1: coef holds the affine block-unit form
     int age_max;
     float theta_s, theta_d;
+    int spread;         // 1: the mixed variance carries the spread of the mixed means
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -481,19 +482,34 @@ __device__ __forceinline__ GlobalSrc<T, COH> global_src(const StreamArgs& a) {
 
 // Area-weighted mix of the four overlapped blocks whose top-left one is k0
 // (all four on the grid; the weights sum to 1).
+// With spread, Yi et al.'s mixture variance: the spread of the four means
+// about their mix, sum w (mu_k - mu~)^2, is added to the mixed variance.
 template <typename Src>
-__device__ __forceinline__ Comp mix4(const Src& src, int k0, const Weights& w) {
+__device__ __forceinline__ Comp mix4(const Src& src, int k0, const Weights& w, bool spread) {
     const int k1 = k0 + src.pitch;
     const float2 W00 = dup2(w.w00), W10 = dup2(w.w10), W01 = dup2(w.w01), W11 = dup2(w.w11);
+    const float2 m00 = src.ld_mu(k0), m10 = src.ld_mu(k0 + 1);
+    const float2 m01 = src.ld_mu(k1), m11 = src.ld_mu(k1 + 1);
     float2 mu, var, ag;
-    mu = __fmul2_rn(W00, src.ld_mu(k0));
-    mu = __ffma2_rn(W10, src.ld_mu(k0 + 1), mu);
-    mu = __ffma2_rn(W01, src.ld_mu(k1), mu);
-    mu = __ffma2_rn(W11, src.ld_mu(k1 + 1), mu);
+    mu = __fmul2_rn(W00, m00);
+    mu = __ffma2_rn(W10, m10, mu);
+    mu = __ffma2_rn(W01, m01, mu);
+    mu = __ffma2_rn(W11, m11, mu);
     var = __fmul2_rn(W00, src.ld_var(k0));
     var = __ffma2_rn(W10, src.ld_var(k0 + 1), var);
     var = __ffma2_rn(W01, src.ld_var(k1), var);
     var = __ffma2_rn(W11, src.ld_var(k1 + 1), var);
+    if (spread) {
+        const float2 nm = make_float2(-mu.x, -mu.y);
+        float2 d = __fadd2_rn(m00, nm);
+        var = __ffma2_rn(__fmul2_rn(W00, d), d, var);
+        d = __fadd2_rn(m10, nm);
+        var = __ffma2_rn(__fmul2_rn(W10, d), d, var);
+        d = __fadd2_rn(m01, nm);
+        var = __ffma2_rn(__fmul2_rn(W01, d), d, var);
+        d = __fadd2_rn(m11, nm);
+        var = __ffma2_rn(__fmul2_rn(W11, d), d, var);
+    }
     ag = __fmul2_rn(W00, age2f(src.ld_ag(k0)));
     ag = __ffma2_rn(W10, age2f(src.ld_ag(k0 + 1)), ag);
     ag = __ffma2_rn(W01, age2f(src.ld_ag(k1)), ag);
@@ -505,13 +521,16 @@ __device__ __forceinline__ Comp mix4(const Src& src, int k0, const Weights& w) {
 // area-weighted mix of the previous blocks its back-projected square
 // overlaps.  At the grid border the blocks off the grid are dropped and the
 // remaining weights renormalised.  src must hold the blocks (i0 .. i0+1,
-// j0 .. j0+1) that lie on the grid.
-template <typename Src>
+// j0 .. j0+1) that lie on the grid.  SPREAD: the kernel is built to honour
+// a.spread (the mixture-variance option); without it the option's code is
+// compiled out, and with it the register demand grows.
+template <bool SPREAD, typename Src>
 __device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p, const Src& src) {
     if (!p.ok) return no_source();
     const Weights w = overlap(p);
+    const bool spread = SPREAD && a.spread != 0;
     if (p.i0 >= 0 && p.i0 + 1 < a.Gx && p.j0 >= 0 && p.j0 + 1 < a.Gy)
-        return mix4(src, src.at(p.i0, p.j0), w);
+        return mix4(src, src.at(p.i0, p.j0), w, spread);
     float wsum = 0.f;
     float2 mu = make_float2(0.f, 0.f), var = mu, ag = mu;
 #pragma unroll
@@ -528,12 +547,24 @@ __device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p, const
         }
     }
     if (!(wsum >= kMinWeight)) return no_source();
-    return comp_from(make_float2(mu.x / wsum, mu.y / wsum), make_float2(var.x / wsum, var.y / wsum),
+    const float2 mt = make_float2(mu.x / wsum, mu.y / wsum);
+    if (spread) {   // second pass: the spread of the in-grid means about their mix
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = p.i0 + (q & 1), j = p.j0 + (q >> 1);
+            const float wq = q == 0 ? w.w00 : q == 1 ? w.w10 : q == 2 ? w.w01 : w.w11;
+            if (i >= 0 && i < a.Gx && j >= 0 && j < a.Gy) {
+                const float2 d = __fadd2_rn(src.ld_mu(src.at(i, j)), make_float2(-mt.x, -mt.y));
+                var = __ffma2_rn(__fmul2_rn(dup2(wq), d), d, var);
+            }
+        }
+    }
+    return comp_from(mt, make_float2(var.x / wsum, var.y / wsum),
                      make_float2(ag.x / wsum, ag.y / wsum));
 }
-template <typename T, bool COH>
+template <typename T, bool COH, bool SPREAD>
 __device__ __forceinline__ Comp gather(const StreamArgs& a, const Proj& p) {
-    return gather(a, p, global_src<T, COH>(a));
+    return gather<SPREAD>(a, p, global_src<T, COH>(a));
 }
 
 // ------------------------------------------------------------------ (b)
@@ -935,7 +966,7 @@ __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, i
     }
 }
 
-template <int B, typename T, int NW, int RPT, bool COH>
+template <int B, typename T, int NW, int RPT, bool COH, bool SPREAD>
 __device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty0,
                                             const Proj (&pj)[RPT][kLaneBlocks<B>],
                                             const Stats (&st)[RPT][kLaneBlocks<B>],
@@ -943,7 +974,7 @@ __device__ __forceinline__ void tile_update(const StreamArgs& a, int tx0, int ty
                                             float (&thr)[RPT][kLaneBlocks<B>]) {
     const GlobalSrc<T, COH> src = global_src<T, COH>(a);
     tile_update_with<B, T, NW, RPT>(a, tx0, ty0, pj, st, muA, thr,
-                                    [&](const Proj& p) { return gather(a, p, src); });
+                                    [&](const Proj& p) { return gather<SPREAD>(a, p, src); });
 }
 
 // Both extremes of a block's pixels pass the background test: then every

@@ -64,6 +64,7 @@ struct dmsgm_ctx {
     int use_pdl;
     int seq_tile_rows;           // 0: automatic
     int kernel;                  // DMSGM_KERNEL_*
+    int mix_spread;              // 1: mixed variance carries the spread of the mixed means
     int last_kernel;             // kernel of the last dmsgm_process step
     int step_rpt;                // strip rows per warp of the per-tile kernel at tile_rows = 8 B (0: not chosen yet)
     int pipe_maps;               // state tensor maps of the pipelined kernel: 0 not yet, 1 ok, -1 unsupported
@@ -116,6 +117,17 @@ int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* H3x
 // tells whether it did.  automatic: only where it is expected to be faster.
 int launch_pipe(dmsgm_ctx* h, const CUtensorMap& frame_map, const StreamArgs& a, const Coef& c,
                 cudaStream_t s, bool automatic, bool* launched);
+
+// Launch the per-tile frame-step kernel for block size B (dmsgm_step.cuh,
+// instantiated in dmsgm_step_b<B>.cu).
+template <int B>
+cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
+                              const Coef& k, cudaStream_t s);
+extern template cudaError_t launch_step_block<1>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
+extern template cudaError_t launch_step_block<2>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
+extern template cudaError_t launch_step_block<4>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
+extern template cudaError_t launch_step_block<8>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
+extern template cudaError_t launch_step_block<16>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
 
 // Launch the batched persistent kernel (dmsgm_batch.cu).
 int launch_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,

@@ -201,11 +201,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
             tile_update_with<B, T, NW, 1>(a, tx0, ty0, pj, st, muA, thr, [&](const Proj& p) {
                 const unsigned li = unsigned(p.i0 - box.rx0), lj = unsigned(p.j0 - box.ry0);
                 return (li <= unsigned(G::kBoxW - 2) && lj <= unsigned(G::kBoxH - 2))
-                           ? gather(a, p, box)
-                           : gather(a, p, glob);
+                           ? gather<false>(a, p, box)
+                           : gather<false>(a, p, glob);
             });
         } else {
-            tile_update<B, T, NW, 1, false>(a, tx0, ty0, pj, st, muA, thr);
+            tile_update<B, T, NW, 1, false, false>(a, tx0, ty0, pj, st, muA, thr);
         }
         tile_mask<B, NW, 1>(a, sm.frame[s], tx0, ty0, st, muA, thr);
         if (!more) break;
@@ -311,6 +311,7 @@ int launch_pipe(dmsgm_ctx* h, const CUtensorMap& fmap, const StreamArgs& a, cons
     *launched = false;
     if (!a.first && !a.affine) return DMSGM_OK;   // general projective form: per-tile kernel
     if (h->H % h->B) return DMSGM_OK;              // a cut bottom block row: per-tile kernel
+    if (h->mix_spread) return DMSGM_OK;            // the mixture-variance option: per-tile kernel
     const int q = h->tile_rows / h->B;
     const bool f16 = h->prec == DMSGM_STATE_FP16;
 #define DMSGM_PIPE(BB, TT, NWW) return launch_pipe_t<BB, TT, NWW>(h, fmap, a, c, s, automatic, launched);

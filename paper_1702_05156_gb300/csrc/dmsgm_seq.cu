@@ -41,6 +41,7 @@ struct SeqParams {
     int first;              // 1: frame 0 has no previous state
     int age_max;
     float theta_s, theta_d;
+    int spread;             // mixed variance carries the spread of the mixed means
     int tiles_x, tiles_y;
     int rx, ry;             // dependency radius, in tiles
     uint8_t affine[kSeqMaxFrames];
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
     a.age_max = p.age_max;
     a.theta_s = p.theta_s;
     a.theta_d = p.theta_d;
+    a.spread = p.spread;
 
     auto origins = [&](int k, Origin* o) {
         const int t = threadIdx.x;
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 2 : 1))
         }
         // critical path: gather, mix, update, store the state
         float muA[RPT][BPL], thr[RPT][BPL];
-        tile_update<B, T, NW, RPT, true>(a, tx0, ty0, pj, sts, muA, thr);
+        tile_update<B, T, NW, RPT, true, false>(a, tx0, ty0, pj, sts, muA, thr);
         __syncthreads();
         if (threadIdx.x == 0) {   // publish: this tile's frame-k state is visible
             __threadfence();
@@ -239,8 +241,9 @@ static int capacity(const dmsgm_ctx* h, int nw, int rpt) {
 // most that fit the GPU at all; {0, 0} if none fits.
 static SeqShape pick_shape(const dmsgm_ctx* h, int sms) {
     static const SeqShape shapes[] = {{8, 1}, {16, 1}, {16, 2}, {16, 4}};
-    // built for blocks 4 and 8 on whole block rows
-    if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0)) return SeqShape{0, 0};
+    // built for blocks 4 and 8 on whole block rows, without the
+    // mixture-variance option (those calls run per frame)
+    if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0) || h->mix_spread) return SeqShape{0, 0};
     if (h->seq_tile_rows) {   // asked for: use it if the tiles fit the GPU at once
         for (const SeqShape& sh : shapes) {
             if (sh.nw * sh.rpt * h->B != h->seq_tile_rows) continue;
@@ -367,6 +370,7 @@ int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* Hs,
         p.age_max = h->age_max;
         p.theta_s = h->theta_s;
         p.theta_d = h->theta_d;
+        p.spread = h->mix_spread;
         p.tiles_x = tiles_x;
         p.tiles_y = tiles_y;
         p.rx = rx;

@@ -1,0 +1,135 @@
+// dmsgm_step.cuh -- the per-tile frame-step kernel and its launch, as a
+// template over the block size.  Each block size is instantiated in its own
+// translation unit (dmsgm_step_b<B>.cu) so that they compile in parallel.
+#pragma once
+
+#include <mutex>
+
+#include "dmsgm_internal.h"
+
+namespace dmsgm {
+
+constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // 2 s: only a broken copy gets here
+
+// 8x8 blocks, one strip row per warp: 32 registers (full occupancy); two
+// rows per warp: 64.  4x4 blocks keep the compiler's choice.
+template <int B, int NW, int RPT>
+constexpr int step_min_blocks() { return B == 8 ? (RPT == 1 ? 64 : 32) / NW : 1; }
+
+template <int B, typename T, int NW, int RPT, bool SPREAD>
+__global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
+    dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, const Coef k,
+                      int* status) {
+    constexpr int STRIPS = NW * RPT;          // strip rows per tile
+    constexpr int TILE_H = STRIPS * B;
+    __shared__ __align__(128) uint8_t tile[TILE_H * kTileW];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ Origin orig[2 * STRIPS];
+    const int tx0 = blockIdx.x * kTileW;
+    const int ty0 = blockIdx.y * TILE_H;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, TILE_H * kTileW);
+        tma_load_2d(tile, &tmap, tx0, ty0, &bar);
+    }
+    fill_origins<B>(a, k, tx0, ty0, STRIPS, orig);
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
+    if (__syncthreads_or(!ok)) {
+        // report, give the copy one more bounded chance to land, and leave
+        if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+        mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
+        return;
+    }
+    // The pixels, their block statistics and the back-projections do not
+    // depend on the previous frame's kernel, so they run before its end;
+    // the state does.
+    constexpr int BPL = kLaneBlocks<B>;
+    const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
+    Stats st[RPT][BPL];
+    Proj pj[RPT][BPL];
+    tile_stats<B, NW, RPT>(a, tile, ty0, xin, st);
+    tile_project<B, NW, RPT>(a, k, tx0, ty0, orig, pj);
+    pdl_wait();
+    pdl_launch_dependents();
+    float muA[RPT][BPL], thr[RPT][BPL];
+    tile_update<B, T, NW, RPT, false, SPREAD>(a, tx0, ty0, pj, st, muA, thr);
+    tile_mask<B, NW, RPT>(a, tile, tx0, ty0, st, muA, thr);
+}
+
+template <int B, typename T, int NW, int RPT>
+static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, const Coef& k,
+                                 int* status, cudaStream_t s, bool pdl) {
+    // the mixture-variance option has its own build of the kernel
+    auto kern = a.spread ? dmsgm_step_kernel<B, T, NW, RPT, true> : dmsgm_step_kernel<B, T, NW, RPT, false>;
+    constexpr int TILE_H = NW * RPT * B;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
+    cfg.blockDim = dim3(NW * 32, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, tmap, a, k, status);
+}
+
+// How many CTAs of one per-tile kernel shape the GPU holds at once.
+template <int B, typename T, int NW, int RPT>
+static int step_capacity(int device) {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    std::lock_guard<std::mutex> g(mu);
+    if (device < 0 || device >= 64) return 0;
+    if (!cache[device]) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_step_kernel<B, T, NW, RPT, false>,
+                                                          NW * 32, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cache[device] = per_sm * sms;
+    }
+    return cache[device];
+}
+
+// Strip rows per warp for tile_rows = 8 B: 8 warps x 1 row when the frame's
+// CTAs fit the GPU at once; otherwise 4 warps x 2 rows, which holds the
+// frame in fewer resident warps (a single wave at 3840 x 2160) instead of
+// leaving a partial second wave.
+template <int B, typename T>
+static int step_rpt_q8(const dmsgm_ctx* h) {
+    const int ctas = ((h->W + kTileW - 1) / kTileW) * ((h->H + 8 * B - 1) / (8 * B));
+    const int cap = step_capacity<B, T, 8, 1>(h->device);
+    return (cap > 0 && ctas > cap) ? 2 : 1;
+}
+
+// tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1) or (4, 2), (8, 2)}
+template <int B>
+cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
+                              const Coef& k, cudaStream_t s) {
+    const int q = h->tile_rows / B;   // 4, 8 or 16
+    const bool f16 = h->prec == DMSGM_STATE_FP16;
+    const bool pdl = h->use_pdl != 0;
+    if (q == 8 && h->step_rpt == 0)
+        h->step_rpt = f16 ? step_rpt_q8<B, __half>(h) : step_rpt_q8<B, float>(h);
+    const int rpt = q == 8 ? h->step_rpt : (q == 16 ? 2 : 1);
+    int* st = h->status_dev;
+#define DMSGM_CASE(TT, QQ, NWW, RR) \
+    if (q == QQ && rpt == RR) return launch_step_t<B, TT, NWW, RR>(tmap, a, k, st, s, pdl);
+    if (!f16) {
+        DMSGM_CASE(float, 4, 4, 1) DMSGM_CASE(float, 8, 8, 1) DMSGM_CASE(float, 8, 4, 2)
+        DMSGM_CASE(float, 16, 8, 2)
+    } else {
+        DMSGM_CASE(__half, 4, 4, 1) DMSGM_CASE(__half, 8, 8, 1) DMSGM_CASE(__half, 8, 4, 2)
+        DMSGM_CASE(__half, 16, 8, 2)
+    }
+#undef DMSGM_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dmsgm

@@ -1,0 +1,8 @@
+// dmsgm_step_b16.cu -- the per-tile frame-step kernel for 16x16 blocks
+// (one translation unit per block size, so the builds run in parallel).
+#include "dmsgm_step.cuh"
+
+namespace dmsgm {
+template cudaError_t launch_step_block<16>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&,
+                                           const Coef&, cudaStream_t);
+}  // namespace dmsgm

@@ -51,7 +51,7 @@ class Dmsgm:
     def __init__(self, width: int, height: int, block: int = 4, theta_s: float = 2.0,
                  theta_d: float = 4.0, age_max: int = 30, precision: str = "fp32",
                  tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None,
-                 seq_tile_rows: int = 0, kernel: str = "auto"):
+                 seq_tile_rows: int = 0, kernel: str = "auto", mix_spread: bool = False):
         prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
         opts = _lib.dmsgm_opts()
         opts.precision = prec
@@ -60,6 +60,7 @@ class Dmsgm:
         opts.seq_tile_rows = seq_tile_rows
         opts.kernel = {"auto": DMSGM_KERNEL_AUTO, "tile": DMSGM_KERNEL_TILE,
                        "pipe": DMSGM_KERNEL_PIPE}[kernel]
+        opts.mix_spread = 1 if mix_spread else 0
         self._state_mem = state_mem
         if state_mem is not None:
             opts.state_mem = state_mem.data_ptr()

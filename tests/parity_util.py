@@ -85,7 +85,7 @@ def exempt_blocks(dg: np.ndarray, theta_s: float) -> np.ndarray:
 
 def compare_step(prev: dict | None, got: dict, got_mask_bits: np.ndarray, frame: np.ndarray,
                  H: np.ndarray, *, block: int, theta_s=2.0, theta_d=4.0, age_max=30,
-                 rel: float = 1e-5) -> StepReport:
+                 rel: float = 1e-5, mix_spread: bool = False) -> StepReport:
     """prev/got: GPU state dicts (arrays (Gy, Gx)) before/after the frame;
     prev None = first frame.  got_mask_bits: unpacked uint8 (H, W)."""
     pst = None
@@ -93,7 +93,7 @@ def compare_step(prev: dict | None, got: dict, got_mask_bits: np.ndarray, frame:
         pst = state_from_arrays(*(np.asarray(prev[k], dtype=np.float64) for k in
                                   ("muA", "varA", "ageA", "muC", "varC", "ageC")))
     ost, omask, dg = oracle_step(frame, H, pst, block=block, theta_s=theta_s, theta_d=theta_d,
-                                 age_max=age_max, diag=True)
+                                 age_max=age_max, diag=True, mix_spread=mix_spread)
     r = StepReport()
     ex = exempt_blocks(dg, theta_s)
     keep = ~ex
