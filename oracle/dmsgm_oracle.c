@@ -348,3 +348,88 @@ int oracle_run(int W, int H, int B, double theta_s, double theta_d, int age_max,
                          muA, varA, ageA, muC, varC, ageC,
                          tmu_A, tvar_A, tage_A, tmu_C, tvar_C, tage_C, masks);
 }
+
+/*
+ * Preprocessing (the paper's Gaussian blur then 3x3 median, both clamping
+ * coordinates to the frame; Sec. 2.1 and the appendix filter listings).
+ *
+ * Readings where the paper leaves the filter open:
+ *   P1 the Gaussian comes first, then the median;
+ *   P2 the N x N Gaussian (N odd, sigma > 0) is the outer product of the 1-D
+ *      weights g(x) = exp(-x^2 / (2 sigma^2)), x = -N/2 .. N/2, normalised
+ *      and quantised to 8-bit fixed point: q(x) = round(256 g(x) / sum g)
+ *      for x != 0 and q(0) = 256 - sum_{x != 0} q(x), so the 2-D weights
+ *      q(i) q(j) sum to exactly 65536;
+ *   P3 the blurred pixel is floor(sum_ij q(i) q(j) I(r+i, c+j) / 65536) --
+ *      the paper's float sum cast to an 8-bit value, computed exactly;
+ *   P4 the median is the 5th smallest of the 9 clamped neighbours.
+ * gauss_size 0 skips the blur; median 0 skips the median.
+ */
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int oracle_gauss_weights(int gauss_size, double sigma, int* q)
+{
+    if (gauss_size < 1 || gauss_size % 2 == 0 || !(sigma > 0.0)) return -1;
+    const int h = gauss_size / 2;
+    double g[64], sum = 0.0;
+    if (gauss_size > 63) return -1;
+    for (int x = -h; x <= h; ++x) {
+        g[x + h] = exp(-(double)x * x / (2.0 * sigma * sigma));
+        sum += g[x + h];
+    }
+    int rest = 0;
+    for (int x = -h; x <= h; ++x)
+        if (x != 0) {
+            q[x + h] = (int)floor(256.0 * g[x + h] / sum + 0.5);
+            rest += q[x + h];
+        }
+    q[h] = 256 - rest;
+    return 0;
+}
+
+int oracle_prefilter(int W, int H, const unsigned char* in, unsigned char* out,
+                     int gauss_size, double sigma, int median)
+{
+    if (W <= 0 || H <= 0) return -1;
+    const size_t n = (size_t)W * H;
+    /* the blurred frame goes to out; the caller applies the median to it */
+    if (gauss_size > 0) {
+        int q[64];
+        if (oracle_gauss_weights(gauss_size, sigma, q)) return -1;
+        const int h = gauss_size / 2;
+        for (int r = 0; r < H; ++r)
+            for (int c = 0; c < W; ++c) {
+                long long s = 0;
+                for (int i = -h; i <= h; ++i)
+                    for (int j = -h; j <= h; ++j)
+                        s += (long long)q[i + h] * q[j + h] *
+                             in[(size_t)clampi(r + i, 0, H - 1) * W + clampi(c + j, 0, W - 1)];
+                out[(size_t)r * W + c] = (unsigned char)(s >> 16);
+            }
+    } else {
+        memcpy(out, in, n);
+    }
+    return median ? 1 : 0;   /* the caller applies the median (oracle_median3) */
+}
+
+int oracle_median3(int W, int H, const unsigned char* in, unsigned char* out)
+{
+    if (W <= 0 || H <= 0) return -1;
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c) {
+            unsigned char w[9];
+            int k = 0;
+            for (int i = -1; i <= 1; ++i)
+                for (int j = -1; j <= 1; ++j)
+                    w[k++] = in[(size_t)clampi(r + i, 0, H - 1) * W + clampi(c + j, 0, W - 1)];
+            /* insertion sort, then the middle element */
+            for (int a = 1; a < 9; ++a) {
+                unsigned char v = w[a];
+                int b = a - 1;
+                while (b >= 0 && w[b] > v) { w[b + 1] = w[b]; --b; }
+                w[b + 1] = v;
+            }
+            out[(size_t)r * W + c] = w[4];
+        }
+    return 0;
+}

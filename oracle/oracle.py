@@ -61,6 +61,13 @@ def _load():
             lib.oracle_run_ex.restype = ctypes.c_int
             lib.oracle_run_ex.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
                 ctypes.c_int] * 3 + [P] * 15
+            lib.oracle_gauss_weights.restype = ctypes.c_int
+            lib.oracle_gauss_weights.argtypes = [ctypes.c_int, ctypes.c_double, P]
+            lib.oracle_prefilter.restype = ctypes.c_int
+            lib.oracle_prefilter.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_int]
+            lib.oracle_median3.restype = ctypes.c_int
+            lib.oracle_median3.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
             lib.oracle_diag_stride.restype = ctypes.c_int
             assert lib.oracle_diag_stride() == len(DIAG)
             _lib = lib
@@ -152,3 +159,31 @@ def oracle_run(frames: np.ndarray, Hs: np.ndarray, *, block: int,
     if rc:
         raise ValueError(f"oracle_run failed ({rc})")
     return st, masks
+
+
+def gauss_weights(gauss_size: int, sigma: float) -> np.ndarray:
+    """The quantised 1-D Gaussian weights (sum 256) of the preprocessing blur."""
+    lib = _load()
+    q = np.zeros(64, dtype=np.int32)
+    if lib.oracle_gauss_weights(int(gauss_size), float(sigma), _ptr(q)):
+        raise ValueError("invalid Gaussian size or sigma")
+    return q[:gauss_size].copy()
+
+
+def prefilter(frame: np.ndarray, *, gauss_size: int = 5, sigma: float = 1.0,
+              median: bool = True) -> np.ndarray:
+    """The preprocessing of the paper's Sec. 2.1: N x N Gaussian blur, then
+    the 3 x 3 median, both clamp-to-border (readings P1-P4 in the C file)."""
+    lib = _load()
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    h, w = frame.shape
+    blur = np.empty_like(frame)
+    if lib.oracle_prefilter(w, h, _ptr(frame), _ptr(blur), int(gauss_size), float(sigma),
+                            int(bool(median))) < 0:
+        raise ValueError("invalid preprocessing arguments")
+    if not median:
+        return blur
+    out = np.empty_like(frame)
+    if lib.oracle_median3(w, h, _ptr(blur), _ptr(out)):
+        raise ValueError("invalid size")
+    return out

@@ -548,3 +548,68 @@ def test_spread_is_the_mixture_variance_by_sampling_weights():
     inside = ((iy < 2)[:, None] & (ix < 2)[None, :])
     v = vals[inside]
     np.testing.assert_allclose(d[0, 0, DIAG["VAR_A"]], v.var(), rtol=1e-3)
+
+
+# ---------------------------------------------------------------- preprocessing (P1-P4)
+def _brute_blur(img, q):
+    h = len(q) // 2
+    p = np.pad(img.astype(np.int64), h, mode="edge")
+    k = np.outer(q, q).astype(np.int64)
+    H, W = img.shape
+    out = np.zeros((H, W), np.int64)
+    for i in range(len(q)):
+        for j in range(len(q)):
+            out += k[i, j] * p[i:i + H, j:j + W]
+    return (out >> 16).astype(np.uint8)
+
+
+def _brute_median(img):
+    p = np.pad(img, 1, mode="edge")
+    H, W = img.shape
+    win = np.stack([p[i:i + H, j:j + W] for i in range(3) for j in range(3)])
+    return np.sort(win, axis=0)[4]
+
+
+@pytest.mark.parametrize("n,sigma", [(3, 0.8), (5, 1.0), (5, 2.5), (7, 1.5), (9, 3.0)])
+def test_gauss_weights_quantise_the_normalised_gaussian(n, sigma):
+    """Weights sum to exactly 256, are symmetric and unimodal; each off-centre
+    weight is the normalised Gaussian rounded to the nearest 1/256, and the
+    centre weight takes up their rounding (at most (N-1)/2 steps of 1/256)."""
+    q = oracle.gauss_weights(n, sigma)
+    assert q.sum() == 256 and np.array_equal(q, q[::-1])
+    assert np.all(np.diff(q[: n // 2 + 1]) >= 0)
+    x = np.arange(n) - n // 2
+    g = np.exp(-x.astype(np.float64) ** 2 / (2 * sigma ** 2))
+    err = np.abs(q / 256.0 - g / g.sum())
+    off = np.arange(n) != n // 2
+    assert np.all(err[off] <= 0.5 / 256)
+    assert err[n // 2] <= (n - 1) * 0.5 / 256
+
+
+@pytest.mark.parametrize("shape", [(7, 9), (16, 16), (1, 5), (12, 3)])
+@pytest.mark.parametrize("n,sigma", [(3, 0.8), (5, 1.0), (7, 1.5)])
+def test_blur_equals_brute_force_clamped_convolution(shape, n, sigma):
+    rng = np.random.default_rng(sum(shape) + n)
+    img = rng.integers(0, 256, shape, dtype=np.uint8)
+    got = oracle.prefilter(img, gauss_size=n, sigma=sigma, median=False)
+    assert np.array_equal(got, _brute_blur(img, oracle.gauss_weights(n, sigma)))
+
+
+@pytest.mark.parametrize("shape", [(7, 9), (16, 16), (1, 5), (2, 2), (12, 3)])
+def test_median_equals_brute_force_clamped_window(shape):
+    rng = np.random.default_rng(shape[0] * 100 + shape[1])
+    img = rng.integers(0, 256, shape, dtype=np.uint8)
+    got = oracle.prefilter(img, gauss_size=0, median=True)
+    assert np.array_equal(got, _brute_median(img))
+    both = oracle.prefilter(img, gauss_size=5, sigma=1.0, median=True)
+    assert np.array_equal(both, _brute_median(_brute_blur(img, oracle.gauss_weights(5, 1.0))))
+
+
+def test_filters_keep_constants_remove_impulses_keep_ramps():
+    c = np.full((10, 12), 77, np.uint8)
+    assert np.array_equal(oracle.prefilter(c, gauss_size=7, sigma=2.0), c)
+    spike = c.copy()
+    spike[4, 5] = 250
+    assert np.array_equal(oracle.prefilter(spike, gauss_size=0, median=True), c)
+    ramp = np.tile(np.arange(0, 240, 20, dtype=np.uint8), (10, 1))
+    assert np.array_equal(oracle.prefilter(ramp, gauss_size=0, median=True), ramp)
