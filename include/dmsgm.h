@@ -108,6 +108,15 @@ typedef struct {
                            means, sum_k w_k (var_k + (mu_k - mu~)^2) / sum w;
                            0 (default): the variances alone (Sec. 2.4).  Not
                            available through dmsgm_process_seq_noalloc.      */
+    int pre_gauss;      /* preprocessing (Sec. 2.1), applied to every frame
+                           before the step, as dmsgm_prefilter: Gaussian size
+                           (0: none, or odd 3..15) ...                       */
+    double pre_sigma;   /* ... and its sigma (> 0)                            */
+    int pre_median;     /* 1: then the 3 x 3 median.  With either filter the
+                           handle owns two W*H scratch frames, the step runs
+                           without programmatic dependent launch, and the
+                           batched and multi-frame paths are not available
+                           (DMSGM_ERR_UNSUPPORTED / per-frame launches).     */
 } dmsgm_opts;
 
 enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1, DMSGM_KERNEL_PIPE = 2 };
@@ -236,6 +245,20 @@ int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n,
 #define DMSGM_MAX_BATCH 256
 int dmsgm_process_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,
                         const double* H3x3s, uint32_t* const* masks_dev, void* cuda_stream);
+
+/* Preprocessing of the paper's Sec. 2.1: an N x N Gaussian blur (gauss_size
+ * N odd in 3..15 with sigma > 0, or 0 for none), then a 3 x 3 median
+ * (median 1, or 0 for none), both clamping coordinates to the frame.  The
+ * 1-D weights are the normalised Gaussian rounded to 1/256 off the centre,
+ * the centre weight making the sum exactly 256; the 2-D kernel is their
+ * outer product and a blurred pixel is floor(sum / 65536) -- the paper's
+ * float sum cast to an 8-bit value, computed exactly.  The median is the 5th
+ * of the 9 clamped neighbours of the blurred frame.
+ * in_dev, out_dev: W*H bytes each, device, 16-byte aligned, not
+ * overlapping; W % 16 == 0.  At least one filter.  Asynchronous on
+ * cuda_stream. */
+int dmsgm_prefilter(const uint8_t* in_dev, uint8_t* out_dev, int width, int height,
+                    int gauss_size, double sigma, int median, void* cuda_stream);
 
 /* Launch shape of the batched kernel; zero-initialised = built-in choice.
  * A work item is a 256 x (8*block) pixel tile of one stream. */

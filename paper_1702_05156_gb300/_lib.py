@@ -35,14 +35,17 @@ EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm
            "dmsgm_process_host", "dmsgm_process_batch",
            "dmsgm_process_batch_ex", "dmsgm_process_batch_host",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
-           "dmsgm_status", "dmsgm_selftest_wait", "dmsgm_last_error", "dmsgm_version")
+           "dmsgm_status", "dmsgm_selftest_wait", "dmsgm_prefilter", "dmsgm_last_error",
+           "dmsgm_version")
 
 
 class dmsgm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("state_mem", ctypes.c_void_p),
                 ("state_bytes", ctypes.c_size_t), ("tile_rows", ctypes.c_int),
                 ("use_pdl", ctypes.c_int), ("seq_tile_rows", ctypes.c_int),
-                ("kernel", ctypes.c_int), ("mix_spread", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("mix_spread", ctypes.c_int),
+                ("pre_gauss", ctypes.c_int), ("pre_sigma", ctypes.c_double),
+                ("pre_median", ctypes.c_int)]
 
 
 class dmsgm_batch_opts(ctypes.Structure):
@@ -101,6 +104,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_get_info": (I, [P, P]),
             "dmsgm_status": (I, [P]),
             "dmsgm_selftest_wait": (I, [P, ctypes.c_ulonglong, P]),
+            "dmsgm_prefilter": (I, [P, P, I, I, I, ctypes.c_double, I, P]),
             "dmsgm_last_error": (ctypes.c_char_p, []),
             "dmsgm_version": (ctypes.c_char_p, []),
         }
@@ -220,6 +224,12 @@ def dmsgm_status(h) -> int:
 
 def dmsgm_selftest_wait(h, timeout_ns: int, stream: int = 0):
     _check(load_library().dmsgm_selftest_wait(h, timeout_ns, stream))
+
+
+def dmsgm_prefilter(in_dev: int, out_dev: int, width: int, height: int, gauss_size: int,
+                    sigma: float, median: int, stream: int = 0):
+    _check(load_library().dmsgm_prefilter(in_dev, out_dev, width, height, gauss_size, sigma,
+                                          median, stream))
 
 
 def dmsgm_last_error() -> str:

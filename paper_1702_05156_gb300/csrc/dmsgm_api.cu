@@ -44,13 +44,13 @@ __global__ void dmsgm_selftest_wait_kernel(int* status, unsigned long long timeo
 
 // The per-tile kernel of the handle's block size (dmsgm_step.cuh).
 static cudaError_t launch_step(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
-                               const Coef& k, cudaStream_t s) {
+                               const Coef& k, cudaStream_t s, bool pdl) {
     switch (h->B) {
-        case 1: return launch_step_block<1>(h, tmap, a, k, s);
-        case 2: return launch_step_block<2>(h, tmap, a, k, s);
-        case 4: return launch_step_block<4>(h, tmap, a, k, s);
-        case 8: return launch_step_block<8>(h, tmap, a, k, s);
-        case 16: return launch_step_block<16>(h, tmap, a, k, s);
+        case 1: return launch_step_block<1>(h, tmap, a, k, s, pdl);
+        case 2: return launch_step_block<2>(h, tmap, a, k, s, pdl);
+        case 4: return launch_step_block<4>(h, tmap, a, k, s, pdl);
+        case 8: return launch_step_block<8>(h, tmap, a, k, s, pdl);
+        case 16: return launch_step_block<16>(h, tmap, a, k, s, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -189,18 +189,32 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
     int affine = 0;
     if (!make_coef(H3x3, h->B, &c, &affine))
         return fail(DMSGM_ERR_INVALID_ARG, "homography is not finite in FP32");
+    int rc;
+    bool pdl = h->use_pdl != 0;
+    if (h->pre_buf) {
+        // Sec. 2.1 preprocessing into the handle's scratch frame (two of
+        // them, alternating, so a frame's filter never overwrites the pixels
+        // the previous frame's kernel may still read); the step then waits
+        // for the filter in plain stream order
+        uint8_t* dst = h->pre_buf + size_t(h->frames & 1) * h->W * h->H;
+        rc = launch_prefilter(frame_dev, dst, h->W, h->H, h->pre_gauss, h->pre_sigma,
+                              h->pre_median, s);
+        if (rc) return rc;
+        frame_dev = dst;
+        pdl = false;
+    }
     const CUtensorMap* tm = nullptr;
-    int rc = frame_map(h, frame_dev, &tm);
+    rc = frame_map(h, frame_dev, &tm);
     if (rc) return rc;
     StreamArgs a;
     fill_args(h, affine, mask_dev, &a);
     bool launched = false;
-    if (h->kernel != DMSGM_KERNEL_TILE) {
+    if (h->kernel != DMSGM_KERNEL_TILE && !h->pre_buf) {
         rc = launch_pipe(h, *tm, a, c, s, h->kernel == DMSGM_KERNEL_AUTO, &launched);
         if (rc) return rc;
     }
     if (!launched) {
-        cudaError_t e = launch_step(h, *tm, a, c, s);
+        cudaError_t e = launch_step(h, *tm, a, c, s, pdl);
         if (e != cudaSuccess)
             return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     }
@@ -329,6 +343,16 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     }
     h->kernel = opts.kernel;
     h->mix_spread = opts.mix_spread ? 1 : 0;
+    if ((opts.pre_gauss && (opts.pre_gauss < 3 || opts.pre_gauss > 15 || opts.pre_gauss % 2 == 0 ||
+                            !(opts.pre_sigma > 0.0) || !std::isfinite(opts.pre_sigma))) ||
+        (opts.pre_median != 0 && opts.pre_median != 1)) {
+        delete h;
+        return fail(DMSGM_ERR_INVALID_ARG, "preprocessing: Gaussian size 0 or odd 3..15 with sigma > 0, "
+                    "median 0 or 1");
+    }
+    h->pre_gauss = opts.pre_gauss;
+    h->pre_sigma = opts.pre_sigma;
+    h->pre_median = opts.pre_median;
     h->state_bytes = need;
     if (opts.state_mem) {
         h->mem = opts.state_mem;
@@ -341,6 +365,15 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
                         "cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
         }
         h->owns_mem = true;
+    }
+    if (h->pre_gauss || h->pre_median) {   // two scratch frames for the preprocessing
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->pre_buf), 2 * size_t(W) * H);
+        if (e != cudaSuccess) {
+            if (h->owns_mem) cudaFree(h->mem);
+            delete h;
+            return fail(e == cudaErrorMemoryAllocation ? DMSGM_ERR_OOM : DMSGM_ERR_CUDA,
+                        "cudaMalloc of the preprocessing frames failed: %s", cudaGetErrorString(e));
+        }
     }
     carve(h);
     // Only the control block needs a defined value (the status word); the
@@ -368,9 +401,10 @@ int dmsgm_destroy(dmsgm_t h) {
     // Memory the handle owns may still be in use by queued work; memory the
     // caller lent it is the caller's to order.
     cudaError_t e = cudaSuccess;
-    if (h->owns_mem || h->stage.slots) e = cudaDeviceSynchronize();
+    if (h->owns_mem || h->stage.slots || h->pre_buf) e = cudaDeviceSynchronize();
     free_stage(h);
     if (h->owns_mem && h->mem) cudaFree(h->mem);
+    if (h->pre_buf) cudaFree(h->pre_buf);
     delete h;
     if (e != cudaSuccess) return fail(DMSGM_ERR_CUDA, "synchronize failed: %s", cudaGetErrorString(e));
     return DMSGM_OK;

@@ -65,6 +65,10 @@ struct dmsgm_ctx {
     int seq_tile_rows;           // 0: automatic
     int kernel;                  // DMSGM_KERNEL_*
     int mix_spread;              // 1: mixed variance carries the spread of the mixed means
+    int pre_gauss;               // preprocessing: Gaussian size (0: none)
+    double pre_sigma;            //   its sigma
+    int pre_median;              //   1: 3 x 3 median
+    uint8_t* pre_buf;            //   two scratch frames (NULL: no preprocessing)
     int last_kernel;             // kernel of the last dmsgm_process step
     int step_rpt;                // strip rows per warp of the per-tile kernel at tile_rows = 8 B (0: not chosen yet)
     int pipe_maps;               // state tensor maps of the pipelined kernel: 0 not yet, 1 ok, -1 unsupported
@@ -122,12 +126,16 @@ int launch_pipe(dmsgm_ctx* h, const CUtensorMap& frame_map, const StreamArgs& a,
 // instantiated in dmsgm_step_b<B>.cu).
 template <int B>
 cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
-                              const Coef& k, cudaStream_t s);
-extern template cudaError_t launch_step_block<1>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
-extern template cudaError_t launch_step_block<2>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
-extern template cudaError_t launch_step_block<4>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
-extern template cudaError_t launch_step_block<8>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
-extern template cudaError_t launch_step_block<16>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t);
+                              const Coef& k, cudaStream_t s, bool pdl);
+extern template cudaError_t launch_step_block<1>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<2>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<4>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<8>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<16>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+
+// Sec. 2.1 preprocessing of one frame (dmsgm_prefilter.cu).
+int launch_prefilter(const uint8_t* in_dev, uint8_t* out_dev, int W, int H, int gauss_size,
+                     double sigma, int median, cudaStream_t s);
 
 // Launch the batched persistent kernel (dmsgm_batch.cu).
 int launch_batch(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,

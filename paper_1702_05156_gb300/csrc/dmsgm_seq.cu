@@ -242,8 +242,9 @@ static int capacity(const dmsgm_ctx* h, int nw, int rpt) {
 static SeqShape pick_shape(const dmsgm_ctx* h, int sms) {
     static const SeqShape shapes[] = {{8, 1}, {16, 1}, {16, 2}, {16, 4}};
     // built for blocks 4 and 8 on whole block rows, without the
-    // mixture-variance option (those calls run per frame)
-    if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0) || h->mix_spread) return SeqShape{0, 0};
+    // mixture-variance option or preprocessing (those calls run per frame)
+    if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0) || h->mix_spread || h->pre_buf)
+        return SeqShape{0, 0};
     if (h->seq_tile_rows) {   // asked for: use it if the tiles fit the GPU at once
         for (const SeqShape& sh : shapes) {
             if (sh.nw * sh.rpt * h->B != h->seq_tile_rows) continue;

@@ -111,10 +111,9 @@ static int step_rpt_q8(const dmsgm_ctx* h) {
 // tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1) or (4, 2), (8, 2)}
 template <int B>
 cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
-                              const Coef& k, cudaStream_t s) {
+                              const Coef& k, cudaStream_t s, bool pdl) {
     const int q = h->tile_rows / B;   // 4, 8 or 16
     const bool f16 = h->prec == DMSGM_STATE_FP16;
-    const bool pdl = h->use_pdl != 0;
     if (q == 8 && h->step_rpt == 0)
         h->step_rpt = f16 ? step_rpt_q8<B, __half>(h) : step_rpt_q8<B, float>(h);
     const int rpt = q == 8 ? h->step_rpt : (q == 16 ? 2 : 1);

@@ -51,7 +51,8 @@ class Dmsgm:
     def __init__(self, width: int, height: int, block: int = 4, theta_s: float = 2.0,
                  theta_d: float = 4.0, age_max: int = 30, precision: str = "fp32",
                  tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None,
-                 seq_tile_rows: int = 0, kernel: str = "auto", mix_spread: bool = False):
+                 seq_tile_rows: int = 0, kernel: str = "auto", mix_spread: bool = False,
+                 prefilter: tuple | None = None):
         prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
         opts = _lib.dmsgm_opts()
         opts.precision = prec
@@ -61,6 +62,10 @@ class Dmsgm:
         opts.kernel = {"auto": DMSGM_KERNEL_AUTO, "tile": DMSGM_KERNEL_TILE,
                        "pipe": DMSGM_KERNEL_PIPE}[kernel]
         opts.mix_spread = 1 if mix_spread else 0
+        if prefilter is not None:   # (gauss_size, sigma, median): Sec. 2.1 preprocessing
+            opts.pre_gauss, opts.pre_sigma, opts.pre_median = (int(prefilter[0]),
+                                                               float(prefilter[1]),
+                                                               1 if prefilter[2] else 0)
         self._state_mem = state_mem
         if state_mem is not None:
             opts.state_mem = state_mem.data_ptr()
@@ -169,6 +174,19 @@ class Dmsgm:
             self.close()
         except Exception:
             pass
+
+
+def prefilter(frame: torch.Tensor, gauss_size: int = 5, sigma: float = 1.0, median: bool = True,
+              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The paper's preprocessing (Sec. 2.1) of one uint8 (H, W) CUDA frame:
+    N x N Gaussian blur (gauss_size 0: none), then the 3 x 3 median."""
+    assert frame.dtype == torch.uint8 and frame.is_cuda and frame.is_contiguous()
+    H, W = frame.shape
+    if out is None:
+        out = torch.empty_like(frame)
+    _lib.dmsgm_prefilter(frame.data_ptr(), out.data_ptr(), W, H, gauss_size, sigma,
+                         1 if median else 0, _stream_handle(stream))
+    return out
 
 
 def process_batch(models, frames, Hs, masks, stream=None, ctas: int = 0, use_pdl: bool = False):
