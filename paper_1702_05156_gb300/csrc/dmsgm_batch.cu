@@ -134,6 +134,31 @@ __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origi
     return true;
 }
 
+// One work item per CTA: as the per-frame kernel, the item's pixels, block
+// statistics and projections run before the previous step's kernel ends;
+// only the gathers, update and mask wait for it.
+template <int B, typename T, bool SPREAD>
+__device__ __forceinline__ bool run_single(const BatchItem& it, int t, const Origin* orig,
+                                           const uint8_t* tile, uint64_t* bar) {
+    constexpr int BPL = kLaneBlocks<B>;
+    const StreamArgs a = item_args(it);
+    int tx0, ty0;
+    item_origin(it, t, tx0, ty0);
+    Proj pj[1][BPL];
+    tile_project<B, kBatchWarps, 1>(a, it.coef, tx0, ty0, orig, pj);
+    const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
+    if (__syncthreads_or(!ok)) return false;
+    const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
+    Stats st[1][BPL];
+    tile_stats<B, kBatchWarps, 1>(a, tile, ty0, xin, st);
+    pdl_wait();
+    pdl_launch_dependents();
+    float muA[1][BPL], thr[1][BPL];
+    tile_update<B, T, kBatchWarps, 1, false, SPREAD>(a, tx0, ty0, pj, st, muA, thr);
+    tile_mask<B, kBatchWarps, 1>(a, tile, tx0, ty0, st, muA, thr);
+    return true;
+}
+
 // SPREAD: built to honour the streams' mixture-variance option (each item
 // still follows its own flag); without it the option's code is compiled out.
 template <int CAP, bool SPREAD>
@@ -150,6 +175,22 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4)
     }
     __syncthreads();
     int t = blockIdx.x;
+    if (gridDim.x >= p.total) {   // one work item per CTA (the launch is uniform in this)
+        if (t >= p.total) return;
+        if (threadIdx.x < 32) stage_item<CAP>(p, t, meta[0], orig[0], tile[0], &bar[0]);
+        __syncthreads();           // the item's stream and origins are visible
+        const BatchItem& it = p.item[meta[0][0]];
+        const int kind = (it.B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
+        bool ok;
+        switch (kind) {
+            case 0: ok = run_single<4, float, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
+            case 1: ok = run_single<4, __half, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
+            case 2: ok = run_single<8, float, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
+            default: ok = run_single<8, __half, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
+        }
+        if (!ok && threadIdx.x == 0) atomicOr(reinterpret_cast<int*>(it.mem), kStatusWaitTimeout);
+        return;
+    }
     // the first tile's pixels do not depend on the previous step
     if (t < p.total && threadIdx.x < 32) stage_item<CAP>(p, t, meta[0], orig[0], tile[0], &bar[0]);
     pdl_wait();
