@@ -427,7 +427,9 @@ def run_serving(args, dev):
 
 def run_extras(args, dev, stream):
     """Other configurations of the same kernel, reported beside the headline:
-    4K at block 4/8, FP32/FP16 state (one pass of 100 frames per step)."""
+    4K at block 4/8, FP32/FP16 state (one pass of 100 frames per step),
+    blocks 1, 2 and 16, the mixture-variance option, and the preprocessing
+    filters on their own."""
     import torch
     from paper_1702_05156_gb300 import dmsgm
     from paper_1702_05156_gb300.synth import make_stream, spec_for
@@ -437,41 +439,60 @@ def run_extras(args, dev, stream):
     W, H, T = 3840, 2160, args.extra_frames
     frames, Hs = make_stream(spec_for(W, H, T, seed=args.seed), device=dev)
     masks = dmsgm.new_mask(H, W, dev, n=T)
-    for B in (4, 8):
-        for prec in ("fp32", "fp16"):
-            m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl)
 
-            def one_pass():
-                for t in range(T):
-                    m.process(frames[t], Hs[t], masks[t], stream=stream)
-            with torch.cuda.stream(stream):
-                one_pass()
-            stream.synchronize()
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=stream):
-                one_pass()
-            with torch.cuda.stream(stream):
-                for _ in range(2):
-                    g.replay()
-            stream.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            reps = 5
-            e0.record(stream)
-            with torch.cuda.stream(stream):
-                for _ in range(reps):
-                    g.replay()
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            per = ms / 1e3 / (reps * T)
-            bpp = bytes_per_pixel(B, prec)
-            ach = bpp * W * H / per / 1e9
-            res[f"4k_b{B}_{prec}"] = {"mpix_s": round(W * H / per / 1e6, 1),
-                                      "frame_us": round(per * 1e6, 3),
-                                      "bytes_per_frame": int(bpp * W * H),
-                                      "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4)}
-            m.close()
+    def graph_time(one_pass, reps):
+        """Seconds per pass of a captured pass (two warm replays first)."""
+        with torch.cuda.stream(stream):
+            one_pass()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            one_pass()
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                g.replay()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    # 4K single stream: block 4 / 8, FP32 / FP16 state; then the widened
+    # forms: blocks 1, 2 and 16 (FP32, fewer frames for block 1 and 2) and
+    # the mixture-variance option (block 4)
+    runs = [(B, prec, False, T) for B in (4, 8) for prec in ("fp32", "fp16")]
+    runs += [(16, "fp32", False, T), (2, "fp32", False, min(T, 20)), (1, "fp32", False, min(T, 10)),
+             (4, "fp32", True, T)]
+    for B, prec, spread, n in runs:
+        m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl, mix_spread=spread)
+
+        def one_pass():
+            for t in range(n):
+                m.process(frames[t], Hs[t], masks[t], stream=stream)
+        per = graph_time(one_pass, 5 if n >= 50 else 3) / n
+        bpp = bytes_per_pixel(B, prec)
+        ach = bpp * W * H / per / 1e9
+        key = f"4k_b{B}_{prec}" + ("_spread" if spread else "")
+        res[key] = {"mpix_s": round(W * H / per / 1e6, 1), "frame_us": round(per * 1e6, 3),
+                    "bytes_per_frame": int(bpp * W * H), "achieved_gbs": round(ach, 1),
+                    "frac": round(ach / peak, 4)}
+        m.close()
+    # the Sec. 2.1 preprocessing on its own (5 x 5 Gaussian, sigma 1, then
+    # the 3 x 3 median), HD and 4K: 2 bytes per pixel (read + write)
+    for (w, h) in ((1920, 1080), (3840, 2160)):
+        src = frames[0, :h, :w].contiguous()
+        dst = torch.empty_like(src)
+        per = graph_time(lambda: [dmsgm.prefilter(src, 5, 1.0, True, out=dst, stream=stream)
+                                  for _ in range(20)], 5) / 20
+        ach = 2 * w * h / per / 1e9
+        res[f"prefilter_{w}x{h}"] = {"mpix_s": round(w * h / per / 1e6, 1),
+                                     "frame_us": round(per * 1e6, 3), "achieved_gbs": round(ach, 1),
+                                     "frac": round(ach / peak, 4)}
     del frames, masks
     torch.cuda.empty_cache()
     return res
