@@ -428,8 +428,9 @@ def run_serving(args, dev):
 def run_extras(args, dev, stream):
     """Other configurations of the same kernel, reported beside the headline:
     4K at block 4/8, FP32/FP16 state (one pass of 100 frames per step),
-    blocks 1, 2 and 16, the mixture-variance option, and the preprocessing
-    filters on their own."""
+    blocks 1, 2 and 16, the mixture-variance option, the preprocessing
+    filters on their own, and the step with the preprocessing fused into its
+    tile or run as a separate pass."""
     import torch
     from paper_1702_05156_gb300 import dmsgm
     from paper_1702_05156_gb300.synth import make_stream, spec_for
@@ -468,6 +469,8 @@ def run_extras(args, dev, stream):
     runs = [(B, prec, False, T) for B in (4, 8) for prec in ("fp32", "fp16")]
     runs += [(16, "fp32", False, T), (2, "fp32", False, min(T, 20)), (1, "fp32", False, min(T, 10)),
              (4, "fp32", True, T)]
+    if args.extra == 2:   # the preprocessing forms only
+        runs = []
     for B, prec, spread, n in runs:
         m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl, mix_spread=spread)
 
@@ -484,7 +487,7 @@ def run_extras(args, dev, stream):
         m.close()
     # the Sec. 2.1 preprocessing on its own (5 x 5 Gaussian, sigma 1, then
     # the 3 x 3 median), HD and 4K: 2 bytes per pixel (read + write)
-    for (w, h) in ((1920, 1080), (3840, 2160)):
+    for (w, h) in ((3840, 2160), (1920, 1080)):
         src = frames[0, :h, :w].contiguous()
         dst = torch.empty_like(src)
         per = graph_time(lambda: [dmsgm.prefilter(src, 5, 1.0, True, out=dst, stream=stream)
@@ -493,6 +496,28 @@ def run_extras(args, dev, stream):
         res[f"prefilter_{w}x{h}"] = {"mpix_s": round(w * h / per / 1e6, 1),
                                      "frame_us": round(per * 1e6, 3), "achieved_gbs": round(ach, 1),
                                      "frac": round(ach / peak, 4)}
+    # the step with the same preprocessing, block 4, FP32: filtered inside the
+    # step kernel's tile (fused), and as its own pass before the step
+    for (w, h, name) in ((3840, 2160, "4k"), (1920, 1080, "hd")):
+        n = min(T, 50)
+        if (w, h) == (W, H):
+            fr, hs = frames, Hs
+        else:
+            fr, hs = make_stream(spec_for(w, h, n, seed=args.seed), device=dev)
+        mk = dmsgm.new_mask(h, w, dev, n=n)
+        for sep in (False, True):
+            m = dmsgm.Dmsgm(w, h, 4, use_pdl=args.pdl, prefilter=(5, 1.0, True),
+                            prefilter_separate=sep)
+
+            def one_pass():
+                for t in range(n):
+                    m.process(fr[t], hs[t], mk[t], stream=stream)
+            per = graph_time(one_pass, 5) / n
+            res[f"{name}_b4_fp32_pre_" + ("separate" if sep else "fused")] = {
+                "mpix_s": round(w * h / per / 1e6, 1), "frame_us": round(per * 1e6, 3),
+                "fused": m.info().pre_fused}
+            m.close()
+        del fr, hs, mk
     del frames, masks
     torch.cuda.empty_cache()
     return res
@@ -564,7 +589,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--extra", type=int, default=1)
+    ap.add_argument("--extra", type=int, default=1,
+                    help="1: all extra configurations, 2: the preprocessing forms only, 0: none")
     ap.add_argument("--extra-frames", type=int, default=100)
     ap.add_argument("--ref-frames", type=int, default=4)
     ap.add_argument("--batched", type=int, default=1)

@@ -113,10 +113,17 @@ typedef struct {
                            (0: none, or odd 3..15) ...                       */
     double pre_sigma;   /* ... and its sigma (> 0)                            */
     int pre_median;     /* 1: then the 3 x 3 median.  With either filter the
-                           handle owns two W*H scratch frames, the step runs
-                           without programmatic dependent launch, and the
                            batched and multi-frame paths are not available
-                           (DMSGM_ERR_UNSUPPORTED / per-frame launches).     */
+                           (DMSGM_ERR_UNSUPPORTED / per-frame launches).
+                           For block 4 or 8 with the default tile_rows (32),
+                           Gaussian size 0, 3, 5 or 7 and mix_spread 0, the
+                           step kernel filters its own tile (the filter runs
+                           before the wait on the previous frame's kernel);
+                           otherwise the handle owns two W*H scratch frames,
+                           the filter runs as its own pass and the step
+                           without programmatic dependent launch.  Results
+                           are identical.                                    */
+    int pre_separate;   /* 1: always run the preprocessing as its own pass   */
 } dmsgm_opts;
 
 enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1, DMSGM_KERNEL_PIPE = 2 };
@@ -137,6 +144,7 @@ typedef struct {
                                     DMSGM_KERNEL_TILE or DMSGM_KERNEL_PIPE;
                                     0 before the first                        */
     int mix_spread;              /* dmsgm_opts.mix_spread in use              */
+    int pre_fused;               /* 1: the step kernel filters its own tile   */
 } dmsgm_info;
 
 /* Device bytes a handle needs for its state: a 256-byte control block, one

@@ -191,6 +191,18 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
         return fail(DMSGM_ERR_INVALID_ARG, "homography is not finite in FP32");
     int rc;
     bool pdl = h->use_pdl != 0;
+    if (h->pre_fused) {
+        // the step kernel filters its own tile (Sec. 2.1 preprocessing)
+        StreamArgs a;
+        fill_args(h, affine, mask_dev, &a);
+        const cudaError_t e = h->B == 4 ? launch_step_pre_block<4>(h, frame_dev, a, c, s, pdl)
+                                        : launch_step_pre_block<8>(h, frame_dev, a, c, s, pdl);
+        if (e != cudaSuccess)
+            return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+        h->last_kernel = DMSGM_KERNEL_TILE;
+        advance(h);
+        return DMSGM_OK;
+    }
     if (h->pre_buf) {
         // Sec. 2.1 preprocessing into the handle's scratch frame (two of
         // them, alternating, so a frame's filter never overwrites the pixels
@@ -345,7 +357,8 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     h->mix_spread = opts.mix_spread ? 1 : 0;
     if ((opts.pre_gauss && (opts.pre_gauss < 3 || opts.pre_gauss > 15 || opts.pre_gauss % 2 == 0 ||
                             !(opts.pre_sigma > 0.0) || !std::isfinite(opts.pre_sigma))) ||
-        (opts.pre_median != 0 && opts.pre_median != 1)) {
+        (opts.pre_median != 0 && opts.pre_median != 1) ||
+        (opts.pre_separate != 0 && opts.pre_separate != 1)) {
         delete h;
         return fail(DMSGM_ERR_INVALID_ARG, "preprocessing: Gaussian size 0 or odd 3..15 with sigma > 0, "
                     "median 0 or 1");
@@ -353,6 +366,14 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     h->pre_gauss = opts.pre_gauss;
     h->pre_sigma = opts.pre_sigma;
     h->pre_median = opts.pre_median;
+    if (h->pre_gauss || h->pre_median) {
+        if (!make_filt_args(h->pre_gauss, h->pre_sigma, h->pre_median, &h->filt, &h->pre_half)) {
+            delete h;
+            return fail(DMSGM_ERR_INVALID_ARG, "preprocessing: invalid Gaussian");
+        }
+        h->pre_fused = !opts.pre_separate && (B == 4 || B == 8) && tile_rows == 32 &&
+                       !h->mix_spread && h->pre_half <= 3;
+    }
     h->state_bytes = need;
     if (opts.state_mem) {
         h->mem = opts.state_mem;
@@ -366,7 +387,7 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
         }
         h->owns_mem = true;
     }
-    if (h->pre_gauss || h->pre_median) {   // two scratch frames for the preprocessing
+    if ((h->pre_gauss || h->pre_median) && !h->pre_fused) {   // two scratch frames for the separate pass
         cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->pre_buf), 2 * size_t(W) * H);
         if (e != cudaSuccess) {
             if (h->owns_mem) cudaFree(h->mem);
@@ -646,6 +667,7 @@ int dmsgm_get_info(dmsgm_t h, dmsgm_info* o) {
     o->kernel = h->kernel;
     o->last_kernel = h->last_kernel;
     o->mix_spread = h->mix_spread;
+    o->pre_fused = h->pre_fused;
     return DMSGM_OK;
 }
 

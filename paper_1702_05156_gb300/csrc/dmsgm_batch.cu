@@ -266,7 +266,7 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
         if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0))
             return fail(DMSGM_ERR_UNSUPPORTED,
                         "batched streams take blocks 4 and 8 on whole block rows (stream %d)", i);
-        if (h->pre_buf)
+        if (h->pre_gauss || h->pre_median)
             return fail(DMSGM_ERR_UNSUPPORTED, "batched streams take no preprocessing (stream %d)", i);
         BatchItem& it = p.item[i];
         it.frame = frames[i];

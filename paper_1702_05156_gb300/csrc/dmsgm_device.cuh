@@ -803,7 +803,9 @@ __device__ __forceinline__ int strip_rows(const StreamArgs& a, int ty0, int s) {
 }
 
 // Block statistics of the lane's blocks (Sec. 2.2 M_i, and the extremes for
-// V_i), over the pixels inside the frame.
+// V_i), over the pixels inside the frame.  Lanes past the frame's right edge
+// read whatever the staged tile holds there: their statistics are never used
+// (no state store, no mask bit, no vote).
 template <int B, int NW, int RPT>
 __device__ __forceinline__ void tile_stats(const StreamArgs& a, const uint8_t* tile, int ty0,
                                            bool xin, Stats (&st)[RPT][kLaneBlocks<B>]) {
@@ -814,7 +816,7 @@ __device__ __forceinline__ void tile_stats(const StreamArgs& a, const uint8_t* t
         const int vr = strip_rows<B>(a, ty0, s);
         if constexpr (B == 1) {
             // one pixel per block: M = min = max = the pixel
-            const uint2 v = xin ? tile_words<B>(tile, s, lane) : make_uint2(0u, 0u);
+            const uint2 v = tile_words<B>(tile, s, lane);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const float f = byte_f(j < 4 ? v.x : v.y, j & 3);
@@ -827,7 +829,7 @@ __device__ __forceinline__ void tile_stats(const StreamArgs& a, const uint8_t* t
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 if (i >= vr) break;
-                const uint2 v = xin ? tile_words<B>(tile, B * s + i, lane) : make_uint2(0u, 0u);
+                const uint2 v = tile_words<B>(tile, B * s + i, lane);
                 const uint32_t w[2] = {v.x, v.y};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -855,7 +857,7 @@ __device__ __forceinline__ void tile_stats(const StreamArgs& a, const uint8_t* t
             uint32_t lw[B], rw[B];
 #pragma unroll
             for (int i = 0; i < B; ++i) {
-                const uint2 v = xin ? tile_words<B>(tile, B * s + i, lane) : make_uint2(0u, 0u);
+                const uint2 v = tile_words<B>(tile, B * s + i, lane);
                 lw[i] = v.x;
                 rw[i] = v.y;
             }

@@ -11,6 +11,7 @@
 
 #include "dmsgm.h"
 #include "dmsgm_device.cuh"
+#include "dmsgm_filter.cuh"
 
 namespace dmsgm {
 
@@ -68,7 +69,10 @@ struct dmsgm_ctx {
     int pre_gauss;               // preprocessing: Gaussian size (0: none)
     double pre_sigma;            //   its sigma
     int pre_median;              //   1: 3 x 3 median
-    uint8_t* pre_buf;            //   two scratch frames (NULL: no preprocessing)
+    int pre_half;                //   Gaussian half-size after weight quantisation (0: no blur)
+    int pre_fused;               //   1: the step kernel filters its own tile
+    dmsgm::FiltArgs filt;        //   the filter's weights
+    uint8_t* pre_buf;            //   two scratch frames of the separate pass (NULL: none)
     int last_kernel;             // kernel of the last dmsgm_process step
     int step_rpt;                // strip rows per warp of the per-tile kernel at tile_rows = 8 B (0: not chosen yet)
     int pipe_maps;               // state tensor maps of the pipelined kernel: 0 not yet, 1 ok, -1 unsupported
@@ -132,6 +136,19 @@ extern template cudaError_t launch_step_block<2>(dmsgm_ctx*, const CUtensorMap&,
 extern template cudaError_t launch_step_block<4>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
 extern template cudaError_t launch_step_block<8>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
 extern template cudaError_t launch_step_block<16>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+
+// The preprocessing filter's weights (dmsgm_prefilter.cu): false if the
+// Gaussian size or sigma is invalid; *half is 0 when the quantised blur is the
+// identity.
+bool make_filt_args(int gauss_size, double sigma, int median, FiltArgs* f, int* half);
+
+// The per-tile frame step with the preprocessing fused in, for block sizes 4
+// and 8 with 32-row tiles and Gaussian half-sizes up to 3 (dmsgm_step_pre.cuh).
+template <int B>
+cudaError_t launch_step_pre_block(const dmsgm_ctx* h, const uint8_t* frame, const StreamArgs& a,
+                                  const Coef& k, cudaStream_t s, bool pdl);
+extern template cudaError_t launch_step_pre_block<4>(const dmsgm_ctx*, const uint8_t*, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_pre_block<8>(const dmsgm_ctx*, const uint8_t*, const StreamArgs&, const Coef&, cudaStream_t, bool);
 
 // Sec. 2.1 preprocessing of one frame (dmsgm_prefilter.cu).
 int launch_prefilter(const uint8_t* in_dev, uint8_t* out_dev, int W, int H, int gauss_size,

@@ -52,6 +52,9 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
     tile_stats<B, NW, RPT>(a, tile, ty0, xin, st);
     tile_project<B, NW, RPT>(a, k, tx0, ty0, orig, pj);
     pdl_wait();
+    // Triggered here, not at entry: an earlier trigger lets the CTAs of
+    // several later frames start, and their pixel loads and statistics then
+    // compete with this frame's update, the recurrence's critical path.
     pdl_launch_dependents();
     float muA[RPT][BPL], thr[RPT][BPL];
     tile_update<B, T, NW, RPT, false, SPREAD>(a, tx0, ty0, pj, st, muA, thr);

@@ -52,7 +52,7 @@ class Dmsgm:
                  theta_d: float = 4.0, age_max: int = 30, precision: str = "fp32",
                  tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None,
                  seq_tile_rows: int = 0, kernel: str = "auto", mix_spread: bool = False,
-                 prefilter: tuple | None = None):
+                 prefilter: tuple | None = None, prefilter_separate: bool = False):
         prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
         opts = _lib.dmsgm_opts()
         opts.precision = prec
@@ -66,6 +66,7 @@ class Dmsgm:
             opts.pre_gauss, opts.pre_sigma, opts.pre_median = (int(prefilter[0]),
                                                                float(prefilter[1]),
                                                                1 if prefilter[2] else 0)
+            opts.pre_separate = 1 if prefilter_separate else 0
         self._state_mem = state_mem
         if state_mem is not None:
             opts.state_mem = state_mem.data_ptr()
