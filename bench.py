@@ -280,7 +280,7 @@ def run_gpu(args):
         avg_launch_s = ms / 1e3 / (args.steps * T)
         achieved = per_launch_bytes / avg_launch_s / 1e9
         tag = f"dmsgm_step_kernel {W}x{H} B{B} {prec}"
-        traffic = ncu_traffic(tag, pbuild._fingerprint())
+        traffic = ncu_traffic(tag, pbuild.kernel_fingerprint(f"dmsgm_step_b{B}.cu"))
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),

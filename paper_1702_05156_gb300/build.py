@@ -43,6 +43,31 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
+def kernel_fingerprint(tu: str) -> str:
+    """Hash of one translation unit under csrc/, the repository headers it
+    includes (transitively) and the compile flags: it changes exactly when the
+    code compiled into that unit's kernels does, not when other units do."""
+    seen, todo = [], [os.path.join(CSRC, tu)]
+    while todo:
+        p = todo.pop()
+        if p in seen or not os.path.exists(p):
+            continue
+        seen.append(p)
+        with open(p, "rb") as f:
+            for line in f.read().decode(errors="replace").splitlines():
+                line = line.strip()
+                if line.startswith("#include \""):
+                    name = line.split('"')[1]
+                    todo += [os.path.join(d, name) for d in (CSRC, INCLUDE)]
+    h = hashlib.sha256()
+    for p in sorted(seen):
+        with open(p, "rb") as f:
+            h.update(os.path.relpath(p, ROOT).encode())
+            h.update(f.read())
+    h.update(" ".join(ARCH + [f for f in FLAGS if f not in (INCLUDE, CSRC)]).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     """Compile every .cu under csrc/ and link libdmsgm.so; returns its path."""
     fp = _fingerprint() + " ".join(extra_flags or [])
