@@ -1,5 +1,6 @@
-"""FP64 CPU oracle of the DMSGM block-grid step (arXiv:1702.05156, Sec. 2.2-2.4)
-and of the preprocessing filters (Sec. 2.1).
+"""FP64 CPU oracle of the DMSGM block-grid step (arXiv:1702.05156, Sec. 2.2-2.4),
+of the preprocessing filters (Sec. 2.1) and of the motion-estimation front
+end that produces the homography (Sec. 2.4, Sec. 3.1.3).
 
 TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
 baseline leg use it to check and time the CUDA library.  The product package
@@ -7,6 +8,15 @@ never imports it.
 """
 from .oracle import (  # noqa: F401
     DIAG,
+    HOMOG_DEFAULTS,
+    corners,
+    estimate_homography,
+    pyr_down,
+    ransac,
+    sample4,
+    score_map,
+    splitmix64,
+    track,
     OracleState,
     build_oracle,
     gauss_weights,

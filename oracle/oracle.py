@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dmsgm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "homog_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -32,11 +33,11 @@ DIAG = dict(M=0, NOSRC=1, WSUM=2, MU_A=3, VAR_A=4, XAGE_A=5, MU_C=6, VAR_C=7,
 def build_oracle(force: bool = False) -> str:
     """Compile ``liboracle.so`` with gcc (no -ffast-math, no FP contraction)."""
     stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+             or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(p) for p in _SRCS))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -187,3 +188,151 @@ def prefilter(frame: np.ndarray, *, gauss_size: int = 5, sigma: float = 1.0,
     if lib.oracle_median3(w, h, _ptr(blur), _ptr(out)):
         raise ValueError("invalid size")
     return out
+
+
+# ----------------------------------------------------------------------------
+# Motion-estimation front end (homog_oracle.c, readings M1-M8): corners,
+# pyramidal tracking, RANSAC homography.
+
+def _homog_sigs(lib):
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ho_score_map.restype = None
+    lib.ho_score_map.argtypes = [P, I, I, I, P]
+    lib.ho_corners.restype = I
+    lib.ho_corners.argtypes = [P, I, I, I, D, D, I, P, P, P]
+    lib.ho_pyr_down.restype = None
+    lib.ho_pyr_down.argtypes = [P, I, I, P]
+    lib.ho_track.restype = I
+    lib.ho_track.argtypes = [P, P, I, I, I, I, I, D, D, P, I, P, P]
+    lib.ho_splitmix64.restype = ctypes.c_uint64
+    lib.ho_splitmix64.argtypes = [ctypes.c_uint64]
+    lib.ho_sample4.restype = I
+    lib.ho_sample4.argtypes = [ctypes.c_uint64, I, I, P]
+    lib.ho_ransac.restype = I
+    lib.ho_ransac.argtypes = [P, P, I, I, I, I, D, ctypes.c_uint64, P, P, P]
+    lib.ho_estimate.restype = I
+    lib.ho_estimate.argtypes = [P, P, I, I, I, D, D, I, I, I, I, D, D, I, D, ctypes.c_uint64,
+                                P, P, P]
+    return lib
+
+
+_homog_ready = False
+
+
+def _hlib():
+    global _homog_ready
+    lib = _load()
+    if not _homog_ready:
+        _homog_sigs(lib)
+        _homog_ready = True
+    return lib
+
+
+# defaults: the paper's window (20 x 20, read as half-width 10) and 5 levels;
+# the others are the usual defaults of the methods
+HOMOG_DEFAULTS = dict(block_size=3, quality=0.01, min_distance=10.0, max_corners=500, levels=5,
+                      win_half=10, max_iters=30, eps=0.01, min_eig=1e-3, ransac_iters=2000,
+                      thresh=3.0, seed=0)
+
+
+def score_map(img: np.ndarray, block_size: int = 3) -> np.ndarray:
+    """M1: the FP32 Shi-Tomasi score of every pixel."""
+    lib = _hlib()
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    h, w = img.shape
+    out = np.empty((h, w), dtype=np.float32)
+    lib.ho_score_map(_ptr(img), w, h, int(block_size), _ptr(out))
+    return out
+
+
+def corners(img: np.ndarray, block_size: int = 3, quality: float = 0.01,
+            min_distance: float = 10.0, max_corners: int = 500):
+    """M2-M4: corner pixel indices (m x 2, x then y), strongest first, their
+    scores and the number of candidates before the cap."""
+    lib = _hlib()
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    h, w = img.shape
+    xy = np.zeros((max_corners, 2), dtype=np.int32)
+    sc = np.zeros(max_corners, dtype=np.float32)
+    nc = ctypes.c_int(0)
+    m = lib.ho_corners(_ptr(img), w, h, int(block_size), float(quality), float(min_distance),
+                       int(max_corners), _ptr(xy), _ptr(sc), ctypes.byref(nc))
+    if m < 0:
+        raise ValueError("invalid corner arguments")
+    return xy[:m].copy(), sc[:m].copy(), nc.value
+
+
+def pyr_down(img: np.ndarray) -> np.ndarray:
+    """M5: one pyramid step."""
+    lib = _hlib()
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    h, w = img.shape
+    out = np.empty(((h + 1) // 2, (w + 1) // 2), dtype=np.uint8)
+    lib.ho_pyr_down(_ptr(img), w, h, _ptr(out))
+    return out
+
+
+def track(prev: np.ndarray, cur: np.ndarray, pts: np.ndarray, levels: int = 5,
+          win_half: int = 10, max_iters: int = 30, eps: float = 0.01, min_eig: float = 1e-3):
+    """M6: pyramidal Lucas-Kanade of points (n x 2 pixel indices) from prev
+    to cur: tracked positions (n x 2) and status (n, 1 = tracked)."""
+    lib = _hlib()
+    prev = np.ascontiguousarray(prev, dtype=np.uint8)
+    cur = np.ascontiguousarray(cur, dtype=np.uint8)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    h, w = prev.shape
+    out = np.empty_like(pts)
+    st = np.zeros(len(pts), dtype=np.uint8)
+    if lib.ho_track(_ptr(prev), _ptr(cur), w, h, int(levels), int(win_half), int(max_iters),
+                    float(eps), float(min_eig), _ptr(pts), len(pts), _ptr(out), _ptr(st)):
+        raise ValueError("invalid tracking arguments")
+    return out, st
+
+
+def splitmix64(z: int) -> int:
+    return int(_hlib().ho_splitmix64(ctypes.c_uint64(z & (2 ** 64 - 1))))
+
+
+def sample4(seed: int, m: int, n: int) -> np.ndarray | None:
+    idx = np.zeros(4, dtype=np.int32)
+    rc = _hlib().ho_sample4(ctypes.c_uint64(seed), int(m), int(n), _ptr(idx))
+    return None if rc else idx
+
+
+def ransac(src: np.ndarray, dst: np.ndarray, width: int, height: int, iters: int = 2000,
+           thresh: float = 3.0, seed: int = 0):
+    """M7-M8: the homography src -> dst (pixel coordinates): (H 3x3, inlier
+    mask, inlier count, best hypothesis); H is None when no model exists."""
+    lib = _hlib()
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    dst = np.ascontiguousarray(dst, dtype=np.float64).reshape(-1, 2)
+    n = len(src)
+    Hm = np.zeros(9)
+    inl = np.zeros(max(n, 1), dtype=np.uint8)
+    best = ctypes.c_int(-1)
+    cnt = lib.ho_ransac(_ptr(src), _ptr(dst), n, int(width), int(height), int(iters),
+                        float(thresh), ctypes.c_uint64(seed), _ptr(Hm), _ptr(inl),
+                        ctypes.byref(best))
+    if cnt < 0:
+        return None, inl[:n], 0, -1
+    return Hm.reshape(3, 3), inl[:n].astype(bool), cnt, best.value
+
+
+def estimate_homography(prev: np.ndarray, cur: np.ndarray, **kw):
+    """The front end end to end: (H mapping cur pixel centres to prev ones,
+    inlier count, corners, tracked points); H is None on failure."""
+    p = dict(HOMOG_DEFAULTS)
+    p.update(kw)
+    lib = _hlib()
+    prev = np.ascontiguousarray(prev, dtype=np.uint8)
+    cur = np.ascontiguousarray(cur, dtype=np.uint8)
+    h, w = prev.shape
+    Hm = np.zeros(9)
+    nc, nt = ctypes.c_int(0), ctypes.c_int(0)
+    cnt = lib.ho_estimate(_ptr(prev), _ptr(cur), w, h, p["block_size"], p["quality"],
+                          p["min_distance"], p["max_corners"], p["levels"], p["win_half"],
+                          p["max_iters"], p["eps"], p["min_eig"], p["ransac_iters"], p["thresh"],
+                          ctypes.c_uint64(p["seed"]), _ptr(Hm), ctypes.byref(nc), ctypes.byref(nt))
+    if cnt < 0:
+        return None, 0, nc.value, nt.value
+    return Hm.reshape(3, 3), cnt, nc.value, nt.value
