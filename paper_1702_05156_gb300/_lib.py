@@ -36,7 +36,11 @@ EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm
            "dmsgm_process_batch_ex", "dmsgm_process_batch_host",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
            "dmsgm_status", "dmsgm_selftest_wait", "dmsgm_prefilter", "dmsgm_last_error",
-           "dmsgm_version")
+           "dmsgm_version",
+           # include/dmsgm_homog.h
+           "dmsgm_homog_default_params", "dmsgm_homog_create", "dmsgm_homog_estimate",
+           "dmsgm_homog_corners", "dmsgm_homog_track", "dmsgm_homog_ransac",
+           "dmsgm_homog_destroy")
 
 
 class dmsgm_opts(ctypes.Structure):
@@ -108,6 +112,13 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_prefilter": (I, [P, P, I, I, I, ctypes.c_double, I, P]),
             "dmsgm_last_error": (ctypes.c_char_p, []),
             "dmsgm_version": (ctypes.c_char_p, []),
+            "dmsgm_homog_default_params": (None, [P]),
+            "dmsgm_homog_create": (I, [I, I, P, P]),
+            "dmsgm_homog_estimate": (I, [P, P, P, P, P, P]),
+            "dmsgm_homog_corners": (I, [P, P, P, P, P, P, P]),
+            "dmsgm_homog_track": (I, [P, P, P, P, I, P, P, P]),
+            "dmsgm_homog_ransac": (I, [P, P, P, I, P, P, P, P]),
+            "dmsgm_homog_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -239,3 +250,76 @@ def dmsgm_last_error() -> str:
 
 def dmsgm_version() -> str:
     return load_library().dmsgm_version().decode()
+
+
+# ----------------------------------------------------------- include/dmsgm_homog.h
+class dmsgm_homog_params(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int), ("quality", ctypes.c_double),
+                ("min_distance", ctypes.c_double), ("max_corners", ctypes.c_int),
+                ("levels", ctypes.c_int), ("win_half", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("eps", ctypes.c_double),
+                ("min_eig", ctypes.c_double), ("ransac_iters", ctypes.c_int),
+                ("thresh", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
+class dmsgm_homog_result(ctypes.Structure):
+    _fields_ = [("corners", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("tracked", ctypes.c_int), ("inliers", ctypes.c_int), ("best", ctypes.c_int)]
+
+
+def dmsgm_homog_default_params() -> dmsgm_homog_params:
+    p = dmsgm_homog_params()
+    load_library().dmsgm_homog_default_params(ctypes.byref(p))
+    return p
+
+
+def dmsgm_homog_create(width: int, height: int, params: dmsgm_homog_params | None = None):
+    h = ctypes.c_void_p()
+    _check(load_library().dmsgm_homog_create(width, height,
+                                             ctypes.byref(params) if params is not None else None,
+                                             ctypes.byref(h)))
+    return h
+
+
+def dmsgm_homog_destroy(h):
+    _check(load_library().dmsgm_homog_destroy(h))
+
+
+def dmsgm_homog_estimate(h, prev_dev: int, cur_dev: int, stream: int = 0):
+    Hm = np.zeros(9)
+    res = dmsgm_homog_result()
+    _check(load_library().dmsgm_homog_estimate(h, prev_dev, cur_dev, Hm.ctypes.data,
+                                               ctypes.byref(res), stream))
+    return Hm.reshape(3, 3), res
+
+
+def dmsgm_homog_corners(h, img_dev: int, max_corners: int, stream: int = 0):
+    xy = np.zeros((max_corners, 2), dtype=np.int32)
+    sc = np.zeros(max_corners, dtype=np.float32)
+    n, nc = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load_library().dmsgm_homog_corners(h, img_dev, xy.ctypes.data, sc.ctypes.data,
+                                              ctypes.byref(n), ctypes.byref(nc), stream))
+    return xy[:n.value].copy(), sc[:n.value].copy(), nc.value
+
+
+def dmsgm_homog_track(h, prev_dev: int, cur_dev: int, pts, stream: int = 0):
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float32).reshape(-1, 2))
+    n = len(pts)
+    out = np.zeros((n, 2), dtype=np.float32)
+    st = np.zeros(n, dtype=np.uint8)
+    _check(load_library().dmsgm_homog_track(h, prev_dev, cur_dev, pts.ctypes.data, n,
+                                            out.ctypes.data, st.ctypes.data, stream))
+    return out, st
+
+
+def dmsgm_homog_ransac(h, src, dst, stream: int = 0):
+    src = np.ascontiguousarray(np.asarray(src, dtype=np.float64).reshape(-1, 2))
+    dst = np.ascontiguousarray(np.asarray(dst, dtype=np.float64).reshape(-1, 2))
+    n = len(src)
+    Hm = np.zeros(9)
+    inl = np.zeros(max(n, 1), dtype=np.uint8)
+    res = dmsgm_homog_result()
+    _check(load_library().dmsgm_homog_ransac(h, src.ctypes.data, dst.ctypes.data, n,
+                                             Hm.ctypes.data, inl.ctypes.data, ctypes.byref(res),
+                                             stream))
+    return Hm.reshape(3, 3), inl[:n].astype(bool), res

@@ -26,6 +26,12 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 
+# Per-unit flags: the RANSAC unit evaluates FP64 expressions exactly as
+# written (no fused multiply-add), so its inlier counts equal the reference
+# evaluation of the same operations.
+UNIT_FLAGS = {"dmsgm_homog_ransac.cu": ["-fmad=false"]}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -40,6 +46,7 @@ def _fingerprint() -> str:
             h.update(os.path.relpath(p, ROOT).encode())
             h.update(f.read())
     h.update(" ".join(ARCH + [f for f in FLAGS if f not in (INCLUDE, CSRC)]).encode())
+    h.update(repr(sorted(UNIT_FLAGS.items())).encode())
     return h.hexdigest()
 
 
@@ -81,7 +88,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(src, obj):
-        cmd = [NVCC, *ARCH, *FLAGS, *(extra_flags or []), "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *UNIT_FLAGS.get(os.path.basename(src), []),
+               *(extra_flags or []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)

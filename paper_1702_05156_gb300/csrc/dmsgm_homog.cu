@@ -1,0 +1,782 @@
+// dmsgm_homog.cu -- the motion-estimation front end on the GPU: Shi-Tomasi
+// corners of the previous frame, Bouguet's pyramidal Lucas-Kanade into the
+// current one (Sec. 2.4, Sec. 3.1.3 and the motion-compensation appendix of
+// arXiv:1702.05156), and the C ABI of dmsgm_homog.h.  The RANSAC that turns
+// the tracked pairs into the homography is in dmsgm_homog_ransac.cu.
+//
+// Corners, one pass per step, all on the device (counts and cuts pass through
+// a control block, no host round trip):
+//   score    tiled: the frame tile with its halo and the Sobel gradients in
+//            shared memory, the structure tensor summed over the window, the
+//            score in FP32 in the fixed order of IEEE operations the method
+//            defines, and the frame maximum (atomicMax on the float bits,
+//            scores being >= 0);
+//   select   the strongest 8192 local maxima exactly, without sorting them
+//            all: a histogram of the scores' high 16 bits finds the bucket of
+//            the cut, a second one of the low 16 bits inside it the cut value;
+//            candidates above it are kept, those at it (ties) are ordered by
+//            index;
+//   sort     one CTA, bitonic, in shared memory: (score desc, index asc);
+//   spacing  one warp takes the sorted candidates 32 at a time: each lane
+//            checks a spacing grid of the kept corners (cells of
+//            ceil(min_distance) pixels, so that a conflict lies in the 3 x 3
+//            neighbouring cells) and the earlier lanes of its group, and the
+//            group is resolved in order with warp shuffles.
+// Tracking: one warp per point; per level the window's previous-frame
+// samples (intensity and both gradients, bilinear) stay in shared memory for
+// the iterations, which sample the current frame and reduce with shuffles.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "dmsgm_homog.cuh"
+
+namespace dmsgm {
+
+__device__ __forceinline__ int clampi_d(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// ---------------------------------------------------------------- scores
+constexpr int kScTX = 32, kScTY = 8;
+
+template <int BS>
+__global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* __restrict__ img, int W,
+                                                       int H, float* __restrict__ score,
+                                                       uint32_t* __restrict__ ctrl) {
+    constexpr int r = BS / 2, R = r + 1;
+    constexpr int IW = kScTX + 2 * R, IH = kScTY + 2 * R;   // staged pixels (clamped)
+    constexpr int GW = kScTX + 2 * r, GH = kScTY + 2 * r;   // gradients of the window positions
+    __shared__ int px[IH][IW];
+    __shared__ int gx[GH][GW], gy[GH][GW];
+    const int x0 = blockIdx.x * kScTX, y0 = blockIdx.y * kScTY;
+    for (int i = threadIdx.x; i < IW * IH; i += 256) {
+        const int yy = i / IW, xx = i - yy * IW;
+        px[yy][xx] = img[size_t(clampi_d(y0 - R + yy, 0, H - 1)) * W + clampi_d(x0 - R + xx, 0, W - 1)];
+    }
+    __syncthreads();
+    // the gradient of a window position is that of the clamped position
+    for (int i = threadIdx.x; i < GW * GH; i += 256) {
+        const int yy = i / GW, xx = i - yy * GW;
+        const int cx = clampi_d(x0 - r + xx, 0, W - 1) - (x0 - R);
+        const int cy = clampi_d(y0 - r + yy, 0, H - 1) - (y0 - R);
+        gx[yy][xx] = (px[cy - 1][cx + 1] + 2 * px[cy][cx + 1] + px[cy + 1][cx + 1]) -
+                     (px[cy - 1][cx - 1] + 2 * px[cy][cx - 1] + px[cy + 1][cx - 1]);
+        gy[yy][xx] = (px[cy + 1][cx - 1] + 2 * px[cy + 1][cx] + px[cy + 1][cx + 1]) -
+                     (px[cy - 1][cx - 1] + 2 * px[cy - 1][cx] + px[cy - 1][cx + 1]);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % kScTX, ty = threadIdx.x / kScTX;
+    const int x = x0 + tx, y = y0 + ty;
+    uint32_t bits = 0;
+    if (x < W && y < H) {
+        int A = 0, B = 0, C = 0;
+#pragma unroll
+        for (int j = 0; j < BS; ++j)
+#pragma unroll
+            for (int i = 0; i < BS; ++i) {
+                const int a = gx[ty + j][tx + i], b = gy[ty + j][tx + i];
+                A += a * a;
+                B += a * b;
+                C += b * b;
+            }
+        const float fa = __int2float_rn(A), fb = __int2float_rn(B), fc = __int2float_rn(C);
+        const float t = __fadd_rn(fa, fc);
+        const float d = __fsub_rn(fa, fc);
+        const float e = __fmul_rn(d, d);
+        const float f = __fmul_rn(fb, fb);
+        const float g = __fmul_rn(4.0f, f);
+        const float rr = __fsqrt_rn(__fadd_rn(e, g));
+        float s = __fmul_rn(0.5f, __fsub_rn(t, rr));
+        s = s > 0.0f ? s : 0.0f;
+        score[size_t(y) * W + x] = s;
+        bits = __float_as_uint(s);
+    }
+    bits = __reduce_max_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicMax(&ctrl[kCtrlMaxBits], bits);
+}
+
+// ---------------------------------------------------------------- candidates
+// The candidate predicate at (x, y): an interior local maximum above the cut.
+__device__ __forceinline__ bool ho_is_cand(const float* __restrict__ s, int W, int H, int x, int y,
+                                           float thr, uint32_t& bits) {
+    if (x < 1 || y < 1 || x > W - 2 || y > H - 2) return false;
+    const float* row = s + size_t(y) * W + x;
+    const float v = row[0];
+    if (!(v > thr)) return false;
+#pragma unroll
+    for (int j = -1; j <= 1; ++j)
+#pragma unroll
+        for (int i = -1; i <= 1; ++i)
+            if ((i || j) && row[j * W + i] > v) return false;
+    bits = __float_as_uint(v);
+    return true;
+}
+
+// mode 0: histogram of the high 16 bits and the count; 1: histogram of the
+// low 16 bits inside the cut's bucket; 2: collect the keys above / at the cut
+__global__ void __launch_bounds__(256) ho_cand_kernel(const float* __restrict__ s, int W, int H,
+                                                      double quality, int mode, uint32_t* ctrl,
+                                                      uint32_t* hist_hi, uint32_t* hist_lo,
+                                                      unsigned long long* keys) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (mode > 0 && mode < 2 && ctrl[kCtrlTakeAll]) return;
+    const float thr = __fmul_rn(__double2float_rn(quality), __uint_as_float(ctrl[kCtrlMaxBits]));
+    uint32_t bits = 0;
+    if (x >= W || y >= H || !ho_is_cand(s, W, H, x, y, thr, bits)) return;
+    if (mode == 0) {
+        atomicAdd(&hist_hi[bits >> 16], 1u);
+        atomicAdd(&ctrl[kCtrlCand], 1u);
+    } else if (mode == 1) {
+        if ((bits >> 16) == ctrl[kCtrlHiCut]) atomicAdd(&hist_lo[bits & 0xFFFFu], 1u);
+    } else {
+        const unsigned long long key =
+            (static_cast<unsigned long long>(~bits) << 32) | static_cast<uint32_t>(y * W + x);
+        const uint32_t cut = ctrl[kCtrlCut];
+        if (ctrl[kCtrlTakeAll] || bits > cut) {
+            const uint32_t k = atomicAdd(&ctrl[kCtrlNGt], 1u);   // < kHoKmax by the cut
+            if (k < uint32_t(kHoKmax)) keys[k] = key;
+            else ctrl[kCtrlOverflow] = 1;
+        } else if (bits == cut) {
+            const uint32_t k = atomicAdd(&ctrl[kCtrlNEq], 1u);
+            if (k < uint32_t(kHoTieCap)) keys[kHoKmax + k] = key;
+            else ctrl[kCtrlOverflow] = 1;
+        }
+    }
+}
+
+// Inclusive-from-the-top scan of a 65536-bucket histogram by one CTA of 1024
+// threads: the bucket b where the count of buckets above b is < need and
+// that count plus hist[b] reaches it; *above = that count.
+__device__ void ho_find_cut(const uint32_t* hist, uint32_t need, uint32_t* cut, uint32_t* above) {
+    __shared__ uint32_t warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int top = 65535 - 64 * t;   // this thread's buckets: top, top - 1, .., top - 63
+    uint32_t local = 0;
+    for (int b = 0; b < 64; ++b) local += hist[top - b];
+    // exclusive prefix over threads (thread 0 holds the highest buckets)
+    uint32_t v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    if (lane == 31) warp_sum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_sum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t n = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += n;
+        }
+        warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = (warp ? warp_sum[warp - 1] : 0u) + v - local;
+    if (before < need && before + local >= need) {
+        uint32_t cum = before;
+        for (int b = 0; b < 64; ++b) {
+            const uint32_t h = hist[top - b];
+            if (cum + h >= need) {
+                *cut = uint32_t(top - b);
+                *above = cum;
+                break;
+            }
+            cum += h;
+        }
+    }
+}
+
+// stage 0: after the high histogram; stage 1: after the low one
+__global__ void __launch_bounds__(1024) ho_select_kernel(int stage, uint32_t* ctrl,
+                                                         const uint32_t* hist_hi,
+                                                         const uint32_t* hist_lo) {
+    __shared__ uint32_t cut, above;
+    if (threadIdx.x == 0) {
+        cut = 0;
+        above = 0;
+    }
+    __syncthreads();
+    if (stage == 0) {
+        if (ctrl[kCtrlCand] <= uint32_t(kHoKmax)) {
+            if (threadIdx.x == 0) ctrl[kCtrlTakeAll] = 1;
+            return;
+        }
+        ho_find_cut(hist_hi, kHoKmax, &cut, &above);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ctrl[kCtrlHiCut] = cut;
+            ctrl[kCtrlAboveHi] = above;
+        }
+    } else {
+        if (ctrl[kCtrlTakeAll]) return;
+        const uint32_t a = ctrl[kCtrlAboveHi];
+        ho_find_cut(hist_lo, kHoKmax - a, &cut, &above);
+        __syncthreads();
+        if (threadIdx.x == 0) ctrl[kCtrlCut] = (ctrl[kCtrlHiCut] << 16) | cut;
+    }
+}
+
+// one CTA of 1024 threads; dynamic shared memory: kHoSortCap keys
+__global__ void __launch_bounds__(1024) ho_sort_kernel(uint32_t* ctrl,
+                                                       const unsigned long long* keys,
+                                                       unsigned long long* sel) {
+    extern __shared__ unsigned long long sk[];
+    const uint32_t ngt = min(ctrl[kCtrlNGt], uint32_t(kHoKmax));
+    const uint32_t neq = min(ctrl[kCtrlNEq], uint32_t(kHoTieCap));
+    const int n = int(ngt + neq);
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += 1024)
+        sk[i] = i < int(ngt) ? keys[i] : (i < n ? keys[kHoKmax + (i - int(ngt))] : ~0ull);
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += 1024) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const unsigned long long a = sk[i], b = sk[p];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        sk[i] = b;
+                        sk[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    const int ns = min(n, kHoKmax);
+    for (int i = threadIdx.x; i < ns; i += 1024) sel[i] = sk[i];
+    if (threadIdx.x == 0) ctrl[kCtrlNSel] = uint32_t(ns);
+}
+
+// one warp
+__global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
+                                                        const unsigned long long* __restrict__ sel,
+                                                        int W, double min_dist, int max_corners,
+                                                        int* grid, int gw, int gh, int cell,
+                                                        int* corners, float* cscore,
+                                                        float2* pts) {
+    const int lane = threadIdx.x;
+    const int n = int(ctrl[kCtrlNSel]);
+    const double md2 = min_dist * min_dist;
+    const bool spaced = md2 > 1.0;   // distinct pixels are >= 1 apart
+    constexpr int CS = 1 + kHoCellCap;
+    int count = 0;
+    for (int g = 0; g < n && count < max_corners; g += 32) {
+        const int k = g + lane;
+        const bool valid = k < n;
+        const unsigned long long key = valid ? sel[k] : 0ull;
+        const int idx = int(uint32_t(key));
+        const int x = idx % W, y = idx / W;
+        bool blocked = !valid;
+        uint32_t conf = 0;
+        if (spaced) {
+            if (valid) {
+                const int cx = x / cell, cy = y / cell;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int qx = cx + dx, qy = cy + dy;
+                        if (qx < 0 || qy < 0 || qx >= gw || qy >= gh) continue;
+                        const int* c = grid + size_t(qy * gw + qx) * CS;
+                        const int cnt = min(c[0], kHoCellCap);
+                        for (int e = 0; e < cnt; ++e) {
+                            const int ax = c[1 + e] & 0xFFFF, ay = c[1 + e] >> 16;
+                            const long long ddx = x - ax, ddy = y - ay;
+                            if (double(ddx * ddx + ddy * ddy) < md2) blocked = true;
+                        }
+                    }
+            }
+            for (int j = 0; j < 32; ++j) {
+                const int xj = __shfl_sync(0xffffffffu, x, j), yj = __shfl_sync(0xffffffffu, y, j);
+                const long long ddx = x - xj, ddy = y - yj;
+                if (j < lane && g + j < n && double(ddx * ddx + ddy * ddy) < md2) conf |= 1u << j;
+            }
+        }
+        uint32_t acc = 0;
+        for (int i = 0; i < 32; ++i) {
+            const bool mine = !blocked && !(conf & acc) && count + __popc(acc) < max_corners;
+            acc |= uint32_t(__shfl_sync(0xffffffffu, mine ? 1 : 0, i)) << i;
+        }
+        if ((acc >> lane) & 1u) {
+            const int pos = count + __popc(acc & ((1u << lane) - 1u));
+            corners[2 * pos] = x;
+            corners[2 * pos + 1] = y;
+            cscore[pos] = __uint_as_float(~uint32_t(key >> 32));
+            pts[pos] = make_float2(float(x), float(y));
+            if (spaced) {
+                int* c = grid + size_t((y / cell) * gw + x / cell) * CS;
+                const int e = atomicAdd(c, 1);
+                if (e < kHoCellCap) c[1 + e] = x | (y << 16);
+                else ctrl[kCtrlOverflow] = 1;
+            }
+        }
+        __syncwarp();
+        count += __popc(acc);
+    }
+    // leave the grid empty for the next call
+    if (spaced)
+        for (int k = lane; k < count; k += 32) {
+            const int x = corners[2 * k], y = corners[2 * k + 1];
+            grid[size_t((y / cell) * gw + x / cell) * CS] = 0;
+        }
+    if (lane == 0) {
+        ctrl[kCtrlNCorners] = uint32_t(count);
+        ctrl[kCtrlNPts] = uint32_t(count);
+    }
+}
+
+// ---------------------------------------------------------------- pyramid
+__global__ void __launch_bounds__(256) ho_pyr_kernel(const uint8_t* __restrict__ in0,
+                                                     const uint8_t* __restrict__ in1, int w, int h,
+                                                     uint8_t* __restrict__ out0,
+                                                     uint8_t* __restrict__ out1, int w2, int h2) {
+    const uint8_t* in = blockIdx.z ? in1 : in0;
+    uint8_t* out = blockIdx.z ? out1 : out0;
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= w2 || y >= h2) return;
+    const int k[5] = {1, 4, 6, 4, 1};
+    int s = 0;
+#pragma unroll
+    for (int j = -2; j <= 2; ++j) {
+        const uint8_t* row = in + size_t(clampi_d(2 * y + j, 0, h - 1)) * w;
+        int rs = 0;
+#pragma unroll
+        for (int i = -2; i <= 2; ++i) rs += k[i + 2] * row[clampi_d(2 * x + i, 0, w - 1)];
+        s += k[j + 2] * rs;
+    }
+    out[size_t(y) * w2 + x] = uint8_t((s + 128) >> 8);
+}
+
+// ---------------------------------------------------------------- tracking
+struct HoTrackArgs {
+    HoPyr P, Q;
+    int levels, wh, max_iters, n_fixed;
+    float eps2, min_eig;
+    const float2* pts;
+    const uint32_t* npts;   // device count (NULL: n_fixed)
+    float2* out;
+    uint8_t* status;
+};
+
+constexpr int kTrackWarps = 4;
+
+__device__ __forceinline__ float ho_px(const uint8_t* p, int w, int h, int x, int y) {
+    return float(p[size_t(clampi_d(y, 0, h - 1)) * w + clampi_d(x, 0, w - 1)]);
+}
+
+__device__ __forceinline__ float ho_bil(float v00, float v10, float v01, float v11, float fx,
+                                        float fy) {
+    return (1.0f - fx) * (1.0f - fy) * v00 + fx * (1.0f - fy) * v10 + (1.0f - fx) * fy * v01 +
+           fx * fy * v11;
+}
+
+__device__ __forceinline__ float ho_wsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kTrackWarps * 32) ho_track_kernel(const HoTrackArgs a) {
+    extern __shared__ float tsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * kTrackWarps + warp;
+    const int n = a.npts ? int(*a.npts) : a.n_fixed;
+    if (k >= n) return;   // the whole warp: nothing below synchronises the CTA
+    const int ws = 2 * a.wh + 1, NS = ws * ws;
+    float* sI = tsm + size_t(warp) * 3 * NS;
+    float* sX = sI + NS;
+    float* sY = sX + NS;
+    const float2 u = a.pts[k];
+    float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
+    bool ok = true;
+    for (int l = a.levels; l >= 0 && ok; --l) {
+        const float sc = ldexpf(1.0f, -l);
+        const float ux = u.x * sc, uy = u.y * sc;
+        const uint8_t* P = a.P.p[l];
+        const int w = a.P.w[l], h = a.P.h[l];
+        const float fx0 = floorf(ux), fy0 = floorf(uy);
+        const int ix = int(fx0), iy = int(fy0);
+        const float fx = ux - fx0, fy = uy - fy0;
+        float ga = 0.f, gb = 0.f, gc = 0.f;
+        for (int s = lane; s < NS; s += 32) {
+            const int i = s % ws - a.wh, j = s / ws - a.wh;
+            const int x0 = ix + i, y0 = iy + j;
+            float v[4][4];   // pixels x0-1 .. x0+2, y0-1 .. y0+2
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) v[jj][ii] = ho_px(P, w, h, x0 - 1 + ii, y0 - 1 + jj);
+            const float I = ho_bil(v[1][1], v[1][2], v[2][1], v[2][2], fx, fy);
+            const float Ix = ho_bil(0.5f * (v[1][2] - v[1][0]), 0.5f * (v[1][3] - v[1][1]),
+                                    0.5f * (v[2][2] - v[2][0]), 0.5f * (v[2][3] - v[2][1]), fx, fy);
+            const float Iy = ho_bil(0.5f * (v[2][1] - v[0][1]), 0.5f * (v[2][2] - v[0][2]),
+                                    0.5f * (v[3][1] - v[1][1]), 0.5f * (v[3][2] - v[1][2]), fx, fy);
+            sI[s] = I;
+            sX[s] = Ix;
+            sY[s] = Iy;
+            ga += Ix * Ix;
+            gb += Ix * Iy;
+            gc += Iy * Iy;
+        }
+        ga = ho_wsum(ga);
+        gb = ho_wsum(gb);
+        gc = ho_wsum(gc);
+        const float det = ga * gc - gb * gb;
+        const float lmin = 0.5f * ((ga + gc) - sqrtf((ga - gc) * (ga - gc) + 4.0f * gb * gb));
+        if (lmin / float(NS) < a.min_eig || det == 0.0f) {
+            ok = false;
+            break;
+        }
+        __syncwarp();
+        const uint8_t* Qp = a.Q.p[l];
+        float vx = 0.f, vy = 0.f;
+        for (int it = 0; it < a.max_iters; ++it) {
+            const float qx = ux + gx + vx, qy = uy + gy + vy;
+            const float qx0 = floorf(qx), qy0 = floorf(qy);
+            const int jx = int(qx0), jy = int(qy0);
+            const float qfx = qx - qx0, qfy = qy - qy0;
+            float bx = 0.f, by = 0.f;
+            for (int s = lane; s < NS; s += 32) {
+                const int i = s % ws - a.wh, j = s / ws - a.wh;
+                const int x0 = jx + i, y0 = jy + j;
+                const float J = ho_bil(ho_px(Qp, w, h, x0, y0), ho_px(Qp, w, h, x0 + 1, y0),
+                                       ho_px(Qp, w, h, x0, y0 + 1), ho_px(Qp, w, h, x0 + 1, y0 + 1),
+                                       qfx, qfy);
+                const float d = sI[s] - J;
+                bx += d * sX[s];
+                by += d * sY[s];
+            }
+            bx = ho_wsum(bx);
+            by = ho_wsum(by);
+            const float ex = (gc * bx - gb * by) / det;
+            const float ey = (ga * by - gb * bx) / det;
+            vx += ex;
+            vy += ey;
+            if (ex * ex + ey * ey < a.eps2) break;
+        }
+        dx = vx;
+        dy = vy;
+        if (l > 0) {
+            gx = 2.0f * (gx + dx);
+            gy = 2.0f * (gy + dy);
+        }
+        __syncwarp();
+    }
+    const float px = u.x + gx + dx, py = u.y + gy + dy;
+    if (ok && !(px >= 0.0f && px <= float(a.P.w[0] - 1) && py >= 0.0f && py <= float(a.P.h[0] - 1)))
+        ok = false;
+    if (lane == 0) {
+        a.out[k] = make_float2(px, py);
+        a.status[k] = ok ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------- launches
+static int ho_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return DMSGM_OK;
+    return fail(e == cudaErrorMemoryAllocation ? DMSGM_ERR_OOM : DMSGM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+static int ho_corner_launches(dmsgm_homog_ctx* h, const uint8_t* img, cudaStream_t s) {
+    const int W = h->W, H = h->H;
+    const dim3 grid((W + kScTX - 1) / kScTX, (H + kScTY - 1) / kScTY);
+    switch (h->p.block_size) {
+        case 1: ho_score_kernel<1><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
+        case 3: ho_score_kernel<3><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
+        case 5: ho_score_kernel<5><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
+        default: ho_score_kernel<7><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
+    }
+    const dim3 cgrid((W + 31) / 32, (H + 7) / 8);
+    for (int mode = 0; mode < 3; ++mode) {
+        ho_cand_kernel<<<cgrid, 256, 0, s>>>(h->score, W, H, h->p.quality, mode, h->ctrl,
+                                             h->hist_hi, h->hist_lo, h->keys);
+        if (mode < 2) ho_select_kernel<<<1, 1024, 0, s>>>(mode, h->ctrl, h->hist_hi, h->hist_lo);
+    }
+    ho_sort_kernel<<<1, 1024, kHoSortCap * sizeof(unsigned long long), s>>>(h->ctrl, h->keys, h->sel);
+    ho_spacing_kernel<<<1, 32, 0, s>>>(h->ctrl, h->sel, W, h->p.min_distance, h->p.max_corners,
+                                       h->grid, h->gw, h->gh, h->cell, h->corners, h->cscore,
+                                       h->pts_in);
+    return ho_check(cudaGetLastError(), "corner kernels");
+}
+
+static void ho_pyramids(const dmsgm_homog_ctx* h, const uint8_t* prev, const uint8_t* cur,
+                        HoPyr* P, HoPyr* Q) {
+    for (int l = 0; l <= h->p.levels; ++l) {
+        P->w[l] = Q->w[l] = h->lw[l];
+        P->h[l] = Q->h[l] = h->lh[l];
+        P->p[l] = l ? h->pyr[0][l] : prev;
+        Q->p[l] = l ? h->pyr[1][l] : cur;
+    }
+}
+
+static int ho_track_launches(dmsgm_homog_ctx* h, const uint8_t* prev, const uint8_t* cur,
+                             int n_fixed, bool device_count, cudaStream_t s) {
+    for (int l = 1; l <= h->p.levels; ++l) {
+        const dim3 grid((h->lw[l] + 31) / 32, (h->lh[l] + 7) / 8, 2);
+        ho_pyr_kernel<<<grid, 256, 0, s>>>(l > 1 ? h->pyr[0][l - 1] : prev,
+                                           l > 1 ? h->pyr[1][l - 1] : cur, h->lw[l - 1],
+                                           h->lh[l - 1], h->pyr[0][l], h->pyr[1][l], h->lw[l],
+                                           h->lh[l]);
+    }
+    HoTrackArgs a;
+    ho_pyramids(h, prev, cur, &a.P, &a.Q);
+    a.levels = h->p.levels;
+    a.wh = h->p.win_half;
+    a.max_iters = h->p.max_iters;
+    a.n_fixed = n_fixed;
+    a.eps2 = float(h->p.eps * h->p.eps);
+    a.min_eig = float(h->p.min_eig);
+    a.pts = h->pts_in;
+    a.npts = device_count ? h->ctrl + kCtrlNPts : nullptr;
+    a.out = h->pts_out;
+    a.status = h->status;
+    const int ns = (2 * a.wh + 1) * (2 * a.wh + 1);
+    const size_t smem = size_t(kTrackWarps) * 3 * ns * sizeof(float);
+    const int n = device_count ? h->p.max_corners : n_fixed;
+    if (n > 0)
+        ho_track_kernel<<<(n + kTrackWarps - 1) / kTrackWarps, kTrackWarps * 32, smem, s>>>(a);
+    return ho_check(cudaGetLastError(), "tracking kernels");
+}
+
+}  // namespace dmsgm
+
+using namespace dmsgm;
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+void dmsgm_homog_default_params(dmsgm_homog_params* p) {
+    if (!p) return;
+    p->block_size = 3;
+    p->quality = 0.01;
+    p->min_distance = 10.0;
+    p->max_corners = 500;
+    p->levels = 5;
+    p->win_half = 10;
+    p->max_iters = 30;
+    p->eps = 0.01;
+    p->min_eig = 1e-3;
+    p->ransac_iters = 2000;
+    p->thresh = 3.0;
+    p->seed = 0;
+}
+
+int dmsgm_homog_destroy(dmsgm_homog_t h) {
+    if (!h) return DMSGM_OK;
+    cudaStreamSynchronize(0);
+    void* bufs[] = {h->score, h->zeroed, h->keys, h->sel, h->grid, h->corners, h->cscore,
+                    h->pts_in, h->pts_out, h->status, h->src, h->dst, h->inl, h->hyp,
+                    h->hcount, h->rout};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (int i = 0; i < 2; ++i)
+        for (int l = 0; l <= kHoMaxLevels; ++l)
+            if (h->pyr[i][l]) cudaFree(h->pyr[i][l]);
+    if (h->host) cudaFreeHost(h->host);
+    delete h;
+    return DMSGM_OK;
+}
+
+int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_t* out) {
+    clear_error();
+    if (!out) return fail(DMSGM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    dmsgm_homog_params p;
+    dmsgm_homog_default_params(&p);
+    if (pin) p = *pin;
+    if (W < 16 || H < 16 || W > 16384 || H > 16384 || W % 16)
+        return fail(DMSGM_ERR_INVALID_ARG, "frame %dx%d: need 16 <= W, H <= 16384 and W %% 16 == 0", W, H);
+    if (p.block_size < 1 || p.block_size > 7 || p.block_size % 2 == 0 || !(p.quality > 0.0) ||
+        !std::isfinite(p.quality) || !(p.min_distance >= 0.0) || !std::isfinite(p.min_distance) ||
+        p.min_distance > 4096.0 || p.max_corners < 1 || p.max_corners > kHoMaxPts ||
+        p.levels < 0 || p.levels > kHoMaxLevels || p.win_half < 1 || p.win_half > 15 ||
+        p.max_iters < 1 || !(p.eps >= 0.0) || !std::isfinite(p.eps) || !(p.min_eig >= 0.0) ||
+        !std::isfinite(p.min_eig) || p.ransac_iters < 1 || p.ransac_iters > 65536 ||
+        !(p.thresh > 0.0) || !std::isfinite(p.thresh))
+        return fail(DMSGM_ERR_INVALID_ARG, "invalid homography parameters");
+    dmsgm_homog_ctx* h = new (std::nothrow) dmsgm_homog_ctx();
+    if (!h) return fail(DMSGM_ERR_OOM, "out of host memory");
+    h->W = W;
+    h->H = H;
+    h->p = p;
+    cudaGetDevice(&h->device);
+    h->cell = p.min_distance > 1.0 ? int(std::ceil(p.min_distance)) : 1;
+    h->gw = (W + h->cell - 1) / h->cell;
+    h->gh = (H + h->cell - 1) / h->cell;
+    h->lw[0] = W;
+    h->lh[0] = H;
+    for (int l = 1; l <= p.levels; ++l) {
+        h->lw[l] = (h->lw[l - 1] + 1) / 2;
+        h->lh[l] = (h->lh[l - 1] + 1) / 2;
+    }
+    const size_t zwords = kCtrlWords + 2 * 65536;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    al(reinterpret_cast<void**>(&h->score), sizeof(float) * size_t(W) * H);
+    al(reinterpret_cast<void**>(&h->zeroed), sizeof(uint32_t) * zwords);
+    al(reinterpret_cast<void**>(&h->keys), sizeof(unsigned long long) * kHoSortCap);
+    al(reinterpret_cast<void**>(&h->sel), sizeof(unsigned long long) * kHoKmax);
+    al(reinterpret_cast<void**>(&h->grid), sizeof(int) * size_t(h->gw) * h->gh * (1 + kHoCellCap));
+    al(reinterpret_cast<void**>(&h->corners), sizeof(int) * 2 * kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->cscore), sizeof(float) * kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->pts_in), sizeof(float2) * kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->pts_out), sizeof(float2) * kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->status), kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->src), sizeof(double) * 2 * kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->dst), sizeof(double) * 2 * kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->inl), kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->hyp), sizeof(double) * 9 * size_t(p.ransac_iters));
+    al(reinterpret_cast<void**>(&h->hcount), sizeof(int) * size_t(p.ransac_iters));
+    al(reinterpret_cast<void**>(&h->rout), sizeof(HoRansacOut));
+    for (int i = 0; i < 2; ++i)
+        for (int l = 1; l <= p.levels; ++l)
+            al(reinterpret_cast<void**>(&h->pyr[i][l]), size_t(h->lw[l]) * h->lh[l]);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->host, 256 * 1024);
+    if (e == cudaSuccess) e = cudaMemset(h->grid, 0, sizeof(int) * size_t(h->gw) * h->gh * (1 + kHoCellCap));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   int(kHoSortCap * sizeof(unsigned long long)));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dmsgm_homog_destroy(h);
+        return fail(e == cudaErrorMemoryAllocation ? DMSGM_ERR_OOM : DMSGM_ERR_CUDA,
+                    "homography handle: %s", cudaGetErrorString(e));
+    }
+    h->ctrl = h->zeroed;
+    h->hist_hi = h->zeroed + kCtrlWords;
+    h->hist_lo = h->hist_hi + 65536;
+    *out = h;
+    return DMSGM_OK;
+}
+
+static int ho_frame_ok(const dmsgm_homog_ctx* h, const uint8_t* f) {
+    return f && reinterpret_cast<uintptr_t>(f) % 16 == 0;
+}
+
+// corners of img into the handle's buffers; counts in ctrl
+static int ho_corners_dev(dmsgm_homog_ctx* h, const uint8_t* img, cudaStream_t s) {
+    const size_t zbytes = sizeof(uint32_t) * (kCtrlWords + 2 * 65536);
+    int rc = ho_check(cudaMemsetAsync(h->zeroed, 0, zbytes, s), "clear");
+    if (rc) return rc;
+    return ho_corner_launches(h, img, s);
+}
+
+int dmsgm_homog_corners(dmsgm_homog_t h, const uint8_t* img_dev, int* xy, float* scores, int* n,
+                        int* n_cand, void* stream) {
+    clear_error();
+    if (!h || !ho_frame_ok(h, img_dev) || !xy || !n)
+        return fail(DMSGM_ERR_INVALID_ARG, "NULL handle, output or misaligned frame");
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = ho_corners_dev(h, img_dev, s);
+    if (rc) return rc;
+    uint32_t* hc = static_cast<uint32_t*>(h->host);
+    int* hxy = reinterpret_cast<int*>(hc + kCtrlWords);
+    float* hs = reinterpret_cast<float*>(hxy + 2 * kHoMaxPts);
+    rc = ho_check(cudaMemcpyAsync(hc, h->ctrl, sizeof(uint32_t) * kCtrlWords, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaMemcpyAsync(hxy, h->corners, sizeof(int) * 2 * h->p.max_corners, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaMemcpyAsync(hs, h->cscore, sizeof(float) * h->p.max_corners, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaStreamSynchronize(s), "corners");
+    if (rc) return rc;
+    if (hc[kCtrlOverflow])
+        return fail(DMSGM_ERR_UNSUPPORTED, "more than %d candidates tied at the selection cut", kHoTieCap);
+    const int m = int(hc[kCtrlNCorners]);
+    memcpy(xy, hxy, sizeof(int) * 2 * m);
+    if (scores) memcpy(scores, hs, sizeof(float) * m);
+    *n = m;
+    if (n_cand) *n_cand = int(hc[kCtrlCand]);
+    return DMSGM_OK;
+}
+
+int dmsgm_homog_track(dmsgm_homog_t h, const uint8_t* prev_dev, const uint8_t* cur_dev,
+                      const float* pts, int n, float* out, uint8_t* status, void* stream) {
+    clear_error();
+    if (!h || !ho_frame_ok(h, prev_dev) || !ho_frame_ok(h, cur_dev) || n < 0 || n > kHoMaxPts ||
+        (n > 0 && (!pts || !out || !status)))
+        return fail(DMSGM_ERR_INVALID_ARG, "invalid tracking arguments (n <= %d)", kHoMaxPts);
+    if (n == 0) return DMSGM_OK;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* hp = static_cast<float*>(h->host);
+    memcpy(hp, pts, sizeof(float) * 2 * n);
+    int rc = ho_check(cudaMemcpyAsync(h->pts_in, hp, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, s), "copy");
+    if (!rc) rc = ho_track_launches(h, prev_dev, cur_dev, n, false, s);
+    uint8_t* hs = reinterpret_cast<uint8_t*>(hp + 2 * kHoMaxPts);
+    if (!rc) rc = ho_check(cudaMemcpyAsync(hp, h->pts_out, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaMemcpyAsync(hs, h->status, n, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaStreamSynchronize(s), "tracking");
+    if (rc) return rc;
+    memcpy(out, hp, sizeof(float) * 2 * n);
+    memcpy(status, hs, n);
+    return DMSGM_OK;
+}
+
+static void ho_result(const HoRansacOut& r, double* H3x3, dmsgm_homog_result* res) {
+    if (r.inliers < 0) {
+        for (int i = 0; i < 9; ++i) H3x3[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    } else {
+        memcpy(H3x3, r.H, sizeof r.H);
+    }
+    if (res) {
+        res->inliers = r.inliers;
+        res->best = r.best;
+    }
+}
+
+int dmsgm_homog_ransac(dmsgm_homog_t h, const double* src, const double* dst, int n,
+                       double H3x3[9], uint8_t* inliers, dmsgm_homog_result* res, void* stream) {
+    clear_error();
+    if (!h || !H3x3 || n < 0 || n > kHoMaxPts || (n > 0 && (!src || !dst)))
+        return fail(DMSGM_ERR_INVALID_ARG, "invalid RANSAC arguments (n <= %d)", kHoMaxPts);
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* hd = static_cast<double*>(h->host);
+    memcpy(hd, src, sizeof(double) * 2 * n);
+    memcpy(hd + 2 * kHoMaxPts, dst, sizeof(double) * 2 * n);
+    uint32_t* hn = reinterpret_cast<uint32_t*>(hd + 4 * kHoMaxPts);
+    *hn = uint32_t(n);
+    int rc = ho_check(cudaMemcpyAsync(h->src, hd, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s), "copy");
+    if (!rc) rc = ho_check(cudaMemcpyAsync(h->dst, hd + 2 * kHoMaxPts, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s), "copy");
+    if (!rc) rc = ho_check(cudaMemcpyAsync(h->ctrl + kCtrlNPairs, hn, sizeof(uint32_t), cudaMemcpyHostToDevice, s), "copy");
+    if (!rc) rc = ho_launch_ransac(h, false, s);
+    HoRansacOut* ho = reinterpret_cast<HoRansacOut*>(hn + 4);
+    uint8_t* hi = reinterpret_cast<uint8_t*>(ho + 1);
+    if (!rc) rc = ho_check(cudaMemcpyAsync(ho, h->rout, sizeof(HoRansacOut), cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc && n) rc = ho_check(cudaMemcpyAsync(hi, h->inl, n, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaStreamSynchronize(s), "RANSAC");
+    if (rc) return rc;
+    ho_result(*ho, H3x3, res);
+    if (inliers && n) memcpy(inliers, hi, n);
+    return DMSGM_OK;
+}
+
+int dmsgm_homog_estimate(dmsgm_homog_t h, const uint8_t* prev_dev, const uint8_t* cur_dev,
+                         double H3x3[9], dmsgm_homog_result* res, void* stream) {
+    clear_error();
+    if (!h || !H3x3 || !ho_frame_ok(h, prev_dev) || !ho_frame_ok(h, cur_dev))
+        return fail(DMSGM_ERR_INVALID_ARG, "NULL handle or output, or misaligned frame");
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = ho_corners_dev(h, prev_dev, s);
+    if (!rc) rc = ho_track_launches(h, prev_dev, cur_dev, 0, true, s);
+    if (!rc) rc = ho_launch_ransac(h, true, s);
+    uint32_t* hc = static_cast<uint32_t*>(h->host);
+    HoRansacOut* ho = reinterpret_cast<HoRansacOut*>(hc + kCtrlWords);
+    if (!rc) rc = ho_check(cudaMemcpyAsync(hc, h->ctrl, sizeof(uint32_t) * kCtrlWords, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaMemcpyAsync(ho, h->rout, sizeof(HoRansacOut), cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaStreamSynchronize(s), "homography");
+    if (rc) return rc;
+    if (hc[kCtrlOverflow])
+        return fail(DMSGM_ERR_UNSUPPORTED, "more than %d candidates tied at the selection cut", kHoTieCap);
+    ho_result(*ho, H3x3, res);
+    if (res) {
+        res->corners = int(hc[kCtrlNCorners]);
+        res->candidates = int(hc[kCtrlCand]);
+        res->tracked = int(hc[kCtrlNPairs]);
+    }
+    return DMSGM_OK;
+}
+
+}  // extern "C"

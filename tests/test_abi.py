@@ -19,10 +19,15 @@ def L():
 
 
 def _declared():
-    with open(os.path.join(ROOT, "include", "dmsgm.h")) as f:
-        src = f.read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(dmsgm_[a-z_0-9]+)\s*\(", src))
+    """Every function any public header under include/ declares."""
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        with open(os.path.join(ROOT, "include", h)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(dmsgm_[a-z_0-9]+)\s*\(", src))
     return names
 
 
