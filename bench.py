@@ -469,7 +469,7 @@ def run_extras(args, dev, stream):
     runs = [(B, prec, False, T) for B in (4, 8) for prec in ("fp32", "fp16")]
     runs += [(16, "fp32", False, T), (2, "fp32", False, min(T, 20)), (1, "fp32", False, min(T, 10)),
              (4, "fp32", True, T)]
-    if args.extra == 2:   # the preprocessing forms only
+    if args.extra in (2, 3):   # the preprocessing or the motion-estimation forms only
         runs = []
     for B, prec, spread, n in runs:
         m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl, mix_spread=spread)
@@ -485,6 +485,24 @@ def run_extras(args, dev, stream):
                     "bytes_per_frame": int(bpp * W * H), "achieved_gbs": round(ach, 1),
                     "frac": round(ach / peak, 4)}
         m.close()
+    if args.extra != 3:
+        res.update(run_pre_extras(args, dev, stream, frames, Hs, masks, graph_time, peak))
+    if args.extra in (1, 3):
+        res.update(run_homog_extras(args, dev, stream, frames, Hs))
+    del frames, masks
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_pre_extras(args, dev, stream, frames, Hs, masks, graph_time, peak):
+    """The preprocessing forms: the filter alone, and the step with it fused
+    into its tile or as a separate pass."""
+    import torch
+    from paper_1702_05156_gb300 import dmsgm
+    from paper_1702_05156_gb300.synth import make_stream, spec_for
+
+    res = {}
+    W, H, T = 3840, 2160, args.extra_frames
     # the Sec. 2.1 preprocessing on its own (5 x 5 Gaussian, sigma 1, then
     # the 3 x 3 median), HD and 4K: 2 bytes per pixel (read + write)
     for (w, h) in ((3840, 2160), (1920, 1080)):
@@ -518,8 +536,60 @@ def run_extras(args, dev, stream):
                 "fused": m.info().pre_fused}
             m.close()
         del fr, hs, mk
-    del frames, masks
-    torch.cuda.empty_cache()
+    return res
+
+
+def run_homog_extras(args, dev, stream, frames, Hs):
+    """The motion-estimation front end (corners, pyramidal Lucas-Kanade,
+    RANSAC) per frame pair, HD and 4K: device time per estimate (each call
+    ends with its result on the host), and the estimate's distance from the
+    stream's known camera motion at the frame corners."""
+    import time
+
+    import numpy as np
+    import torch
+    from paper_1702_05156_gb300.homog import HomographyEstimator
+    from paper_1702_05156_gb300.synth import make_stream, spec_for
+
+    res = {}
+    for (w, h, name) in ((1920, 1080, "hd"), (3840, 2160, "4k")):
+        n = 12
+        if (w, h) == (3840, 2160):
+            fr, hs = frames[:n], np.asarray(Hs[:n])
+        else:
+            fr, hs = make_stream(spec_for(w, h, n, seed=args.seed), device=dev)
+            hs = np.asarray(hs)
+        # the stand-in stream's moving rectangles hold the strongest corners;
+        # a 0.1 % quality cut keeps the background texture's as well
+        est = HomographyEstimator(w, h, quality=0.001, thresh=1.0)
+        corners = np.array([[0, 0], [w, 0], [0, h], [w, h]], float)
+
+        def apply(Hm, p):
+            q = np.c_[p, np.ones(len(p))] @ Hm.T
+            return q[:, :2] / q[:, 2:]
+        with torch.cuda.stream(stream):
+            for t in range(1, 4):   # warm-up
+                est.estimate(fr[t - 1], fr[t], stream=stream)
+            torch.cuda.synchronize()
+            errs, ins, t0 = [], [], time.perf_counter()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for t in range(1, n):
+                Hm, r = est.estimate(fr[t - 1], fr[t], stream=stream)
+                errs.append(float(np.abs(apply(Hm, corners) - apply(hs[t], corners)).max()))
+                ins.append(r.inliers)
+            e1.record(stream)
+            e1.synchronize()
+            wall = (time.perf_counter() - t0) / (n - 1)
+        dev_s = e0.elapsed_time(e1) / 1e3 / (n - 1)
+        res[f"homog_{name}"] = {"pair_us": round(dev_s * 1e6, 1), "wall_us": round(wall * 1e6, 1),
+                                "mpix_s": round(w * h / wall / 1e6, 1),
+                                "corner_err_px_max": round(max(errs), 3),
+                                "inliers_mean": round(float(np.mean(ins)), 1),
+                                "params": "quality 0.001, ransac thresh 1 px, other defaults"}
+        est.close()
+        del fr
     return res
 
 
@@ -590,7 +660,8 @@ def main():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--extra", type=int, default=1,
-                    help="1: all extra configurations, 2: the preprocessing forms only, 0: none")
+                    help="1: all extra configurations, 2: the preprocessing forms only, "
+                         "3: the motion-estimation front end only, 0: none")
     ap.add_argument("--extra-frames", type=int, default=100)
     ap.add_argument("--ref-frames", type=int, default=4)
     ap.add_argument("--batched", type=int, default=1)

@@ -18,13 +18,14 @@
 //            index;
 //   sort     one CTA, bitonic, in shared memory: (score desc, index asc);
 //   spacing  one warp takes the sorted candidates 32 at a time: each lane
-//            checks a spacing grid of the kept corners (cells of
-//            ceil(min_distance) pixels, so that a conflict lies in the 3 x 3
-//            neighbouring cells) and the earlier lanes of its group, and the
-//            group is resolved in order with warp shuffles.
-// Tracking: one warp per point; per level the window's previous-frame
-// samples (intensity and both gradients, bilinear) stay in shared memory for
-// the iterations, which sample the current frame and reduce with shuffles.
+//            checks the kept corners of the 3 x 3 cells around it (linked
+//            lists per cell of at least ceil(min_distance) pixels, in shared
+//            memory) and the earlier lanes of its group, and the group is
+//            resolved in order with warp shuffles.
+// Tracking: one CTA per point; per level the window's previous-frame samples
+// (intensity and both gradients, bilinear) stay in shared memory for the
+// iterations, which sample a staged patch of the current frame (restaged only
+// when the update leaves it) and reduce across the CTA in a fixed order.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -36,7 +37,7 @@ namespace dmsgm {
 __device__ __forceinline__ int clampi_d(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
 // ---------------------------------------------------------------- scores
-constexpr int kScTX = 32, kScTY = 8;
+constexpr int kScTX = 64, kScTY = 32;   // 256 threads, 8 pixels each
 
 template <int BS>
 __global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* __restrict__ img, int W,
@@ -45,8 +46,9 @@ __global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* __restrict
     constexpr int r = BS / 2, R = r + 1;
     constexpr int IW = kScTX + 2 * R, IH = kScTY + 2 * R;   // staged pixels (clamped)
     constexpr int GW = kScTX + 2 * r, GH = kScTY + 2 * r;   // gradients of the window positions
-    __shared__ int px[IH][IW];
-    __shared__ int gx[GH][GW], gy[GH][GW];
+    __shared__ uint8_t px[IH][IW];
+    __shared__ short gx[GH][GW], gy[GH][GW];
+    __shared__ uint32_t wmax[8];
     const int x0 = blockIdx.x * kScTX, y0 = blockIdx.y * kScTY;
     for (int i = threadIdx.x; i < IW * IH; i += 256) {
         const int yy = i / IW, xx = i - yy * IW;
@@ -58,16 +60,17 @@ __global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* __restrict
         const int yy = i / GW, xx = i - yy * GW;
         const int cx = clampi_d(x0 - r + xx, 0, W - 1) - (x0 - R);
         const int cy = clampi_d(y0 - r + yy, 0, H - 1) - (y0 - R);
-        gx[yy][xx] = (px[cy - 1][cx + 1] + 2 * px[cy][cx + 1] + px[cy + 1][cx + 1]) -
-                     (px[cy - 1][cx - 1] + 2 * px[cy][cx - 1] + px[cy + 1][cx - 1]);
-        gy[yy][xx] = (px[cy + 1][cx - 1] + 2 * px[cy + 1][cx] + px[cy + 1][cx + 1]) -
-                     (px[cy - 1][cx - 1] + 2 * px[cy - 1][cx] + px[cy - 1][cx + 1]);
+        gx[yy][xx] = short((px[cy - 1][cx + 1] + 2 * px[cy][cx + 1] + px[cy + 1][cx + 1]) -
+                           (px[cy - 1][cx - 1] + 2 * px[cy][cx - 1] + px[cy + 1][cx - 1]));
+        gy[yy][xx] = short((px[cy + 1][cx - 1] + 2 * px[cy + 1][cx] + px[cy + 1][cx + 1]) -
+                           (px[cy - 1][cx - 1] + 2 * px[cy - 1][cx] + px[cy - 1][cx + 1]));
     }
     __syncthreads();
-    const int tx = threadIdx.x % kScTX, ty = threadIdx.x / kScTX;
-    const int x = x0 + tx, y = y0 + ty;
+    const int tx = threadIdx.x % kScTX;
     uint32_t bits = 0;
-    if (x < W && y < H) {
+    for (int ty = threadIdx.x / kScTX; ty < kScTY; ty += 256 / kScTX) {
+        const int x = x0 + tx, y = y0 + ty;
+        if (x >= W || y >= H) continue;
         int A = 0, B = 0, C = 0;
 #pragma unroll
         for (int j = 0; j < BS; ++j)
@@ -85,13 +88,19 @@ __global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* __restrict
         const float f = __fmul_rn(fb, fb);
         const float g = __fmul_rn(4.0f, f);
         const float rr = __fsqrt_rn(__fadd_rn(e, g));
-        float s = __fmul_rn(0.5f, __fsub_rn(t, rr));
-        s = s > 0.0f ? s : 0.0f;
-        score[size_t(y) * W + x] = s;
-        bits = __float_as_uint(s);
+        float sc = __fmul_rn(0.5f, __fsub_rn(t, rr));
+        sc = sc > 0.0f ? sc : 0.0f;
+        score[size_t(y) * W + x] = sc;
+        bits = max(bits, __float_as_uint(sc));
     }
     bits = __reduce_max_sync(0xffffffffu, bits);
-    if ((threadIdx.x & 31) == 0 && bits) atomicMax(&ctrl[kCtrlMaxBits], bits);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t m = 0;
+        for (int w = 0; w < 8; ++w) m = max(m, wmax[w]);
+        if (m) atomicMax(&ctrl[kCtrlMaxBits], m);
+    }
 }
 
 // ---------------------------------------------------------------- candidates
@@ -111,34 +120,96 @@ __device__ __forceinline__ bool ho_is_cand(const float* __restrict__ s, int W, i
     return true;
 }
 
-// mode 0: histogram of the high 16 bits and the count; 1: histogram of the
-// low 16 bits inside the cut's bucket; 2: collect the keys above / at the cut
+// The candidates of a kScTX x kScTY tile, 8 rows per thread.  mode 0:
+// histogram of the high 16 bits and the count; 1: histogram of the low 16
+// bits inside the cut's bucket; 2: collect the keys above / at the cut.  The
+// CTA aggregates its counts and key slots (one global atomic per CTA and
+// counter); histogram buckets take one atomic per distinct bucket in a warp.
 __global__ void __launch_bounds__(256) ho_cand_kernel(const float* __restrict__ s, int W, int H,
                                                       double quality, int mode, uint32_t* ctrl,
                                                       uint32_t* hist_hi, uint32_t* hist_lo,
                                                       unsigned long long* keys) {
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (mode > 0 && mode < 2 && ctrl[kCtrlTakeAll]) return;
+    constexpr int ROWS = kScTY / (256 / kScTX);
+    __shared__ uint32_t cnt[2], base[2];
+    if (mode == 1 && ctrl[kCtrlTakeAll]) return;
     const float thr = __fmul_rn(__double2float_rn(quality), __uint_as_float(ctrl[kCtrlMaxBits]));
-    uint32_t bits = 0;
-    if (x >= W || y >= H || !ho_is_cand(s, W, H, x, y, thr, bits)) return;
-    if (mode == 0) {
-        atomicAdd(&hist_hi[bits >> 16], 1u);
-        atomicAdd(&ctrl[kCtrlCand], 1u);
-    } else if (mode == 1) {
-        if ((bits >> 16) == ctrl[kCtrlHiCut]) atomicAdd(&hist_lo[bits & 0xFFFFu], 1u);
-    } else {
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const int x = blockIdx.x * kScTX + int(threadIdx.x) % kScTX;
+    const int y0 = blockIdx.y * kScTY + int(threadIdx.x) / kScTX;
+    const bool take_all = ctrl[kCtrlTakeAll] != 0;
+    const uint32_t hi_cut = ctrl[kCtrlHiCut], cut = ctrl[kCtrlCut];
+    if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t mb[ROWS];            // this thread's candidate bits per row (0: none)
+    uint32_t ng = 0, ne = 0;      // its keys above / at the cut
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int y = y0 + r * (256 / kScTX);
+        uint32_t bits = 0;
+        const bool cand = x < W && y < H && ho_is_cand(s, W, H, x, y, thr, bits);
+        mb[r] = cand ? bits : 0u;   // a candidate's score is > 0: its bits are not 0
+        if (mode == 0) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, cand ? (bits >> 16) : 0xFFFFFFFFu);
+            if (cand && (peers & below) == 0u) atomicAdd(&hist_hi[bits >> 16], uint32_t(__popc(peers)));
+            ng += cand;
+        } else if (mode == 1) {
+            const bool in = cand && (bits >> 16) == hi_cut;
+            const uint32_t peers = __match_any_sync(0xffffffffu, in ? (bits & 0xFFFFu) : 0xFFFFFFFFu);
+            if (in && (peers & below) == 0u) atomicAdd(&hist_lo[bits & 0xFFFFu], uint32_t(__popc(peers)));
+        } else {
+            ng += cand && (take_all || bits > cut);
+            ne += cand && !take_all && bits == cut;
+        }
+    }
+    if (mode == 1) return;
+    // CTA totals: warp sums, one shared atomic per warp, one global per CTA
+    const uint32_t wg = __reduce_add_sync(0xffffffffu, ng), we = __reduce_add_sync(0xffffffffu, ne);
+    // exclusive prefix of this thread inside its warp
+    uint32_t pg = ng, pe = ne;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a1 = __shfl_up_sync(0xffffffffu, pg, o), a2 = __shfl_up_sync(0xffffffffu, pe, o);
+        if (lane >= o) {
+            pg += a1;
+            pe += a2;
+        }
+    }
+    pg -= ng;
+    pe -= ne;
+    uint32_t wbase_g = 0, wbase_e = 0;
+    if (lane == 0) {
+        wbase_g = atomicAdd(&cnt[0], wg);
+        wbase_e = atomicAdd(&cnt[1], we);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (mode == 0) {
+            if (cnt[0]) atomicAdd(&ctrl[kCtrlCand], cnt[0]);
+        } else {
+            base[0] = cnt[0] ? atomicAdd(&ctrl[kCtrlNGt], cnt[0]) : 0u;
+            base[1] = cnt[1] ? atomicAdd(&ctrl[kCtrlNEq], cnt[1]) : 0u;
+        }
+    }
+    if (mode == 0) return;
+    __syncthreads();
+    uint32_t kg = base[0] + __shfl_sync(0xffffffffu, wbase_g, 0) + pg;
+    uint32_t ke = base[1] + __shfl_sync(0xffffffffu, wbase_e, 0) + pe;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const uint32_t bits = mb[r];
+        if (!bits) continue;
+        const int y = y0 + r * (256 / kScTX);
         const unsigned long long key =
             (static_cast<unsigned long long>(~bits) << 32) | static_cast<uint32_t>(y * W + x);
-        const uint32_t cut = ctrl[kCtrlCut];
-        if (ctrl[kCtrlTakeAll] || bits > cut) {
-            const uint32_t k = atomicAdd(&ctrl[kCtrlNGt], 1u);   // < kHoKmax by the cut
-            if (k < uint32_t(kHoKmax)) keys[k] = key;
+        if (take_all || bits > cut) {
+            if (kg < uint32_t(kHoKmax)) keys[kg] = key;   // < kHoKmax by the cut
             else ctrl[kCtrlOverflow] = 1;
+            ++kg;
         } else if (bits == cut) {
-            const uint32_t k = atomicAdd(&ctrl[kCtrlNEq], 1u);
-            if (k < uint32_t(kHoTieCap)) keys[kHoKmax + k] = key;
+            if (ke < uint32_t(kHoTieCap)) keys[kHoKmax + ke] = key;
             else ctrl[kCtrlOverflow] = 1;
+            ++ke;
         }
     }
 }
@@ -151,7 +222,12 @@ __device__ void ho_find_cut(const uint32_t* hist, uint32_t need, uint32_t* cut, 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int top = 65535 - 64 * t;   // this thread's buckets: top, top - 1, .., top - 63
     uint32_t local = 0;
-    for (int b = 0; b < 64; ++b) local += hist[top - b];
+    const uint4* h4 = reinterpret_cast<const uint4*>(hist + (top - 63));
+    uint4 v4[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v4[q] = h4[q];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) local += v4[q].x + v4[q].y + v4[q].z + v4[q].w;
     // exclusive prefix over threads (thread 0 holds the highest buckets)
     uint32_t v = local;
 #pragma unroll
@@ -249,18 +325,28 @@ __global__ void __launch_bounds__(1024) ho_sort_kernel(uint32_t* ctrl,
     if (threadIdx.x == 0) ctrl[kCtrlNSel] = uint32_t(ns);
 }
 
-// one warp
+// One warp.  Dynamic shared memory (when min_distance > 1): the kept
+// corners as linked lists per cell -- head[gw * gh], next[max_corners],
+// position[max_corners] -- with cells of `cell` >= ceil(min_distance) pixels,
+// so that any corner closer than min_distance lies in the 3 x 3 cells around.
 __global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
                                                         const unsigned long long* __restrict__ sel,
                                                         int W, double min_dist, int max_corners,
-                                                        int* grid, int gw, int gh, int cell,
-                                                        int* corners, float* cscore,
-                                                        float2* pts) {
+                                                        int gw, int gh, int cell, int* corners,
+                                                        float* cscore, float2* pts) {
+    extern __shared__ int ssm[];
     const int lane = threadIdx.x;
+    const uint32_t below = (1u << lane) - 1u;
     const int n = int(ctrl[kCtrlNSel]);
     const double md2 = min_dist * min_dist;
     const bool spaced = md2 > 1.0;   // distinct pixels are >= 1 apart
-    constexpr int CS = 1 + kHoCellCap;
+    int* head = ssm;
+    int* nxt = head + gw * gh;
+    int* pos = nxt + max_corners;
+    if (spaced) {
+        for (int i = lane; i < gw * gh; i += 32) head[i] = -1;
+        __syncwarp();
+    }
     int count = 0;
     for (int g = 0; g < n && count < max_corners; g += 32) {
         const int k = g + lane;
@@ -277,11 +363,8 @@ __global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int qx = cx + dx, qy = cy + dy;
                         if (qx < 0 || qy < 0 || qx >= gw || qy >= gh) continue;
-                        const int* c = grid + size_t(qy * gw + qx) * CS;
-                        const int cnt = min(c[0], kHoCellCap);
-                        for (int e = 0; e < cnt; ++e) {
-                            const int ax = c[1 + e] & 0xFFFF, ay = c[1 + e] >> 16;
-                            const long long ddx = x - ax, ddy = y - ay;
+                        for (int e = head[qy * gw + qx]; e >= 0; e = nxt[e]) {
+                            const long long ddx = x - (pos[e] & 0xFFFF), ddy = y - (pos[e] >> 16);
                             if (double(ddx * ddx + ddy * ddy) < md2) blocked = true;
                         }
                     }
@@ -293,32 +376,31 @@ __global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
             }
         }
         uint32_t acc = 0;
-        for (int i = 0; i < 32; ++i) {
-            const bool mine = !blocked && !(conf & acc) && count + __popc(acc) < max_corners;
-            acc |= uint32_t(__shfl_sync(0xffffffffu, mine ? 1 : 0, i)) << i;
+        if (__ballot_sync(0xffffffffu, conf != 0u) == 0u) {
+            // no conflict inside the group: the unblocked lanes, in order, up
+            // to the remaining count
+            acc = __ballot_sync(0xffffffffu, !blocked);
+            while (__popc(acc) > max_corners - count) acc &= ~(1u << (31 - __clz(acc)));
+        } else {
+            for (int i = 0; i < 32; ++i) {
+                const bool mine = !blocked && !(conf & acc) && count + __popc(acc) < max_corners;
+                acc |= uint32_t(__shfl_sync(0xffffffffu, mine ? 1 : 0, i)) << i;
+            }
         }
         if ((acc >> lane) & 1u) {
-            const int pos = count + __popc(acc & ((1u << lane) - 1u));
-            corners[2 * pos] = x;
-            corners[2 * pos + 1] = y;
-            cscore[pos] = __uint_as_float(~uint32_t(key >> 32));
-            pts[pos] = make_float2(float(x), float(y));
+            const int p = count + __popc(acc & below);
+            corners[2 * p] = x;
+            corners[2 * p + 1] = y;
+            cscore[p] = __uint_as_float(~uint32_t(key >> 32));
+            pts[p] = make_float2(float(x), float(y));
             if (spaced) {
-                int* c = grid + size_t((y / cell) * gw + x / cell) * CS;
-                const int e = atomicAdd(c, 1);
-                if (e < kHoCellCap) c[1 + e] = x | (y << 16);
-                else ctrl[kCtrlOverflow] = 1;
+                pos[p] = x | (y << 16);
+                nxt[p] = atomicExch(&head[(y / cell) * gw + x / cell], p);
             }
         }
         __syncwarp();
         count += __popc(acc);
     }
-    // leave the grid empty for the next call
-    if (spaced)
-        for (int k = lane; k < count; k += 32) {
-            const int x = corners[2 * k], y = corners[2 * k + 1];
-            grid[size_t((y / cell) * gw + x / cell) * CS] = 0;
-        }
     if (lane == 0) {
         ctrl[kCtrlNCorners] = uint32_t(count);
         ctrl[kCtrlNPts] = uint32_t(count);
@@ -326,25 +408,33 @@ __global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
 }
 
 // ---------------------------------------------------------------- pyramid
+// 4 horizontally adjacent outputs per thread: a CTA covers 128 x 8 outputs.
 __global__ void __launch_bounds__(256) ho_pyr_kernel(const uint8_t* __restrict__ in0,
                                                      const uint8_t* __restrict__ in1, int w, int h,
                                                      uint8_t* __restrict__ out0,
                                                      uint8_t* __restrict__ out1, int w2, int h2) {
     const uint8_t* in = blockIdx.z ? in1 : in0;
     uint8_t* out = blockIdx.z ? out1 : out0;
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (x >= w2 || y >= h2) return;
+    const int xb = blockIdx.x * 128 + 4 * (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (xb >= w2 || y >= h2) return;
     const int k[5] = {1, 4, 6, 4, 1};
-    int s = 0;
+    int cs[11];   // vertical sums of input columns 2 xb - 2 .. 2 xb + 8
+#pragma unroll
+    for (int c = 0; c < 11; ++c) cs[c] = 0;
 #pragma unroll
     for (int j = -2; j <= 2; ++j) {
         const uint8_t* row = in + size_t(clampi_d(2 * y + j, 0, h - 1)) * w;
-        int rs = 0;
 #pragma unroll
-        for (int i = -2; i <= 2; ++i) rs += k[i + 2] * row[clampi_d(2 * x + i, 0, w - 1)];
-        s += k[j + 2] * rs;
+        for (int c = 0; c < 11; ++c) cs[c] += k[j + 2] * row[clampi_d(2 * xb - 2 + c, 0, w - 1)];
     }
-    out[size_t(y) * w2 + x] = uint8_t((s + 128) >> 8);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (xb + q >= w2) break;
+        int v = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) v += k[i] * cs[2 * q + i];
+        out[size_t(y) * w2 + xb + q] = uint8_t((v + 128) >> 8);
+    }
 }
 
 // ---------------------------------------------------------------- tracking
@@ -358,7 +448,12 @@ struct HoTrackArgs {
     uint8_t* status;
 };
 
-constexpr int kTrackWarps = 4;
+constexpr int kTrackThreads = 128;   // one CTA per point
+constexpr size_t kHoSpaceMax = 200 * 1024;  // shared memory of the spacing kernel
+
+static size_t ho_spacing_smem(int gw, int gh, int max_corners) {
+    return sizeof(int) * (size_t(gw) * gh + 2 * size_t(max_corners));
+}
 
 __device__ __forceinline__ float ho_px(const uint8_t* p, int w, int h, int x, int y) {
     return float(p[size_t(clampi_d(y, 0, h - 1)) * w + clampi_d(x, 0, w - 1)]);
@@ -376,16 +471,48 @@ __device__ __forceinline__ float ho_wsum(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kTrackWarps * 32) ho_track_kernel(const HoTrackArgs a) {
+// CTA sums of three values, the same on every thread (a fixed order: warp
+// trees, then warps 0..3)
+__device__ __forceinline__ float3 ho_csum3(float a, float b, float c, float* red) {
+    a = ho_wsum(a);
+    b = ho_wsum(b);
+    c = ho_wsum(c);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[3 * w] = a;
+        red[3 * w + 1] = b;
+        red[3 * w + 2] = c;
+    }
+    __syncthreads();
+    const float3 r = make_float3(((red[0] + red[3]) + red[6]) + red[9],
+                                 ((red[1] + red[4]) + red[7]) + red[10],
+                                 ((red[2] + red[5]) + red[8]) + red[11]);
+    __syncthreads();
+    return r;
+}
+
+constexpr int kTrackMargin = 2;   // pixels staged around the current frame's window
+
+// shared floats per tracking CTA: the window's samples (3 NS) and a pixel
+// patch (the previous frame's, side ws + 3; the current frame's, side
+// ws + 1 + 2 margins, reused while the iterations stay inside it)
+__host__ __device__ constexpr int ho_track_floats(int wh) {
+    return 3 * (2 * wh + 1) * (2 * wh + 1) + (2 * wh + 2 + 2 * kTrackMargin) * (2 * wh + 2 + 2 * kTrackMargin);
+}
+
+__global__ void __launch_bounds__(kTrackThreads) ho_track_kernel(const HoTrackArgs a) {
     extern __shared__ float tsm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * kTrackWarps + warp;
+    __shared__ float red[12];
+    const int tid = threadIdx.x;
+    const int k = blockIdx.x;
     const int n = a.npts ? int(*a.npts) : a.n_fixed;
-    if (k >= n) return;   // the whole warp: nothing below synchronises the CTA
-    const int ws = 2 * a.wh + 1, NS = ws * ws;
-    float* sI = tsm + size_t(warp) * 3 * NS;
+    if (k >= n) return;   // the whole CTA
+    const int wh = a.wh, ws = 2 * wh + 1, NS = ws * ws;
+    const int PS = ws + 3, QS = ws + 1 + 2 * kTrackMargin;
+    float* sI = tsm;
     float* sX = sI + NS;
     float* sY = sX + NS;
+    float* pt = sY + NS;
     const float2 u = a.pts[k];
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     bool ok = true;
@@ -397,20 +524,22 @@ __global__ void __launch_bounds__(kTrackWarps * 32) ho_track_kernel(const HoTrac
         const float fx0 = floorf(ux), fy0 = floorf(uy);
         const int ix = int(fx0), iy = int(fy0);
         const float fx = ux - fx0, fy = uy - fy0;
+        // the previous frame's pixels ix - wh - 1 .. ix + wh + 2 (and rows)
+        for (int q = tid; q < PS * PS; q += kTrackThreads) {
+            const int r = q / PS, c = q - r * PS;
+            pt[q] = ho_px(P, w, h, ix - wh - 1 + c, iy - wh - 1 + r);
+        }
+        __syncthreads();
         float ga = 0.f, gb = 0.f, gc = 0.f;
-        for (int s = lane; s < NS; s += 32) {
-            const int i = s % ws - a.wh, j = s / ws - a.wh;
-            const int x0 = ix + i, y0 = iy + j;
-            float v[4][4];   // pixels x0-1 .. x0+2, y0-1 .. y0+2
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                for (int ii = 0; ii < 4; ++ii) v[jj][ii] = ho_px(P, w, h, x0 - 1 + ii, y0 - 1 + jj);
-            const float I = ho_bil(v[1][1], v[1][2], v[2][1], v[2][2], fx, fy);
-            const float Ix = ho_bil(0.5f * (v[1][2] - v[1][0]), 0.5f * (v[1][3] - v[1][1]),
-                                    0.5f * (v[2][2] - v[2][0]), 0.5f * (v[2][3] - v[2][1]), fx, fy);
-            const float Iy = ho_bil(0.5f * (v[2][1] - v[0][1]), 0.5f * (v[2][2] - v[0][2]),
-                                    0.5f * (v[3][1] - v[1][1]), 0.5f * (v[3][2] - v[1][2]), fx, fy);
+        for (int s = tid; s < NS; s += kTrackThreads) {
+            const int j = s / ws, i = s - j * ws;
+            const float* b = pt + j * PS + i;   // pixel (x0 - 1, y0 - 1) of the sample
+            const float v11 = b[PS + 1], v12 = b[PS + 2], v21 = b[2 * PS + 1], v22 = b[2 * PS + 2];
+            const float I = ho_bil(v11, v12, v21, v22, fx, fy);
+            const float Ix = ho_bil(0.5f * (v12 - b[PS]), 0.5f * (b[PS + 3] - v11),
+                                    0.5f * (v22 - b[2 * PS]), 0.5f * (b[2 * PS + 3] - v21), fx, fy);
+            const float Iy = ho_bil(0.5f * (v21 - b[1]), 0.5f * (v22 - b[2]),
+                                    0.5f * (b[3 * PS + 1] - v11), 0.5f * (b[3 * PS + 2] - v12), fx, fy);
             sI[s] = I;
             sX[s] = Ix;
             sY[s] = Iy;
@@ -418,38 +547,50 @@ __global__ void __launch_bounds__(kTrackWarps * 32) ho_track_kernel(const HoTrac
             gb += Ix * Iy;
             gc += Iy * Iy;
         }
-        ga = ho_wsum(ga);
-        gb = ho_wsum(gb);
-        gc = ho_wsum(gc);
+        const float3 G = ho_csum3(ga, gb, gc, red);   // also orders the samples' stores
+        ga = G.x;
+        gb = G.y;
+        gc = G.z;
         const float det = ga * gc - gb * gb;
         const float lmin = 0.5f * ((ga + gc) - sqrtf((ga - gc) * (ga - gc) + 4.0f * gb * gb));
         if (lmin / float(NS) < a.min_eig || det == 0.0f) {
             ok = false;
             break;
         }
-        __syncwarp();
         const uint8_t* Qp = a.Q.p[l];
         float vx = 0.f, vy = 0.f;
+        int sx0 = 0, sy0 = 0;
+        bool staged = false;
         for (int it = 0; it < a.max_iters; ++it) {
             const float qx = ux + gx + vx, qy = uy + gy + vy;
             const float qx0 = floorf(qx), qy0 = floorf(qy);
             const int jx = int(qx0), jy = int(qy0);
             const float qfx = qx - qx0, qfy = qy - qy0;
+            // the window needs columns jx - wh .. jx + wh + 1 (and rows)
+            const int ox = jx - wh - sx0, oy = jy - wh - sy0;
+            if (!staged || ox < 0 || oy < 0 || ox > 2 * kTrackMargin || oy > 2 * kTrackMargin) {
+                sx0 = jx - wh - kTrackMargin;
+                sy0 = jy - wh - kTrackMargin;
+                for (int q = tid; q < QS * QS; q += kTrackThreads) {
+                    const int r = q / QS, c = q - r * QS;
+                    pt[q] = ho_px(Qp, w, h, sx0 + c, sy0 + r);
+                }
+                __syncthreads();
+                staged = true;
+            }
+            const float* pw = pt + (jy - wh - sy0) * QS + (jx - wh - sx0);
             float bx = 0.f, by = 0.f;
-            for (int s = lane; s < NS; s += 32) {
-                const int i = s % ws - a.wh, j = s / ws - a.wh;
-                const int x0 = jx + i, y0 = jy + j;
-                const float J = ho_bil(ho_px(Qp, w, h, x0, y0), ho_px(Qp, w, h, x0 + 1, y0),
-                                       ho_px(Qp, w, h, x0, y0 + 1), ho_px(Qp, w, h, x0 + 1, y0 + 1),
-                                       qfx, qfy);
+            for (int s = tid; s < NS; s += kTrackThreads) {
+                const int j = s / ws, i = s - j * ws;
+                const float* b = pw + j * QS + i;
+                const float J = ho_bil(b[0], b[1], b[QS], b[QS + 1], qfx, qfy);
                 const float d = sI[s] - J;
                 bx += d * sX[s];
                 by += d * sY[s];
             }
-            bx = ho_wsum(bx);
-            by = ho_wsum(by);
-            const float ex = (gc * bx - gb * by) / det;
-            const float ey = (ga * by - gb * bx) / det;
+            const float3 bb = ho_csum3(bx, by, 0.f, red);   // also frees the patch
+            const float ex = (gc * bb.x - gb * bb.y) / det;
+            const float ey = (ga * bb.y - gb * bb.x) / det;
             vx += ex;
             vy += ey;
             if (ex * ex + ey * ey < a.eps2) break;
@@ -460,12 +601,11 @@ __global__ void __launch_bounds__(kTrackWarps * 32) ho_track_kernel(const HoTrac
             gx = 2.0f * (gx + dx);
             gy = 2.0f * (gy + dy);
         }
-        __syncwarp();
     }
     const float px = u.x + gx + dx, py = u.y + gy + dy;
     if (ok && !(px >= 0.0f && px <= float(a.P.w[0] - 1) && py >= 0.0f && py <= float(a.P.h[0] - 1)))
         ok = false;
-    if (lane == 0) {
+    if (tid == 0) {
         a.out[k] = make_float2(px, py);
         a.status[k] = ok ? 1 : 0;
     }
@@ -487,16 +627,15 @@ static int ho_corner_launches(dmsgm_homog_ctx* h, const uint8_t* img, cudaStream
         case 5: ho_score_kernel<5><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
         default: ho_score_kernel<7><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
     }
-    const dim3 cgrid((W + 31) / 32, (H + 7) / 8);
     for (int mode = 0; mode < 3; ++mode) {
-        ho_cand_kernel<<<cgrid, 256, 0, s>>>(h->score, W, H, h->p.quality, mode, h->ctrl,
+        ho_cand_kernel<<<grid, 256, 0, s>>>(h->score, W, H, h->p.quality, mode, h->ctrl,
                                              h->hist_hi, h->hist_lo, h->keys);
         if (mode < 2) ho_select_kernel<<<1, 1024, 0, s>>>(mode, h->ctrl, h->hist_hi, h->hist_lo);
     }
     ho_sort_kernel<<<1, 1024, kHoSortCap * sizeof(unsigned long long), s>>>(h->ctrl, h->keys, h->sel);
-    ho_spacing_kernel<<<1, 32, 0, s>>>(h->ctrl, h->sel, W, h->p.min_distance, h->p.max_corners,
-                                       h->grid, h->gw, h->gh, h->cell, h->corners, h->cscore,
-                                       h->pts_in);
+    ho_spacing_kernel<<<1, 32, ho_spacing_smem(h->gw, h->gh, h->p.max_corners), s>>>(
+        h->ctrl, h->sel, W, h->p.min_distance, h->p.max_corners, h->gw, h->gh, h->cell,
+        h->corners, h->cscore, h->pts_in);
     return ho_check(cudaGetLastError(), "corner kernels");
 }
 
@@ -513,7 +652,7 @@ static void ho_pyramids(const dmsgm_homog_ctx* h, const uint8_t* prev, const uin
 static int ho_track_launches(dmsgm_homog_ctx* h, const uint8_t* prev, const uint8_t* cur,
                              int n_fixed, bool device_count, cudaStream_t s) {
     for (int l = 1; l <= h->p.levels; ++l) {
-        const dim3 grid((h->lw[l] + 31) / 32, (h->lh[l] + 7) / 8, 2);
+        const dim3 grid((h->lw[l] + 127) / 128, (h->lh[l] + 7) / 8, 2);
         ho_pyr_kernel<<<grid, 256, 0, s>>>(l > 1 ? h->pyr[0][l - 1] : prev,
                                            l > 1 ? h->pyr[1][l - 1] : cur, h->lw[l - 1],
                                            h->lh[l - 1], h->pyr[0][l], h->pyr[1][l], h->lw[l],
@@ -531,11 +670,10 @@ static int ho_track_launches(dmsgm_homog_ctx* h, const uint8_t* prev, const uint
     a.npts = device_count ? h->ctrl + kCtrlNPts : nullptr;
     a.out = h->pts_out;
     a.status = h->status;
-    const int ns = (2 * a.wh + 1) * (2 * a.wh + 1);
-    const size_t smem = size_t(kTrackWarps) * 3 * ns * sizeof(float);
+    const size_t smem = size_t(ho_track_floats(a.wh)) * sizeof(float);
     const int n = device_count ? h->p.max_corners : n_fixed;
     if (n > 0)
-        ho_track_kernel<<<(n + kTrackWarps - 1) / kTrackWarps, kTrackWarps * 32, smem, s>>>(a);
+        ho_track_kernel<<<n, kTrackThreads, smem, s>>>(a);
     return ho_check(cudaGetLastError(), "tracking kernels");
 }
 
@@ -565,7 +703,7 @@ void dmsgm_homog_default_params(dmsgm_homog_params* p) {
 int dmsgm_homog_destroy(dmsgm_homog_t h) {
     if (!h) return DMSGM_OK;
     cudaStreamSynchronize(0);
-    void* bufs[] = {h->score, h->zeroed, h->keys, h->sel, h->grid, h->corners, h->cscore,
+    void* bufs[] = {h->score, h->zeroed, h->keys, h->sel, h->corners, h->cscore,
                     h->pts_in, h->pts_out, h->status, h->src, h->dst, h->inl, h->hyp,
                     h->hcount, h->rout};
     for (void* b : bufs)
@@ -601,9 +739,19 @@ int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_
     h->H = H;
     h->p = p;
     cudaGetDevice(&h->device);
-    h->cell = p.min_distance > 1.0 ? int(std::ceil(p.min_distance)) : 1;
-    h->gw = (W + h->cell - 1) / h->cell;
-    h->gh = (H + h->cell - 1) / h->cell;
+    // spacing cells: at least ceil(min_distance) pixels, widened until the
+    // per-cell lists fit the spacing kernel's shared memory
+    const int c0 = p.min_distance > 1.0 ? int(std::ceil(p.min_distance)) : 1;
+    for (int f = 1;; ++f) {
+        h->cell = c0 * f;
+        h->gw = (W + h->cell - 1) / h->cell;
+        h->gh = (H + h->cell - 1) / h->cell;
+        if (p.min_distance <= 1.0) {
+            h->gw = h->gh = 0;   // no spacing rule: no grid
+            break;
+        }
+        if (ho_spacing_smem(h->gw, h->gh, p.max_corners) <= kHoSpaceMax) break;
+    }
     h->lw[0] = W;
     h->lh[0] = H;
     for (int l = 1; l <= p.levels; ++l) {
@@ -619,7 +767,6 @@ int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_
     al(reinterpret_cast<void**>(&h->zeroed), sizeof(uint32_t) * zwords);
     al(reinterpret_cast<void**>(&h->keys), sizeof(unsigned long long) * kHoSortCap);
     al(reinterpret_cast<void**>(&h->sel), sizeof(unsigned long long) * kHoKmax);
-    al(reinterpret_cast<void**>(&h->grid), sizeof(int) * size_t(h->gw) * h->gh * (1 + kHoCellCap));
     al(reinterpret_cast<void**>(&h->corners), sizeof(int) * 2 * kHoMaxPts);
     al(reinterpret_cast<void**>(&h->cscore), sizeof(float) * kHoMaxPts);
     al(reinterpret_cast<void**>(&h->pts_in), sizeof(float2) * kHoMaxPts);
@@ -635,9 +782,12 @@ int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_
         for (int l = 1; l <= p.levels; ++l)
             al(reinterpret_cast<void**>(&h->pyr[i][l]), size_t(h->lw[l]) * h->lh[l]);
     if (e == cudaSuccess) e = cudaMallocHost(&h->host, 256 * 1024);
-    if (e == cudaSuccess) e = cudaMemset(h->grid, 0, sizeof(int) * size_t(h->gw) * h->gh * (1 + kHoCellCap));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    int(kHoSortCap * sizeof(unsigned long long)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_spacing_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   int(kHoSpaceMax));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   int(ho_track_floats(15) * sizeof(float)));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         dmsgm_homog_destroy(h);

@@ -14,7 +14,6 @@ constexpr int kHoTieCap = 8192;        // candidates tied at the selection cut h
 constexpr int kHoSortCap = kHoKmax + kHoTieCap;
 constexpr int kHoMaxPts = 4096;        // corners / pairs per call
 constexpr int kHoMaxLevels = 8;
-constexpr int kHoCellCap = 8;          // kept corners per spacing-grid cell
 
 // Control block (device, zeroed per call): words of the corner selection and
 // the counts that pass between kernels without a host round trip.
@@ -52,7 +51,7 @@ struct HoRansacOut {
 struct dmsgm_homog_ctx {
     int W, H, device;
     dmsgm_homog_params p;
-    int gw, gh, cell;                 // spacing grid (cells of `cell` pixels)
+    int gw, gh, cell;                 // spacing cells (`cell` pixels; none when gw == 0)
     float* score;                     // W x H
     uint32_t* zeroed;                 // one memset per call: ctrl, hist_hi, hist_lo
     uint32_t* ctrl;
@@ -60,7 +59,6 @@ struct dmsgm_homog_ctx {
     uint32_t* hist_lo;                // 65536
     unsigned long long* keys;         // kHoSortCap: above-cut keys, then tie keys
     unsigned long long* sel;          // kHoKmax sorted keys
-    int* grid;                        // gw * gh * (1 + kHoCellCap)
     int* corners;                     // kHoMaxPts x 2
     float* cscore;                    // kHoMaxPts
     float2* pts_in;                   // kHoMaxPts

@@ -5,7 +5,8 @@
 // This unit is compiled with -fmad=false: every expression is evaluated as
 // written, one IEEE operation at a time, so a model and its inlier count are
 // the exact values of the method's operations (a hypothesis' count decides
-// which model wins).
+// which model wins).  FP64 runs at a small fraction of the FP32 rate on this
+// part, so the FP64 work is spread over as many threads as it allows.
 //   pairs       one CTA: the tracked points, in corner order, become pairs
 //               (current pixel centre -> previous pixel centre);
 //   hypotheses  one thread per hypothesis: 4 indices from SplitMix64 on the
@@ -14,8 +15,9 @@
 //               with partial pivoting, back to pixel coordinates;
 //   counts      one CTA per hypothesis, threads over the pairs;
 //   best        one CTA: most inliers, lowest index; its inlier mask; the
-//               least-squares refit, each normal-equation entry summed by one
-//               thread over the inliers in index order, solved by one thread.
+//               least-squares refit, its normal equations summed by the CTA (a
+//               fixed order, not the index order: the refit agrees with the
+//               sequential sum to rounding), solved by one thread.
 #include "dmsgm_homog.cuh"
 
 namespace dmsgm {
@@ -265,20 +267,53 @@ __global__ void __launch_bounds__(256) ho_best_kernel(const uint32_t* ctrl, cons
         inl[k] = (e >= 0.0 && e < t2) ? 1 : 0;
     }
     __syncthreads();
-    // normal equations: entry (i, j) of N (i, j < 8) or row i of the right side (64 + i)
+    // normal equations over the inliers: each thread sums the upper triangle
+    // (36) and the right side (8) over inliers k = t, t + 256, ..; a fixed
+    // tree of warp shuffles and one pass over the 8 warps adds the partials
     const HoNorm tn = ho_norm(W, H);
-    if (t < 72) {
-        const int i = t < 64 ? t / 8 : t - 64, j = t % 8;
-        double s = 0.0;
-        for (int k = 0; k < n; ++k) {
-            if (!inl[k]) continue;
-            double r0[8], r1[8], b[2];
-            ho_rows((src[2 * k] - tn.ox) * tn.s, (src[2 * k + 1] - tn.oy) * tn.s,
-                    (dst[2 * k] - tn.ox) * tn.s, (dst[2 * k + 1] - tn.oy) * tn.s, r0, r1, b);
-            if (t < 64) s += r0[i] * r0[j] + r1[i] * r1[j];
-            else s += r0[i] * b[0] + r1[i] * b[1];
+    double acc[44];
+#pragma unroll
+    for (int e = 0; e < 44; ++e) acc[e] = 0.0;
+    for (int k = t; k < n; k += 256) {
+        if (!inl[k]) continue;
+        double r0[8], r1[8], b[2];
+        ho_rows((src[2 * k] - tn.ox) * tn.s, (src[2 * k + 1] - tn.oy) * tn.s,
+                (dst[2 * k] - tn.ox) * tn.s, (dst[2 * k + 1] - tn.oy) * tn.s, r0, r1, b);
+        int e = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = i; j < 8; ++j) acc[e++] += r0[i] * r0[j] + r1[i] * r1[j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[36 + i] += r0[i] * b[0] + r1[i] * b[1];
+    }
+#pragma unroll
+    for (int e = 0; e < 44; ++e) {
+        double v = acc[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[e] = v;
+    }
+    __shared__ double part[8][44];
+    if ((t & 31) == 0)
+#pragma unroll
+        for (int e = 0; e < 44; ++e) part[t >> 5][e] = acc[e];
+    __syncthreads();
+    if (t < 44) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += part[w][t];
+        int i = 0, e = t;   // entry t of the upper triangle -> (i, j)
+        if (t < 36) {
+            while (e >= 8 - i) {
+                e -= 8 - i;
+                ++i;
+            }
+            const int j = i + e;
+            N[i * 8 + j] = v;
+            N[j * 8 + i] = v;
+        } else {
+            N[64 + (t - 36)] = v;
         }
-        N[t] = s;
     }
     __syncthreads();
     if (t == 0) {
