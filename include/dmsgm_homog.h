@@ -33,7 +33,7 @@
  * (they synchronise the stream).  Errors: DMSGM_ERR_INVALID_ARG for bad
  * arguments (nothing launched), DMSGM_ERR_CUDA for launch failures,
  * DMSGM_ERR_OOM, and DMSGM_ERR_UNSUPPORTED when a frame has more tied
- * candidates at the selection cut than the library holds (65536); the
+ * candidates at the selection cut than the library holds (4096); the
  * message is in dmsgm_last_error().  A handle is not thread-safe.
  */
 #ifndef DMSGM_HOMOG_H

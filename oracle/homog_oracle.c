@@ -47,7 +47,8 @@
  *      system (h33 = 1) in coordinates normalised by the frame,
  *      x' = (x - W/2) * 2/max(W,H), by Gaussian elimination with partial
  *      pivoting (a pivot below 1e-12 rejects the hypothesis).  A pair is an
- *      inlier when its reprojection error^2 < thr^2 (and the projected w > 0).
+ *      inlier when it projects in front (w > 0) with reprojection error below
+ *      thr, evaluated without a division: |(X, Y) - w dst|^2 < thr^2 w^2.
  *      Best model: most inliers, ties to the lower index.  All of this in
  *      FP64, no contraction: the GPU evaluates the same operations.
  *   M8 refit: least squares of the same DLT equations over the best model's
@@ -402,15 +403,16 @@ static int model4(const double* src, const double* dst, const int* idx, Norm t, 
     return 0;
 }
 
-/* the squared reprojection error of pair k under Hp (negative: behind) */
-static double reproj2(const double* Hp, const double* src, const double* dst, int k) {
+/* pair k is an inlier of Hp (M7): it projects in front (Z > 0) and within
+ * thr of its partner, |(X, Y) - Z dst|^2 < thr^2 Z^2 */
+static int inlier(const double* Hp, const double* src, const double* dst, int k, double t2) {
     const double x = src[2 * k], y = src[2 * k + 1];
     const double X = Hp[0] * x + Hp[1] * y + Hp[2];
     const double Y = Hp[3] * x + Hp[4] * y + Hp[5];
     const double Z = Hp[6] * x + Hp[7] * y + Hp[8];
-    if (!(Z > 0.0)) return -1.0;
-    const double ex = X / Z - dst[2 * k], ey = Y / Z - dst[2 * k + 1];
-    return ex * ex + ey * ey;
+    if (!(Z > 0.0)) return 0;
+    const double ex = X - dst[2 * k] * Z, ey = Y - dst[2 * k + 1] * Z;
+    return ex * ex + ey * ey < t2 * Z * Z;
 }
 
 /* M7-M8: the homography src -> dst (both n x 2, pixel coordinates of a W x H
@@ -428,10 +430,7 @@ int ho_ransac(const double* src, const double* dst, int n, int W, int H, int ite
         double Hp[9];
         if (ho_sample4(seed, m, n, idx) || model4(src, dst, idx, t, Hp)) continue;
         int cnt = 0;
-        for (int k = 0; k < n; ++k) {
-            const double e = reproj2(Hp, src, dst, k);
-            cnt += (e >= 0.0 && e < t2);
-        }
+        for (int k = 0; k < n; ++k) cnt += inlier(Hp, src, dst, k, t2);
         if (cnt > bestc) {
             bestc = cnt;
             bm = m;
@@ -440,10 +439,7 @@ int ho_ransac(const double* src, const double* dst, int n, int W, int H, int ite
     }
     if (bm < 0) return -1;
     *best = bm;
-    for (int k = 0; k < n; ++k) {
-        const double e = reproj2(Hb, src, dst, k);
-        inl[k] = (uint8_t)(e >= 0.0 && e < t2);
-    }
+    for (int k = 0; k < n; ++k) inl[k] = (uint8_t)inlier(Hb, src, dst, k, t2);
     /* M8: normal equations over the inliers */
     double N[64] = {0}, r[8] = {0}, h[8];
     for (int k = 0; k < n; ++k) {

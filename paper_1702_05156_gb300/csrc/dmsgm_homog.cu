@@ -16,7 +16,8 @@
 //            the cut, a second one of the low 16 bits inside it the cut value;
 //            candidates above it are kept, those at it (ties) are ordered by
 //            index;
-//   sort     one CTA, bitonic, in shared memory: (score desc, index asc);
+//   sort     one CTA, a stable LSD radix sort in shared memory: (score
+//            desc, index asc);
 //   spacing  one warp takes the sorted candidates 32 at a time: each lane
 //            checks the kept corners of the 3 x 3 cells around it (linked
 //            lists per cell of at least ceil(min_distance) pixels, in shared
@@ -292,37 +293,105 @@ __global__ void __launch_bounds__(1024) ho_select_kernel(int stage, uint32_t* ct
     }
 }
 
-// one CTA of 1024 threads; dynamic shared memory: kHoSortCap keys
+// One CTA of 1024 threads: the selected keys in ascending order (score
+// descending, index ascending) by a stable LSD radix sort, 8 passes of 8
+// bits.  Warp w owns keys [w * E * 32, (w + 1) * E * 32) of a pass, lane l
+// the positions e * 32 + l of that range, so that visiting e = 0, 1, ..
+// visits the warp's keys in order; a key's rank among equal digits comes
+// from a match over the lanes plus the warp's running digit count; a scan in
+// (digit, warp) order gives each (digit, warp) its output offset.  Dynamic
+// shared memory: two key buffers of kHoSortCap and 32 x 256 counters.
+constexpr int kSortE = kHoSortCap / 1024;   // keys per thread and pass
+
 __global__ void __launch_bounds__(1024) ho_sort_kernel(uint32_t* ctrl,
                                                        const unsigned long long* keys,
                                                        unsigned long long* sel) {
     extern __shared__ unsigned long long sk[];
+    unsigned long long* A = sk;
+    unsigned long long* Bf = sk + kHoSortCap;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(sk + 2 * kHoSortCap);   // [256][32]: digit-major
+    __shared__ uint32_t wtot[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t below = (1u << lane) - 1u;
     const uint32_t ngt = min(ctrl[kCtrlNGt], uint32_t(kHoKmax));
     const uint32_t neq = min(ctrl[kCtrlNEq], uint32_t(kHoTieCap));
     const int n = int(ngt + neq);
-    int m = 1;
-    while (m < n) m <<= 1;
-    for (int i = threadIdx.x; i < m; i += 1024)
-        sk[i] = i < int(ngt) ? keys[i] : (i < n ? keys[kHoKmax + (i - int(ngt))] : ~0ull);
+    // pad to a multiple of 1024 with the largest key (sorts last)
+    const int m = (n + 1023) & ~1023;
+    const int E = m / 1024;
+    for (int i = t; i < m; i += 1024)
+        A[i] = i < int(ngt) ? keys[i] : (i < n ? keys[kHoKmax + (i - int(ngt))] : ~0ull);
     __syncthreads();
-    for (int k = 2; k <= m; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < m; i += 1024) {
-                const int p = i ^ j;
-                if (p > i) {
-                    const unsigned long long a = sk[i], b = sk[p];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        sk[i] = b;
-                        sk[p] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    for (int pass = 0; pass < 8 && n > 1; ++pass) {
+        const int sh = 8 * pass;
+        for (int i = t; i < 256 * 32; i += 1024) hist[i] = 0;
+        __syncthreads();
+        const int seg = warp * E * 32;
+        uint32_t rank[kSortE];
+#pragma unroll
+        for (int e = 0; e < kSortE; ++e) {
+            if (e >= E) break;
+            const uint32_t d = uint32_t(A[seg + e * 32 + lane] >> sh) & 0xFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = hist[d * 32 + warp];
+            __syncwarp();
+            rank[e] = before + __popc(peers & below);
+            if ((peers & below) == 0u) hist[d * 32 + warp] = before + __popc(peers);
+            __syncwarp();
         }
+        __syncthreads();
+        // exclusive scan of hist in (digit, warp) order: 8192 counters, 8 per thread
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            loc[q] = hist[8 * t + q];
+            sum += loc[q];
+        }
+        uint32_t v = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) wtot[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w2 = wtot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w2, o);
+                if (lane >= o) w2 += y;
+            }
+            wtot[lane] = w2;
+        }
+        __syncthreads();
+        uint32_t run = (warp ? wtot[warp - 1] : 0u) + v - sum;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t c = loc[q];
+            hist[8 * t + q] = run;
+            run += c;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kSortE; ++e) {
+            if (e >= E) break;
+            const unsigned long long k = A[seg + e * 32 + lane];
+            const uint32_t d = uint32_t(k >> sh) & 0xFFu;
+            Bf[hist[d * 32 + warp] + rank[e]] = k;
+        }
+        __syncthreads();
+        unsigned long long* tmp = A;
+        A = Bf;
+        Bf = tmp;
+    }
     const int ns = min(n, kHoKmax);
-    for (int i = threadIdx.x; i < ns; i += 1024) sel[i] = sk[i];
-    if (threadIdx.x == 0) ctrl[kCtrlNSel] = uint32_t(ns);
+    for (int i = t; i < ns; i += 1024) sel[i] = A[i];
+    if (t == 0) ctrl[kCtrlNSel] = uint32_t(ns);
+}
+
+static size_t ho_sort_smem() {
+    return sizeof(unsigned long long) * 2 * kHoSortCap + sizeof(uint32_t) * 256 * 32;
 }
 
 // One warp.  Dynamic shared memory (when min_distance > 1): the kept
@@ -632,7 +701,7 @@ static int ho_corner_launches(dmsgm_homog_ctx* h, const uint8_t* img, cudaStream
                                              h->hist_hi, h->hist_lo, h->keys);
         if (mode < 2) ho_select_kernel<<<1, 1024, 0, s>>>(mode, h->ctrl, h->hist_hi, h->hist_lo);
     }
-    ho_sort_kernel<<<1, 1024, kHoSortCap * sizeof(unsigned long long), s>>>(h->ctrl, h->keys, h->sel);
+    ho_sort_kernel<<<1, 1024, ho_sort_smem(), s>>>(h->ctrl, h->keys, h->sel);
     ho_spacing_kernel<<<1, 32, ho_spacing_smem(h->gw, h->gh, h->p.max_corners), s>>>(
         h->ctrl, h->sel, W, h->p.min_distance, h->p.max_corners, h->gw, h->gh, h->cell,
         h->corners, h->cscore, h->pts_in);
@@ -783,7 +852,7 @@ int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_
             al(reinterpret_cast<void**>(&h->pyr[i][l]), size_t(h->lw[l]) * h->lh[l]);
     if (e == cudaSuccess) e = cudaMallocHost(&h->host, 256 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   int(kHoSortCap * sizeof(unsigned long long)));
+                                                   int(ho_sort_smem()));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_spacing_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    int(kHoSpaceMax));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -10,7 +10,7 @@
 namespace dmsgm {
 
 constexpr int kHoKmax = 8192;          // candidates considered, strongest first
-constexpr int kHoTieCap = 8192;        // candidates tied at the selection cut held
+constexpr int kHoTieCap = 4096;        // candidates tied at the selection cut held
 constexpr int kHoSortCap = kHoKmax + kHoTieCap;
 constexpr int kHoMaxPts = 4096;        // corners / pairs per call
 constexpr int kHoMaxLevels = 8;

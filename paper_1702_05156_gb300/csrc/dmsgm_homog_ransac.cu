@@ -117,16 +117,17 @@ __device__ void ho_denorm(const double* h, HoNorm t, double* Hp) {
     for (int i = 0; i < 9; ++i) Hp[i] = Hp[i] / z;
 }
 
-// squared reprojection error of pair k (negative: projected behind)
-__device__ __forceinline__ double ho_reproj2(const double* Hp, const double* src, const double* dst,
-                                             int k) {
+// pair k is an inlier of Hp: it projects in front (Z > 0) and within thr,
+// |(X, Y) - Z dst|^2 < thr^2 Z^2 (the reprojection error without a division)
+__device__ __forceinline__ bool ho_inlier(const double* Hp, const double* src, const double* dst,
+                                          int k, double t2) {
     const double x = src[2 * k], y = src[2 * k + 1];
     const double X = Hp[0] * x + Hp[1] * y + Hp[2];
     const double Y = Hp[3] * x + Hp[4] * y + Hp[5];
     const double Z = Hp[6] * x + Hp[7] * y + Hp[8];
-    if (!(Z > 0.0)) return -1.0;
-    const double ex = X / Z - dst[2 * k], ey = Y / Z - dst[2 * k + 1];
-    return ex * ex + ey * ey;
+    if (!(Z > 0.0)) return false;
+    const double ex = X - dst[2 * k] * Z, ey = Y - dst[2 * k + 1] * Z;
+    return ex * ex + ey * ey < t2 * Z * Z;
 }
 
 __global__ void __launch_bounds__(1024) ho_pairs_kernel(uint32_t* ctrl, const float2* pin,
@@ -209,10 +210,7 @@ __global__ void __launch_bounds__(128) ho_count_kernel(const uint32_t* ctrl, con
     for (int i = 0; i < 9; ++i) Hp[i] = hyp[9 * size_t(m) + i];
     const double t2 = thr * thr;
     int c = 0;
-    for (int k = threadIdx.x; k < n; k += 128) {
-        const double e = ho_reproj2(Hp, src, dst, k);
-        c += (e >= 0.0 && e < t2);
-    }
+    for (int k = threadIdx.x; k < n; k += 128) c += ho_inlier(Hp, src, dst, k, t2);
     c = __reduce_add_sync(0xffffffffu, c);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
     __syncthreads();
@@ -262,10 +260,7 @@ __global__ void __launch_bounds__(256) ho_best_kernel(const uint32_t* ctrl, cons
         return;
     }
     const double t2 = thr * thr;
-    for (int k = t; k < n; k += 256) {
-        const double e = ho_reproj2(Hb, src, dst, k);
-        inl[k] = (e >= 0.0 && e < t2) ? 1 : 0;
-    }
+    for (int k = t; k < n; k += 256) inl[k] = ho_inlier(Hb, src, dst, k, t2) ? 1 : 0;
     __syncthreads();
     // normal equations over the inliers: each thread sums the upper triangle
     // (36) and the right side (8) over inliers k = t, t + 256, ..; a fixed
