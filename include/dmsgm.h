@@ -325,6 +325,15 @@ int dmsgm_selftest_wait(dmsgm_t h, unsigned long long timeout_ns, void* cuda_str
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dmsgm_last_error(void);
 
+/* Failure-handling tests (never needed otherwise).  spec "launch:n" makes the
+ * n-th frame launch of the process (dmsgm_process and the per-frame launches
+ * of the host and multi-frame entry points; one per dmsgm_process_batch call)
+ * return DMSGM_ERR_CUDA before anything is launched; "alloc:n" makes the n-th
+ * dmsgm_create/_ex return DMSGM_ERR_OOM before allocating.  Counting restarts
+ * at every call; "launch:0,alloc:0" or NULL switch injection off.  The
+ * environment variable DMSGM_FAULT_INJECT, read once, sets the same. */
+void dmsgm_fault_inject(const char* spec);
+
 /* Library version string. */
 const char* dmsgm_version(void);
 

@@ -36,7 +36,7 @@ EXPORTS = ("dmsgm_state_bytes", "dmsgm_host_state_bytes", "dmsgm_create", "dmsgm
            "dmsgm_process_batch_ex", "dmsgm_process_batch_host",
            "dmsgm_get_state", "dmsgm_set_state", "dmsgm_reset", "dmsgm_get_info",
            "dmsgm_status", "dmsgm_selftest_wait", "dmsgm_prefilter", "dmsgm_last_error",
-           "dmsgm_version",
+           "dmsgm_version", "dmsgm_fault_inject",
            # include/dmsgm_homog.h
            "dmsgm_homog_default_params", "dmsgm_homog_create", "dmsgm_homog_estimate",
            "dmsgm_homog_corners", "dmsgm_homog_track", "dmsgm_homog_ransac",
@@ -112,6 +112,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "dmsgm_prefilter": (I, [P, P, I, I, I, ctypes.c_double, I, P]),
             "dmsgm_last_error": (ctypes.c_char_p, []),
             "dmsgm_version": (ctypes.c_char_p, []),
+            "dmsgm_fault_inject": (None, [ctypes.c_char_p]),
             "dmsgm_homog_default_params": (None, [P]),
             "dmsgm_homog_create": (I, [I, I, P, P]),
             "dmsgm_homog_estimate": (I, [P, P, P, P, P, P]),
@@ -250,6 +251,11 @@ def dmsgm_last_error() -> str:
 
 def dmsgm_version() -> str:
     return load_library().dmsgm_version().decode()
+
+
+def dmsgm_fault_inject(spec: str | None):
+    """Failure-handling tests only: "launch:n" / "alloc:n" (see dmsgm.h)."""
+    load_library().dmsgm_fault_inject(spec.encode() if spec else None)
 
 
 # ----------------------------------------------------------- include/dmsgm_homog.h

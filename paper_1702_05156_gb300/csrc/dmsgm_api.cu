@@ -13,9 +13,66 @@
 #include <cstring>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <atomic>
+#include <cstdlib>
+
 #include "dmsgm_internal.h"
 
 namespace dmsgm {
+
+// NVTX range over an entry point (free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Fault injection for failure-handling tests: the n-th frame launch
+// ("launch:n") or the n-th handle allocation ("alloc:n") of the process fails
+// with DMSGM_ERR_CUDA / DMSGM_ERR_OOM before anything reaches the GPU.  Set
+// by dmsgm_fault_inject or, at the first use, the DMSGM_FAULT_INJECT
+// environment variable; off by default.
+struct FaultPlan {
+    std::atomic<long> launch_at{0}, alloc_at{0}, launches{0}, allocs{0};
+};
+static FaultPlan g_fault;
+
+static void fault_parse(const char* spec) {
+    g_fault.launch_at = 0;
+    g_fault.alloc_at = 0;
+    g_fault.launches = 0;
+    g_fault.allocs = 0;
+    if (!spec) return;
+    const char* p = spec;
+    while (*p) {
+        const char* colon = std::strchr(p, ':');
+        if (!colon) break;
+        const long v = std::strtol(colon + 1, nullptr, 10);
+        if (!std::strncmp(p, "launch", colon - p)) g_fault.launch_at = v;
+        if (!std::strncmp(p, "alloc", colon - p)) g_fault.alloc_at = v;
+        const char* comma = std::strchr(colon, ',');
+        if (!comma) break;
+        p = comma + 1;
+    }
+}
+
+static void fault_init() {
+    static std::once_flag once;
+    std::call_once(once, [] { fault_parse(std::getenv("DMSGM_FAULT_INJECT")); });
+}
+
+static bool fault_launch() {
+    fault_init();
+    const long at = g_fault.launch_at.load();
+    return at > 0 && ++g_fault.launches == at;
+}
+
+static bool fault_alloc() {
+    fault_init();
+    const long at = g_fault.alloc_at.load();
+    return at > 0 && ++g_fault.allocs == at;
+}
 
 static thread_local char g_err[512];
 
@@ -189,6 +246,7 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
     int affine = 0;
     if (!make_coef(H3x3, h->B, &c, &affine))
         return fail(DMSGM_ERR_INVALID_ARG, "homography is not finite in FP32");
+    if (fault_launch()) return fail(DMSGM_ERR_CUDA, "injected launch failure (DMSGM_FAULT_INJECT)");
     int rc;
     bool pdl = h->use_pdl != 0;
     if (h->pre_fused) {
@@ -289,6 +347,11 @@ const char* dmsgm_last_error(void) { return g_err; }
 
 const char* dmsgm_version(void) { return "dmsgm-gb300 0.1 (sm_103a)"; }
 
+void dmsgm_fault_inject(const char* spec) {
+    fault_init();
+    fault_parse(spec);
+}
+
 size_t dmsgm_state_bytes(int W, int H, int B, int prec) {
     if (!valid_dims(W, H, B) || (prec != DMSGM_STATE_FP32 && prec != DMSGM_STATE_FP16)) return 0;
     const size_t N = size_t(W / B) * grid_rows(H, B);
@@ -308,6 +371,7 @@ int dmsgm_create(int W, int H, int B, float ts, float td, int age_max, dmsgm_t* 
 int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const dmsgm_opts* o,
                     dmsgm_t* out) {
     clear_error();
+    NvtxRange nvtx("dmsgm_create");
     if (!out) return fail(DMSGM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!valid_dims(W, H, B))
@@ -325,6 +389,7 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     if (!(tile_rows == 4 * B || tile_rows == 8 * B || tile_rows == 16 * B) || tile_rows > 256)
         return fail(DMSGM_ERR_INVALID_ARG, "tile_rows %d must be 4, 8 or 16 times the block and <= 256",
                     tile_rows);
+    if (fault_alloc()) return fail(DMSGM_ERR_OOM, "injected allocation failure (DMSGM_FAULT_INJECT)");
     const size_t need = dmsgm_state_bytes(W, H, B, opts.precision);
     if (opts.state_mem) {
         if (opts.state_bytes < need)
@@ -434,6 +499,7 @@ int dmsgm_destroy(dmsgm_t h) {
 int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9], uint32_t* mask_dev,
                   void* stream) {
     clear_error();
+    NvtxRange nvtx("dmsgm_process");
     if (!h || !frame_dev || !H3x3 || !mask_dev) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
     if (reinterpret_cast<uintptr_t>(frame_dev) % 16)
         return fail(DMSGM_ERR_INVALID_ARG, "frame must be 16-byte aligned");
@@ -447,6 +513,7 @@ int dmsgm_process(dmsgm_t h, const uint8_t* frame_dev, const double H3x3[9], uin
 int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double* Hs,
                       uint32_t* masks_dev, void* stream) {
     clear_error();
+    NvtxRange nvtx("dmsgm_process_seq");
     if (!h || n < 0 || (n > 0 && (!frames_dev || !Hs || !masks_dev)))
         return fail(DMSGM_ERR_INVALID_ARG, "invalid argument");
     if (reinterpret_cast<uintptr_t>(frames_dev) % 16)
@@ -474,6 +541,7 @@ int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double*
 int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n, const double* Hs,
                        uint32_t* masks_host, void* stream) {
     clear_error();
+    NvtxRange nvtx("dmsgm_process_host");
     if (!h || n < 0 || (n > 0 && (!frames_host || !Hs || !masks_host)))
         return fail(DMSGM_ERR_INVALID_ARG, "invalid argument");
     for (long i = 0; i < 9L * n; ++i)
@@ -525,6 +593,7 @@ int dmsgm_process_batch_ex(int n, const dmsgm_t* hs, const uint8_t* const* frame
                            const double* Hs, uint32_t* const* masks_dev,
                            const dmsgm_batch_opts* opts, void* stream) {
     clear_error();
+    NvtxRange nvtx("dmsgm_process_batch");
     if (n < 0 || n > DMSGM_MAX_BATCH) return fail(DMSGM_ERR_INVALID_ARG, "n=%d out of range", n);
     if (n == 0) return DMSGM_OK;
     if (!hs || !frames_dev || !Hs || !masks_dev) return fail(DMSGM_ERR_INVALID_ARG, "NULL argument");
@@ -546,6 +615,7 @@ int dmsgm_process_batch_ex(int n, const dmsgm_t* hs, const uint8_t* const* frame
     if (!g.ok) return fail(DMSGM_ERR_CUDA, "cannot select device %d", hs[0]->device);
     dmsgm_batch_opts o = {};
     if (opts) o = *opts;
+    if (fault_launch()) return fail(DMSGM_ERR_CUDA, "injected launch failure (DMSGM_FAULT_INJECT)");
     return launch_batch(n, hs, frames_dev, Hs, masks_dev, o, static_cast<cudaStream_t>(stream));
 }
 
@@ -554,6 +624,7 @@ int dmsgm_process_batch_host(int n, const dmsgm_t* hs, const uint8_t* const* fra
                              uint32_t* const* masks_dev, uint32_t* const* masks_host,
                              const dmsgm_batch_opts* opts, void* h2d, void* compute, void* d2h) {
     clear_error();
+    NvtxRange nvtx("dmsgm_process_batch_host");
     if (n < 0 || n > DMSGM_MAX_BATCH) return fail(DMSGM_ERR_INVALID_ARG, "n=%d out of range", n);
     if (n == 0) return DMSGM_OK;
     if (!hs || !frames_host || !frames_dev || !masks_dev || !masks_host)

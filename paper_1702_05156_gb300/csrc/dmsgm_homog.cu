@@ -31,6 +31,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dmsgm_homog.cuh"
 
 namespace dmsgm {
@@ -971,9 +973,20 @@ int dmsgm_homog_ransac(dmsgm_homog_t h, const double* src, const double* dst, in
     return DMSGM_OK;
 }
 
+static int ho_estimate(dmsgm_homog_t h, const uint8_t* prev_dev, const uint8_t* cur_dev,
+                       double H3x3[9], dmsgm_homog_result* res, void* stream);
+
 int dmsgm_homog_estimate(dmsgm_homog_t h, const uint8_t* prev_dev, const uint8_t* cur_dev,
                          double H3x3[9], dmsgm_homog_result* res, void* stream) {
     clear_error();
+    nvtxRangePushA("dmsgm_homog_estimate");
+    const int rc = ho_estimate(h, prev_dev, cur_dev, H3x3, res, stream);
+    nvtxRangePop();
+    return rc;
+}
+
+static int ho_estimate(dmsgm_homog_t h, const uint8_t* prev_dev, const uint8_t* cur_dev,
+                       double H3x3[9], dmsgm_homog_result* res, void* stream) {
     if (!h || !H3x3 || !ho_frame_ok(h, prev_dev) || !ho_frame_ok(h, cur_dev))
         return fail(DMSGM_ERR_INVALID_ARG, "NULL handle or output, or misaligned frame");
     DeviceGuard dg(h->device);

@@ -162,6 +162,10 @@ class GpuEngine:
         back (d2h stream); returns an event that completes with the step.
         The server keeps at most two steps in flight, so a stream's device
         slot is never reused before the step that last used it completed."""
+        with torch.cuda.nvtx.range("serve_step"):
+            return self._launch(reqs)
+
+    def _launch(self, reqs):
         n = len(reqs)
         for lo in range(0, n, _lib.DMSGM_MAX_BATCH):
             part = reqs[lo:lo + _lib.DMSGM_MAX_BATCH]
