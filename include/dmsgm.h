@@ -124,6 +124,17 @@ typedef struct {
                            without programmatic dependent launch.  Results
                            are identical.                                    */
     int pre_separate;   /* 1: always run the preprocessing as its own pass   */
+    int checked;        /* 1: the checked build of the frame step: every state
+                           load and store and every mask byte checks its
+                           index against the grid and the frame; an index
+                           out of range is skipped and sets bit 2 of the
+                           device status word (dmsgm_status then returns
+                           DMSGM_ERR_DEVICE_STATUS).
+                           Slower; for debugging.  Not with mix_spread or the
+                           preprocessing (DMSGM_ERR_INVALID_ARG); the
+                           multi-frame entry point runs per-frame launches
+                           and the batched one refuses such handles
+                           (DMSGM_ERR_UNSUPPORTED).                          */
 } dmsgm_opts;
 
 enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1, DMSGM_KERNEL_PIPE = 2 };
@@ -145,6 +156,7 @@ typedef struct {
                                     0 before the first                        */
     int mix_spread;              /* dmsgm_opts.mix_spread in use              */
     int pre_fused;               /* 1: the step kernel filters its own tile   */
+    int checked;                 /* dmsgm_opts.checked in use                 */
 } dmsgm_info;
 
 /* Device bytes a handle needs for its state: a 256-byte control block, one
@@ -311,8 +323,9 @@ int dmsgm_reset(dmsgm_t h);
 int dmsgm_get_info(dmsgm_t h, dmsgm_info* out);
 
 /* Synchronise the handle's device and read its device status word:
- * DMSGM_OK, or DMSGM_ERR_TIMEOUT if a kernel gave up on a wait (the word is
- * then cleared). */
+ * DMSGM_OK; DMSGM_ERR_DEVICE_STATUS if a checked kernel met an index out of
+ * range; DMSGM_ERR_TIMEOUT if a kernel gave up on a wait.  A set word is
+ * cleared. */
 int dmsgm_status(dmsgm_t h);
 
 /* Diagnostic of the device-side failure path: enqueue a kernel that waits on

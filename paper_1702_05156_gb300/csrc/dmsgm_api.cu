@@ -279,7 +279,7 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
     StreamArgs a;
     fill_args(h, affine, mask_dev, &a);
     bool launched = false;
-    if (h->kernel != DMSGM_KERNEL_TILE && !h->pre_buf) {
+    if (h->kernel != DMSGM_KERNEL_TILE && !h->pre_buf && !h->checked) {
         rc = launch_pipe(h, *tm, a, c, s, h->kernel == DMSGM_KERNEL_AUTO, &launched);
         if (rc) return rc;
     }
@@ -420,6 +420,16 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     }
     h->kernel = opts.kernel;
     h->mix_spread = opts.mix_spread ? 1 : 0;
+    if (opts.checked != 0 && opts.checked != 1) {
+        delete h;
+        return fail(DMSGM_ERR_INVALID_ARG, "checked must be 0 or 1");
+    }
+    h->checked = opts.checked;
+    if (h->checked && (h->mix_spread || opts.pre_gauss || opts.pre_median)) {
+        delete h;
+        return fail(DMSGM_ERR_INVALID_ARG, "the checked build covers the plain frame step "
+                    "(no mixture option, no preprocessing)");
+    }
     if ((opts.pre_gauss && (opts.pre_gauss < 3 || opts.pre_gauss > 15 || opts.pre_gauss % 2 == 0 ||
                             !(opts.pre_sigma > 0.0) || !std::isfinite(opts.pre_sigma))) ||
         (opts.pre_median != 0 && opts.pre_median != 1) ||
@@ -739,6 +749,7 @@ int dmsgm_get_info(dmsgm_t h, dmsgm_info* o) {
     o->last_kernel = h->last_kernel;
     o->mix_spread = h->mix_spread;
     o->pre_fused = h->pre_fused;
+    o->checked = h->checked;
     return DMSGM_OK;
 }
 
@@ -752,6 +763,9 @@ int dmsgm_status(dmsgm_t h) {
     if (word) {
         DMSGM_CUDA_TRY(cudaMemset(h->status_dev, 0, sizeof word));
         DMSGM_CUDA_TRY(cudaDeviceSynchronize());
+        if (word & kStatusBounds)
+            return fail(DMSGM_ERR_DEVICE_STATUS,
+                        "a checked kernel met an index out of range and skipped it (status 0x%x)", word);
         return fail(DMSGM_ERR_TIMEOUT, "a kernel gave up waiting for its pixel tile (status 0x%x)", word);
     }
     return DMSGM_OK;

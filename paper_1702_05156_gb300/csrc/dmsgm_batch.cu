@@ -268,6 +268,8 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
                         "batched streams take blocks 4 and 8 on whole block rows (stream %d)", i);
         if (h->pre_gauss || h->pre_median)
             return fail(DMSGM_ERR_UNSUPPORTED, "batched streams take no preprocessing (stream %d)", i);
+        if (h->checked)
+            return fail(DMSGM_ERR_UNSUPPORTED, "batched streams take no checked handles (stream %d)", i);
         BatchItem& it = p.item[i];
         it.frame = frames[i];
         it.mask = masks[i];

@@ -42,6 +42,7 @@ constexpr int kMagicBits = 0x4B400000;
 
 // device status word bits
 constexpr int kStatusWaitTimeout = 1;
+constexpr int kStatusBounds = 2;   // a checked kernel met an index out of range (and skipped it)
 
 // The frame's homography, reduced on the host from FP64 to pairs of floats
 // (hi + lo, "double-float") in one of two forms:
@@ -479,6 +480,25 @@ template <typename T, bool COH>
 __device__ __forceinline__ GlobalSrc<T, COH> global_src(const StreamArgs& a) {
     return GlobalSrc<T, COH>{a.prev.mu, a.prev.var, a.prev.age, a.Gx};
 }
+
+// CheckedSrc: GlobalSrc whose loads check the block index against the grid
+// (n blocks); an index out of range sets kStatusBounds and reads zeros.
+template <typename T, bool COH>
+struct CheckedSrc {
+    GlobalSrc<T, COH> g;
+    int n;
+    int* status;
+    int pitch;
+    __device__ __forceinline__ int at(int i, int j) const { return g.at(i, j); }
+    __device__ __forceinline__ bool ok(int k) const {
+        if (k >= 0 && k < n) return true;
+        atomicOr(status, kStatusBounds);
+        return false;
+    }
+    __device__ __forceinline__ float2 ld_mu(int k) const { return ok(k) ? g.ld_mu(k) : make_float2(0.f, 0.f); }
+    __device__ __forceinline__ float2 ld_var(int k) const { return ok(k) ? g.ld_var(k) : make_float2(0.f, 0.f); }
+    __device__ __forceinline__ uint32_t ld_ag(int k) const { return ok(k) ? g.ld_ag(k) : 0u; }
+};
 
 // Area-weighted mix of the four overlapped blocks whose top-left one is k0
 // (all four on the grid; the weights sum to 1).
@@ -922,13 +942,15 @@ __device__ __forceinline__ void tile_project(const StreamArgs& a, const Coef& k,
 // Gather (gather_fn: Proj -> Comp), update and store the state of the lane's
 // blocks; returns per block the final apparent mean and the mask threshold
 // theta_d * var_A.
-template <int B, typename T, int NW, int RPT, typename GatherFn>
+// CHECK: the state stores check their block index (status: kStatusBounds).
+template <int B, typename T, int NW, int RPT, typename GatherFn, bool CHECK = false>
 __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, int ty0,
                                                  const Proj (&pj)[RPT][kLaneBlocks<B>],
                                                  const Stats (&st)[RPT][kLaneBlocks<B>],
                                                  float (&muA)[RPT][kLaneBlocks<B>],
                                                  float (&thr)[RPT][kLaneBlocks<B>],
-                                                 const GatherFn& gather_fn) {
+                                                 const GatherFn& gather_fn,
+                                                 int* status = nullptr) {
     constexpr int BPL = kLaneBlocks<B>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
@@ -949,7 +971,15 @@ __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, i
         Comp (&c)[BPL] = cc[r];
 #pragma unroll
         for (int j = 0; j < BPL; ++j) dual_mode_step(c[j], st[r][j], a);
-        if (xin && by < a.Gy) {
+        bool store = xin && by < a.Gy;
+        if constexpr (CHECK) {
+            const int k = by * a.Gx + bx;
+            if (store && !(k >= 0 && k + BPL <= a.Gx * a.Gy && bx + BPL <= a.Gx)) {
+                atomicOr(status, kStatusBounds);
+                store = false;
+            }
+        }
+        if (store) {
             const int k = by * a.Gx + bx;   // even for B <= 4: pairs are 16-byte aligned
             if constexpr (B <= 4) {
 #pragma unroll
@@ -993,11 +1023,13 @@ __device__ __forceinline__ bool block_all_bg(const Stats& st, float mu, float th
 // per-pixel test.  Lanes past the frame's right edge but inside the last
 // mask word write zeros, so the padding bits are defined; rows past the
 // frame's bottom edge are not written.
-template <int B, int NW, int RPT>
+// CHECK: every mask byte's row and column are checked (status: kStatusBounds).
+template <int B, int NW, int RPT, bool CHECK = false>
 __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* tile, int tx0,
                                           int ty0, const Stats (&st)[RPT][kLaneBlocks<B>],
                                           const float (&muA)[RPT][kLaneBlocks<B>],
-                                          const float (&thr)[RPT][kLaneBlocks<B>]) {
+                                          const float (&thr)[RPT][kLaneBlocks<B>],
+                                          int* status = nullptr) {
     constexpr int BPL = kLaneBlocks<B>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x = tx0 + kLanePx * lane;
@@ -1011,6 +1043,15 @@ __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* ti
         if (ty0 / B + s >= a.Gy) break;   // warp-uniform
         const int vr = strip_rows<B>(a, ty0, s);
         uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
+        if constexpr (CHECK) {
+            // the rows written are ty0 + B s + i, i < vr; the column byte x / 8
+            const bool bad = active && (ty0 + B * s < 0 || ty0 + B * s + vr > a.H ||
+                                        size_t(x >> 3) >= mrow || vr < 0);
+            if (bad) {
+                atomicOr(status, kStatusBounds);
+                continue;
+            }
+        }
         bool flat = true;   // lanes outside the frame count as flat
         if (xin) {
 #pragma unroll

@@ -66,6 +66,7 @@ struct dmsgm_ctx {
     int seq_tile_rows;           // 0: automatic
     int kernel;                  // DMSGM_KERNEL_*
     int mix_spread;              // 1: mixed variance carries the spread of the mixed means
+    int checked;                 // 1: the per-tile kernel's checked build
     int pre_gauss;               // preprocessing: Gaussian size (0: none)
     double pre_sigma;            //   its sigma
     int pre_median;              //   1: 3 x 3 median

@@ -243,7 +243,7 @@ static SeqShape pick_shape(const dmsgm_ctx* h, int sms) {
     static const SeqShape shapes[] = {{8, 1}, {16, 1}, {16, 2}, {16, 4}};
     // built for blocks 4 and 8 on whole block rows, without the
     // mixture-variance option or preprocessing (those calls run per frame)
-    if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0) || h->mix_spread || h->pre_gauss || h->pre_median)
+    if (!((h->B == 4 || h->B == 8) && h->H % h->B == 0) || h->mix_spread || h->pre_gauss || h->pre_median || h->checked)
         return SeqShape{0, 0};
     if (h->seq_tile_rows) {   // asked for: use it if the tiles fit the GPU at once
         for (const SeqShape& sh : shapes) {

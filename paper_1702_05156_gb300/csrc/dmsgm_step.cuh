@@ -61,11 +61,57 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
     tile_mask<B, NW, RPT>(a, tile, tx0, ty0, st, muA, thr);
 }
 
+// The checked build of the same step (dmsgm_opts.checked): every state load
+// and store and every mask byte checks its index; an index out of range is
+// skipped and sets kStatusBounds in the status word.  No mixture option.
+template <int B, typename T, int NW, int RPT>
+__global__ void __launch_bounds__(NW * 32)
+    dmsgm_step_checked_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a,
+                              const Coef k, int* status) {
+    constexpr int STRIPS = NW * RPT;
+    constexpr int TILE_H = STRIPS * B;
+    __shared__ __align__(128) uint8_t tile[TILE_H * kTileW];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ Origin orig[2 * STRIPS];
+    const int tx0 = blockIdx.x * kTileW;
+    const int ty0 = blockIdx.y * TILE_H;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, TILE_H * kTileW);
+        tma_load_2d(tile, &tmap, tx0, ty0, &bar);
+    }
+    fill_origins<B>(a, k, tx0, ty0, STRIPS, orig);
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+        mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
+        return;
+    }
+    constexpr int BPL = kLaneBlocks<B>;
+    const bool xin = tx0 + kLanePx * int(threadIdx.x & 31) < a.W;
+    Stats st[RPT][BPL];
+    Proj pj[RPT][BPL];
+    tile_stats<B, NW, RPT>(a, tile, ty0, xin, st);
+    tile_project<B, NW, RPT>(a, k, tx0, ty0, orig, pj);
+    pdl_wait();
+    pdl_launch_dependents();
+    float muA[RPT][BPL], thr[RPT][BPL];
+    const CheckedSrc<T, false> src{global_src<T, false>(a), a.Gx * a.Gy, status, a.Gx};
+    auto gather_fn = [&](const Proj& p) { return gather<false>(a, p, src); };
+    tile_update_with<B, T, NW, RPT, decltype(gather_fn), true>(a, tx0, ty0, pj, st, muA, thr,
+                                                               gather_fn, status);
+    tile_mask<B, NW, RPT, true>(a, tile, tx0, ty0, st, muA, thr, status);
+}
+
 template <int B, typename T, int NW, int RPT>
 static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, const Coef& k,
-                                 int* status, cudaStream_t s, bool pdl) {
-    // the mixture-variance option has its own build of the kernel
-    auto kern = a.spread ? dmsgm_step_kernel<B, T, NW, RPT, true> : dmsgm_step_kernel<B, T, NW, RPT, false>;
+                                 int* status, cudaStream_t s, bool pdl, bool checked) {
+    // the mixture-variance option and the checked build have their own kernels
+    auto kern = checked ? dmsgm_step_checked_kernel<B, T, NW, RPT>
+                        : (a.spread ? dmsgm_step_kernel<B, T, NW, RPT, true>
+                                    : dmsgm_step_kernel<B, T, NW, RPT, false>);
     constexpr int TILE_H = NW * RPT * B;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
@@ -121,8 +167,9 @@ cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const Strea
         h->step_rpt = f16 ? step_rpt_q8<B, __half>(h) : step_rpt_q8<B, float>(h);
     const int rpt = q == 8 ? h->step_rpt : (q == 16 ? 2 : 1);
     int* st = h->status_dev;
+    const bool ck = h->checked != 0;
 #define DMSGM_CASE(TT, QQ, NWW, RR) \
-    if (q == QQ && rpt == RR) return launch_step_t<B, TT, NWW, RR>(tmap, a, k, st, s, pdl);
+    if (q == QQ && rpt == RR) return launch_step_t<B, TT, NWW, RR>(tmap, a, k, st, s, pdl, ck);
     if (!f16) {
         DMSGM_CASE(float, 4, 4, 1) DMSGM_CASE(float, 8, 8, 1) DMSGM_CASE(float, 8, 4, 2)
         DMSGM_CASE(float, 16, 8, 2)

@@ -52,7 +52,8 @@ class Dmsgm:
                  theta_d: float = 4.0, age_max: int = 30, precision: str = "fp32",
                  tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None,
                  seq_tile_rows: int = 0, kernel: str = "auto", mix_spread: bool = False,
-                 prefilter: tuple | None = None, prefilter_separate: bool = False):
+                 prefilter: tuple | None = None, prefilter_separate: bool = False,
+                 checked: bool = False):
         prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
         opts = _lib.dmsgm_opts()
         opts.precision = prec
@@ -62,6 +63,7 @@ class Dmsgm:
         opts.kernel = {"auto": DMSGM_KERNEL_AUTO, "tile": DMSGM_KERNEL_TILE,
                        "pipe": DMSGM_KERNEL_PIPE}[kernel]
         opts.mix_spread = 1 if mix_spread else 0
+        opts.checked = 1 if checked else 0
         if prefilter is not None:   # (gauss_size, sigma, median): Sec. 2.1 preprocessing
             opts.pre_gauss, opts.pre_sigma, opts.pre_median = (int(prefilter[0]),
                                                                float(prefilter[1]),
