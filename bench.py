@@ -672,6 +672,18 @@ def main():
     ap.add_argument("--serve-speed", type=float, default=1.0)
     ap.add_argument("--serve-pool", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
+    ap.add_argument("--config", default=None,
+                    help="JSON file of argument defaults (keys: the option names with '_'); "
+                         "options given on the command line override it")
+    pre, _ = ap.parse_known_args()
+    if pre.config:
+        with open(pre.config) as f:
+            cfg = json.load(f)
+        known = {a.dest for a in ap._actions}
+        unknown = sorted(set(cfg) - known)
+        if unknown:
+            ap.error(f"--config: unknown keys {unknown}")
+        ap.set_defaults(**cfg)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -66,3 +66,33 @@ def test_single_rank_reduce_is_identity():
     import bench
     assert bench.reduce_max([1.5, 2.5], torch.device("cpu")) == [1.5, 2.5]
     assert bench.job_rate(2_000_000, 1, 1000.0) == pytest.approx(2.0)
+
+
+def test_config_file_sets_defaults_and_rejects_unknown_keys(tmp_path):
+    """bench.py --config: a JSON file of option defaults; unknown keys are an
+    argument error (exit 2) before any work."""
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"stepz": 3}')
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--config", str(bad)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2 and "unknown keys" in r.stderr
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_cfg", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    good = tmp_path / "good.json"
+    good.write_text('{"steps": 4, "width": 640, "height": 480}')
+    seen = {}
+
+    def fake_run(args):
+        seen.update(vars(args))
+        raise SystemExit(0)
+    orig_argv = sys.argv
+    try:
+        sys.argv = ["bench.py", "--config", str(good), "--steps", "7"]
+        b.run_gpu = fake_run
+        with pytest.raises(SystemExit):
+            b.main()
+    finally:
+        sys.argv = orig_argv
+    assert seen["steps"] == 7 and seen["width"] == 640 and seen["height"] == 480
