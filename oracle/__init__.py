@@ -15,6 +15,7 @@ from .oracle import (  # noqa: F401
     ransac,
     sample4,
     score_map,
+    set_threads,
     splitmix64,
     track,
     OracleState,

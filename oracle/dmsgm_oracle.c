@@ -51,8 +51,8 @@
  * pixels [bx*B, (bx+1)*B) x [by*B, (by+1)*B) clipped to the frame; its centre
  * is ((bx + 0.5) * B, (by + 0.5) * B).
  *
- * Build:  gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so
- *         dmsgm_oracle.c -lm
+ * Build:  gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared [-fopenmp] -o liboracle.so
+ *         dmsgm_oracle.c homog_oracle.c -lm
  * (-ffp-contract=off so that x86 and Arm hosts round identically.)
  */
 #include <math.h>
@@ -145,6 +145,11 @@ int oracle_step_ex(int W, int H, int B, double theta_s, double theta_d, int age_
     if (W <= 0 || H <= 0 || B <= 0) return -1;
     const int Gx = (W + B - 1) / B, Gy = (H + B - 1) / B;
 
+    /* Every block reads only the frame and the previous state and writes only
+     * its own state, mask pixels and diagnostics: the block rows may run on
+     * several threads (OpenMP when built with it, as the paper's CPU version
+     * splits rows over TBB tasks) without changing any result. */
+#pragma omp parallel for schedule(static)
     for (int by = 0; by < Gy; ++by) {
         for (int bx = 0; bx < Gx; ++bx) {
             const size_t k = (size_t)by * Gx + bx;
@@ -297,6 +302,22 @@ int oracle_step(int W, int H, int B, double theta_s, double theta_d, int age_max
                           muA_in, varA_in, ageA_in, muC_in, varC_in, ageC_in,
                           muA_out, varA_out, ageA_out, muC_out, varC_out, ageC_out,
                           mask_out, diag);
+}
+
+/* Threads of the block-row loop (n <= 0: all available); returns the count in
+ * use, 1 when the library was built without OpenMP. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int oracle_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    else omp_set_num_threads(omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /*

@@ -36,9 +36,11 @@ def build_oracle(force: bool = False) -> str:
              or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(p) for p in _SRCS))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, *_SRCS, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"]
+        # OpenMP over the step's block rows when the compiler has it
+        r = subprocess.run(base + ["-fopenmp", "-o", tmp, *_SRCS, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(base + ["-o", tmp, *_SRCS, "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -160,6 +162,15 @@ def oracle_run(frames: np.ndarray, Hs: np.ndarray, *, block: int,
     if rc:
         raise ValueError(f"oracle_run failed ({rc})")
     return st, masks
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the step's block-row loop (0: all available); returns the
+    count in use (1 without OpenMP).  Results do not depend on it."""
+    lib = _load()
+    lib.oracle_threads.restype = ctypes.c_int
+    lib.oracle_threads.argtypes = [ctypes.c_int]
+    return int(lib.oracle_threads(int(n)))
 
 
 def gauss_weights(gauss_size: int, sigma: float) -> np.ndarray:
