@@ -9,15 +9,17 @@
 //   score    tiled: the frame tile with its halo and the Sobel gradients in
 //            shared memory, the structure tensor summed over the window, the
 //            score in FP32 in the fixed order of IEEE operations the method
-//            defines, and the frame maximum (atomicMax on the float bits,
-//            scores being >= 0);
-//   select   the strongest 8192 local maxima exactly, without sorting them
-//            all: a histogram of the scores' high 16 bits finds the bucket of
-//            the cut, a second one of the low 16 bits inside it the cut value;
-//            candidates above it are kept, those at it (ties) are ordered by
-//            index;
-//   sort     one CTA, a stable LSD radix sort in shared memory: (score
-//            desc, index asc);
+//            defines for the tile and a one-pixel ring, the frame maximum
+//            (atomicMax on the float bits, scores being >= 0), and the
+//            tile's local maxima listed with their scores (the score map
+//            itself is never stored);
+//   select   the strongest 8192 candidates (listed maxima above the cut)
+//            exactly, without sorting them all: a histogram of the scores'
+//            high 16 bits finds the bucket of the cut, a second one of the
+//            low 16 bits inside it the cut value; candidates above it are
+//            kept, those at it (ties) are ordered by index;
+//   sort     rank by counting over the GPU (keys are distinct: a key's rank
+//            is the number of smaller ones), then a scatter;
 //   spacing  one warp takes the sorted candidates 32 at a time: each lane
 //            checks the kept corners of the 3 x 3 cells around it (linked
 //            lists per cell of at least ceil(min_distance) pixels, in shared
@@ -42,44 +44,55 @@ __device__ __forceinline__ int clampi_d(int v, int lo, int hi) { return min(max(
 // ---------------------------------------------------------------- scores
 constexpr int kScTX = 64, kScTY = 32;   // 256 threads, 8 pixels each
 
+// Scores of a kScTX x kScTY tile and the ring of pixels around it (the
+// neighbours of the local-maximum test), from the clamped frame tile and its
+// Sobel gradients in shared memory; the tile's maximum goes to the frame's
+// maximum (one atomicMax per CTA), and the tile's interior local maxima with
+// a positive score are listed as keys (~score bits << 32 | index), one
+// global atomic per CTA for their slots.  A candidate (Sec. 2.4 corners:
+// a local maximum above quality x the frame's maximum) is a listed key above
+// the cut, so the later passes read the list, not the frame.
 template <int BS>
-__global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* __restrict__ img, int W,
-                                                       int H, float* __restrict__ score,
+__global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* const* __restrict__ frames,
+                                                       int W, int H,
+                                                       unsigned long long* __restrict__ lmax,
                                                        uint32_t* __restrict__ ctrl) {
-    constexpr int r = BS / 2, R = r + 1;
-    constexpr int IW = kScTX + 2 * R, IH = kScTY + 2 * R;   // staged pixels (clamped)
-    constexpr int GW = kScTX + 2 * r, GH = kScTY + 2 * r;   // gradients of the window positions
+    const uint8_t* __restrict__ img = frames[0];
+    constexpr int r = BS / 2;
+    constexpr int SW = kScTX + 2, SH = kScTY + 2;     // scores: the tile and a 1-pixel ring
+    constexpr int GW = SW + 2 * r, GH = SH + 2 * r;   // gradients of their window positions
+    constexpr int IW = GW + 2, IH = GH + 2;           // staged pixels (clamped)
+    constexpr int ROWS = kScTY / (256 / kScTX);
     __shared__ uint8_t px[IH][IW];
     __shared__ short gx[GH][GW], gy[GH][GW];
-    __shared__ uint32_t wmax[8];
+    __shared__ float sc[SH][SW];
+    __shared__ uint32_t wmax[8], wcnt[8], base;
     const int x0 = blockIdx.x * kScTX, y0 = blockIdx.y * kScTY;
+    const int px0 = x0 - 2 - r, py0 = y0 - 2 - r;     // frame position of px[0][0]
     for (int i = threadIdx.x; i < IW * IH; i += 256) {
         const int yy = i / IW, xx = i - yy * IW;
-        px[yy][xx] = img[size_t(clampi_d(y0 - R + yy, 0, H - 1)) * W + clampi_d(x0 - R + xx, 0, W - 1)];
+        px[yy][xx] = img[size_t(clampi_d(py0 + yy, 0, H - 1)) * W + clampi_d(px0 + xx, 0, W - 1)];
     }
     __syncthreads();
     // the gradient of a window position is that of the clamped position
     for (int i = threadIdx.x; i < GW * GH; i += 256) {
         const int yy = i / GW, xx = i - yy * GW;
-        const int cx = clampi_d(x0 - r + xx, 0, W - 1) - (x0 - R);
-        const int cy = clampi_d(y0 - r + yy, 0, H - 1) - (y0 - R);
+        const int cx = clampi_d(x0 - 1 - r + xx, 0, W - 1) - px0;
+        const int cy = clampi_d(y0 - 1 - r + yy, 0, H - 1) - py0;
         gx[yy][xx] = short((px[cy - 1][cx + 1] + 2 * px[cy][cx + 1] + px[cy + 1][cx + 1]) -
                            (px[cy - 1][cx - 1] + 2 * px[cy][cx - 1] + px[cy + 1][cx - 1]));
         gy[yy][xx] = short((px[cy + 1][cx - 1] + 2 * px[cy + 1][cx] + px[cy + 1][cx + 1]) -
                            (px[cy - 1][cx - 1] + 2 * px[cy - 1][cx] + px[cy - 1][cx + 1]));
     }
     __syncthreads();
-    const int tx = threadIdx.x % kScTX;
-    uint32_t bits = 0;
-    for (int ty = threadIdx.x / kScTX; ty < kScTY; ty += 256 / kScTX) {
-        const int x = x0 + tx, y = y0 + ty;
-        if (x >= W || y >= H) continue;
+    for (int i = threadIdx.x; i < SW * SH; i += 256) {
+        const int yy = i / SW, xx = i - yy * SW;
         int A = 0, B = 0, C = 0;
 #pragma unroll
         for (int j = 0; j < BS; ++j)
 #pragma unroll
-            for (int i = 0; i < BS; ++i) {
-                const int a = gx[ty + j][tx + i], b = gy[ty + j][tx + i];
+            for (int q = 0; q < BS; ++q) {
+                const int a = gx[yy + j][xx + q], b = gy[yy + j][xx + q];
                 A += a * a;
                 B += a * b;
                 C += b * b;
@@ -91,129 +104,179 @@ __global__ void __launch_bounds__(256) ho_score_kernel(const uint8_t* __restrict
         const float f = __fmul_rn(fb, fb);
         const float g = __fmul_rn(4.0f, f);
         const float rr = __fsqrt_rn(__fadd_rn(e, g));
-        float sc = __fmul_rn(0.5f, __fsub_rn(t, rr));
-        sc = sc > 0.0f ? sc : 0.0f;
-        score[size_t(y) * W + x] = sc;
-        bits = max(bits, __float_as_uint(sc));
+        const float v = __fmul_rn(0.5f, __fsub_rn(t, rr));
+        sc[yy][xx] = v > 0.0f ? v : 0.0f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tx = threadIdx.x % kScTX, ty0 = threadIdx.x / kScTX;
+    const int x = x0 + tx;
+    uint32_t bits = 0, nl = 0;
+    unsigned long long kk[ROWS];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+        const int ty = ty0 + q * (256 / kScTX), y = y0 + ty;
+        kk[q] = 0ull;
+        if (x >= W || y >= H) continue;
+        const float v = sc[ty + 1][tx + 1];
+        bits = max(bits, __float_as_uint(v));
+        if (x < 1 || y < 1 || x > W - 2 || y > H - 2 || !(v > 0.0f)) continue;
+        bool lm = true;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if ((i != 1 || j != 1) && sc[ty + j][tx + i] > v) lm = false;
+        if (!lm) continue;
+        kk[q] = (static_cast<unsigned long long>(~__float_as_uint(v)) << 32) | uint32_t(y * W + x);
+        ++nl;
     }
     bits = __reduce_max_sync(0xffffffffu, bits);
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bits;
+    const uint32_t wn = __reduce_add_sync(0xffffffffu, nl);
+    uint32_t pre = nl;   // inclusive prefix in the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += y;
+    }
+    if (lane == 0) {
+        wmax[warp] = bits;
+        wcnt[warp] = wn;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t m = 0;
-        for (int w = 0; w < 8; ++w) m = max(m, wmax[w]);
+        uint32_t m = 0, tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            m = max(m, wmax[w]);
+            const uint32_t c = wcnt[w];
+            wcnt[w] = tot;   // exclusive prefix over warps
+            tot += c;
+        }
         if (m) atomicMax(&ctrl[kCtrlMaxBits], m);
+        base = tot ? atomicAdd(&ctrl[kCtrlLocalMax], tot) : 0u;
     }
+    __syncthreads();
+    uint32_t slot = base + wcnt[warp] + pre - nl;
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q)
+        if (kk[q]) lmax[slot++] = kk[q];
 }
 
 // ---------------------------------------------------------------- candidates
-// The candidate predicate at (x, y): an interior local maximum above the cut.
-__device__ __forceinline__ bool ho_is_cand(const float* __restrict__ s, int W, int H, int x, int y,
-                                           float thr, uint32_t& bits) {
-    if (x < 1 || y < 1 || x > W - 2 || y > H - 2) return false;
-    const float* row = s + size_t(y) * W + x;
-    const float v = row[0];
-    if (!(v > thr)) return false;
-#pragma unroll
-    for (int j = -1; j <= 1; ++j)
-#pragma unroll
-        for (int i = -1; i <= 1; ++i)
-            if ((i || j) && row[j * W + i] > v) return false;
-    bits = __float_as_uint(v);
-    return true;
-}
+// Passes over the listed local maxima (grid-stride, 2048 keys per CTA and
+// round).  A candidate is a listed key whose score is above the cut
+// quality x max (FP32 product).  mode 0: histogram of the candidates' high 16
+// score bits and their count; 1: histogram of the low 16 bits inside the
+// cut's bucket; 2: collect the keys above / at the cut.  Counts and key slots
+// are aggregated per CTA (one global atomic per CTA, round and counter);
+// histogram buckets take one atomic per distinct bucket in a warp.
+// The high-bits histogram of mode 0 is gathered in shared memory when the
+// candidates' high 16 bits (those of the cut up to those of the maximum) span
+// at most kCandSpan buckets, and added to the global one once per CTA and
+// bucket: the busiest buckets would otherwise take one global atomic per
+// warp from every CTA.
+constexpr int kCandPer = 8;
+constexpr int kCandSpan = 8192;
 
-// The candidates of a kScTX x kScTY tile, 8 rows per thread.  mode 0:
-// histogram of the high 16 bits and the count; 1: histogram of the low 16
-// bits inside the cut's bucket; 2: collect the keys above / at the cut.  The
-// CTA aggregates its counts and key slots (one global atomic per CTA and
-// counter); histogram buckets take one atomic per distinct bucket in a warp.
-__global__ void __launch_bounds__(256) ho_cand_kernel(const float* __restrict__ s, int W, int H,
+__global__ void __launch_bounds__(256) ho_cand_kernel(const unsigned long long* __restrict__ lmax,
                                                       double quality, int mode, uint32_t* ctrl,
                                                       uint32_t* hist_hi, uint32_t* hist_lo,
                                                       unsigned long long* keys) {
-    constexpr int ROWS = kScTY / (256 / kScTX);
     __shared__ uint32_t cnt[2], base[2];
+    __shared__ uint32_t shist[kCandSpan];
     if (mode == 1 && ctrl[kCtrlTakeAll]) return;
-    const float thr = __fmul_rn(__double2float_rn(quality), __uint_as_float(ctrl[kCtrlMaxBits]));
+    const uint32_t n = ctrl[kCtrlLocalMax];
+    const uint32_t maxbits = ctrl[kCtrlMaxBits];
+    const float thr = __fmul_rn(__double2float_rn(quality), __uint_as_float(maxbits));
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
-    const int x = blockIdx.x * kScTX + int(threadIdx.x) % kScTX;
-    const int y0 = blockIdx.y * kScTY + int(threadIdx.x) / kScTX;
     const bool take_all = ctrl[kCtrlTakeAll] != 0;
     const uint32_t hi_cut = ctrl[kCtrlHiCut], cut = ctrl[kCtrlCut];
-    if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
-    __syncthreads();
-    uint32_t mb[ROWS];            // this thread's candidate bits per row (0: none)
-    uint32_t ng = 0, ne = 0;      // its keys above / at the cut
+    // candidates have bits > thr's, so their high 16 bits lie in [lo, maxbits >> 16]
+    const uint32_t lo = __float_as_uint(thr) >> 16;
+    const uint32_t span = (maxbits >> 16) - lo + 1u;
+    const bool local = mode == 0 && span <= uint32_t(kCandSpan) && uint32_t(blockIdx.x) * 256u * kCandPer < n;
+    if (local)
+        for (uint32_t b = threadIdx.x; b < span; b += 256) shist[b] = 0;
+    for (uint32_t c0 = blockIdx.x * 256u * kCandPer; c0 < n; c0 += gridDim.x * 256u * kCandPer) {
+        if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        unsigned long long kq[kCandPer];
+        uint32_t ng = 0, ne = 0;   // this thread's keys above / at the cut
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-        const int y = y0 + r * (256 / kScTX);
-        uint32_t bits = 0;
-        const bool cand = x < W && y < H && ho_is_cand(s, W, H, x, y, thr, bits);
-        mb[r] = cand ? bits : 0u;   // a candidate's score is > 0: its bits are not 0
-        if (mode == 0) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, cand ? (bits >> 16) : 0xFFFFFFFFu);
-            if (cand && (peers & below) == 0u) atomicAdd(&hist_hi[bits >> 16], uint32_t(__popc(peers)));
-            ng += cand;
-        } else if (mode == 1) {
-            const bool in = cand && (bits >> 16) == hi_cut;
-            const uint32_t peers = __match_any_sync(0xffffffffu, in ? (bits & 0xFFFFu) : 0xFFFFFFFFu);
-            if (in && (peers & below) == 0u) atomicAdd(&hist_lo[bits & 0xFFFFu], uint32_t(__popc(peers)));
-        } else {
-            ng += cand && (take_all || bits > cut);
-            ne += cand && !take_all && bits == cut;
+        for (int q = 0; q < kCandPer; ++q) {
+            const uint32_t k = c0 + q * 256u + threadIdx.x;
+            const unsigned long long key = k < n ? lmax[k] : 0ull;
+            const uint32_t bits = ~uint32_t(key >> 32);
+            const bool cand = k < n && __uint_as_float(bits) > thr;
+            kq[q] = cand ? key : 0ull;
+            if (mode == 0) {
+                const uint32_t peers = __match_any_sync(0xffffffffu, cand ? (bits >> 16) : 0xFFFFFFFFu);
+                if (cand && (peers & below) == 0u) {
+                    if (local) atomicAdd(&shist[(bits >> 16) - lo], uint32_t(__popc(peers)));
+                    else atomicAdd(&hist_hi[bits >> 16], uint32_t(__popc(peers)));
+                }
+                ng += cand;
+            } else if (mode == 1) {
+                const bool in = cand && (bits >> 16) == hi_cut;
+                const uint32_t peers = __match_any_sync(0xffffffffu, in ? (bits & 0xFFFFu) : 0xFFFFFFFFu);
+                if (in && (peers & below) == 0u) atomicAdd(&hist_lo[bits & 0xFFFFu], uint32_t(__popc(peers)));
+            } else {
+                ng += cand && (take_all || bits > cut);
+                ne += cand && !take_all && bits == cut;
+            }
         }
-    }
-    if (mode == 1) return;
-    // CTA totals: warp sums, one shared atomic per warp, one global per CTA
-    const uint32_t wg = __reduce_add_sync(0xffffffffu, ng), we = __reduce_add_sync(0xffffffffu, ne);
-    // exclusive prefix of this thread inside its warp
-    uint32_t pg = ng, pe = ne;
+        if (mode == 1) continue;
+        const uint32_t wg = __reduce_add_sync(0xffffffffu, ng), we = __reduce_add_sync(0xffffffffu, ne);
+        uint32_t pg = ng, pe = ne;   // inclusive prefixes in the warp
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t a1 = __shfl_up_sync(0xffffffffu, pg, o), a2 = __shfl_up_sync(0xffffffffu, pe, o);
-        if (lane >= o) {
-            pg += a1;
-            pe += a2;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a1 = __shfl_up_sync(0xffffffffu, pg, o), a2 = __shfl_up_sync(0xffffffffu, pe, o);
+            if (lane >= o) {
+                pg += a1;
+                pe += a2;
+            }
         }
-    }
-    pg -= ng;
-    pe -= ne;
-    uint32_t wbase_g = 0, wbase_e = 0;
-    if (lane == 0) {
-        wbase_g = atomicAdd(&cnt[0], wg);
-        wbase_e = atomicAdd(&cnt[1], we);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (mode == 0) {
-            if (cnt[0]) atomicAdd(&ctrl[kCtrlCand], cnt[0]);
-        } else {
-            base[0] = cnt[0] ? atomicAdd(&ctrl[kCtrlNGt], cnt[0]) : 0u;
-            base[1] = cnt[1] ? atomicAdd(&ctrl[kCtrlNEq], cnt[1]) : 0u;
+        pg -= ng;
+        pe -= ne;
+        uint32_t wbase_g = 0, wbase_e = 0;
+        if (lane == 0) {
+            wbase_g = atomicAdd(&cnt[0], wg);
+            wbase_e = atomicAdd(&cnt[1], we);
         }
-    }
-    if (mode == 0) return;
-    __syncthreads();
-    uint32_t kg = base[0] + __shfl_sync(0xffffffffu, wbase_g, 0) + pg;
-    uint32_t ke = base[1] + __shfl_sync(0xffffffffu, wbase_e, 0) + pe;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (mode == 0) {
+                if (cnt[0]) atomicAdd(&ctrl[kCtrlCand], cnt[0]);
+            } else {
+                base[0] = cnt[0] ? atomicAdd(&ctrl[kCtrlNGt], cnt[0]) : 0u;
+                base[1] = cnt[1] ? atomicAdd(&ctrl[kCtrlNEq], cnt[1]) : 0u;
+            }
+        }
+        __syncthreads();
+        if (mode == 0) continue;
+        uint32_t kg = base[0] + __shfl_sync(0xffffffffu, wbase_g, 0) + pg;
+        uint32_t ke = base[1] + __shfl_sync(0xffffffffu, wbase_e, 0) + pe;
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-        const uint32_t bits = mb[r];
-        if (!bits) continue;
-        const int y = y0 + r * (256 / kScTX);
-        const unsigned long long key =
-            (static_cast<unsigned long long>(~bits) << 32) | static_cast<uint32_t>(y * W + x);
-        if (take_all || bits > cut) {
-            if (kg < uint32_t(kHoKmax)) keys[kg] = key;   // < kHoKmax by the cut
-            else ctrl[kCtrlOverflow] = 1;
-            ++kg;
-        } else if (bits == cut) {
-            if (ke < uint32_t(kHoTieCap)) keys[kHoKmax + ke] = key;
-            else ctrl[kCtrlOverflow] = 1;
-            ++ke;
+        for (int q = 0; q < kCandPer; ++q) {
+            const unsigned long long key = kq[q];
+            if (!key) continue;
+            const uint32_t bits = ~uint32_t(key >> 32);
+            if (take_all || bits > cut) {
+                if (kg < uint32_t(kHoKmax)) keys[kg] = key;   // < kHoKmax by the cut
+                else ctrl[kCtrlOverflow] = 1;
+                ++kg;
+            } else if (bits == cut) {
+                if (ke < uint32_t(kHoTieCap)) keys[kHoKmax + ke] = key;
+                else ctrl[kCtrlOverflow] = 1;
+                ++ke;
+            }
         }
+    }
+    if (local) {
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < span; b += 256)
+            if (shist[b]) atomicAdd(&hist_hi[lo + b], shist[b]);
     }
 }
 
@@ -295,122 +358,89 @@ __global__ void __launch_bounds__(1024) ho_select_kernel(int stage, uint32_t* ct
     }
 }
 
-// One CTA of 1024 threads: the selected keys in ascending order (score
-// descending, index ascending) by a stable LSD radix sort, 8 passes of 8
-// bits.  Warp w owns keys [w * E * 32, (w + 1) * E * 32) of a pass, lane l
-// the positions e * 32 + l of that range, so that visiting e = 0, 1, ..
-// visits the warp's keys in order; a key's rank among equal digits comes
-// from a match over the lanes plus the warp's running digit count; a scan in
-// (digit, warp) order gives each (digit, warp) its output offset.  Dynamic
-// shared memory: two key buffers of kHoSortCap and 32 x 256 counters.
-constexpr int kSortE = kHoSortCap / 1024;   // keys per thread and pass
+// The collected keys in ascending order (score descending, index ascending)
+// by counting: keys are distinct, so a key's rank is the number of smaller
+// keys.  Every key above the cut is smaller than every key at it, so the
+// two regions rank separately (the ties after the ngt keys above).  rank:
+// CTA (x, y) counts, for its 256 keys of a region, the smaller keys in the
+// y-th of kHoRankSplit ranges of that region (staged in shared memory);
+// scatter: the partial counts add up to the rank, and keys ranked below
+// kHoKmax are written to it.
+constexpr int kRankCtasGt = kHoKmax / 256, kRankCtasEq = kHoTieCap / 256;
+constexpr int kRankChunk = (kHoKmax + kHoRankSplit - 1) / kHoRankSplit;
 
-__global__ void __launch_bounds__(1024) ho_sort_kernel(uint32_t* ctrl,
-                                                       const unsigned long long* keys,
-                                                       unsigned long long* sel) {
-    extern __shared__ unsigned long long sk[];
-    unsigned long long* A = sk;
-    unsigned long long* Bf = sk + kHoSortCap;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(sk + 2 * kHoSortCap);   // [256][32]: digit-major
-    __shared__ uint32_t wtot[32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint32_t below = (1u << lane) - 1u;
-    const uint32_t ngt = min(ctrl[kCtrlNGt], uint32_t(kHoKmax));
-    const uint32_t neq = min(ctrl[kCtrlNEq], uint32_t(kHoTieCap));
-    const int n = int(ngt + neq);
-    // pad to a multiple of 1024 with the largest key (sorts last)
-    const int m = (n + 1023) & ~1023;
-    const int E = m / 1024;
-    for (int i = t; i < m; i += 1024)
-        A[i] = i < int(ngt) ? keys[i] : (i < n ? keys[kHoKmax + (i - int(ngt))] : ~0ull);
-    __syncthreads();
-    for (int pass = 0; pass < 8 && n > 1; ++pass) {
-        const int sh = 8 * pass;
-        for (int i = t; i < 256 * 32; i += 1024) hist[i] = 0;
-        __syncthreads();
-        const int seg = warp * E * 32;
-        uint32_t rank[kSortE];
-#pragma unroll
-        for (int e = 0; e < kSortE; ++e) {
-            if (e >= E) break;
-            const uint32_t d = uint32_t(A[seg + e * 32 + lane] >> sh) & 0xFFu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t before = hist[d * 32 + warp];
-            __syncwarp();
-            rank[e] = before + __popc(peers & below);
-            if ((peers & below) == 0u) hist[d * 32 + warp] = before + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        // exclusive scan of hist in (digit, warp) order: 8192 counters, 8 per thread
-        uint32_t loc[8], sum = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            loc[q] = hist[8 * t + q];
-            sum += loc[q];
-        }
-        uint32_t v = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        if (lane == 31) wtot[warp] = v;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t w2 = wtot[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, w2, o);
-                if (lane >= o) w2 += y;
-            }
-            wtot[lane] = w2;
-        }
-        __syncthreads();
-        uint32_t run = (warp ? wtot[warp - 1] : 0u) + v - sum;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t c = loc[q];
-            hist[8 * t + q] = run;
-            run += c;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < kSortE; ++e) {
-            if (e >= E) break;
-            const unsigned long long k = A[seg + e * 32 + lane];
-            const uint32_t d = uint32_t(k >> sh) & 0xFFu;
-            Bf[hist[d * 32 + warp] + rank[e]] = k;
-        }
-        __syncthreads();
-        unsigned long long* tmp = A;
-        A = Bf;
-        Bf = tmp;
-    }
-    const int ns = min(n, kHoKmax);
-    for (int i = t; i < ns; i += 1024) sel[i] = A[i];
-    if (t == 0) ctrl[kCtrlNSel] = uint32_t(ns);
+__device__ __forceinline__ void ho_regions(const uint32_t* ctrl, int& ngt, int& neq) {
+    ngt = int(min(ctrl[kCtrlNGt], uint32_t(kHoKmax)));
+    neq = int(min(ctrl[kCtrlNEq], uint32_t(kHoTieCap)));
 }
 
-static size_t ho_sort_smem() {
-    return sizeof(unsigned long long) * 2 * kHoSortCap + sizeof(uint32_t) * 256 * 32;
+__global__ void __launch_bounds__(256) ho_rank_kernel(const uint32_t* ctrl,
+                                                      const unsigned long long* __restrict__ keys,
+                                                      uint32_t* __restrict__ part) {
+    __shared__ __align__(16) unsigned long long sk[kRankChunk];
+    int ngt, neq;
+    ho_regions(ctrl, ngt, neq);
+    const bool tie = blockIdx.x >= kRankCtasGt;
+    const int off = tie ? kHoKmax : 0, nreg = tie ? neq : ngt;
+    const int i0 = (int(blockIdx.x) - (tie ? kRankCtasGt : 0)) * 256;
+    if (i0 >= nreg) return;   // the whole CTA
+    const int chunk = (nreg + kHoRankSplit - 1) / kHoRankSplit;
+    const int j0 = int(blockIdx.y) * chunk, nj = max(0, min(nreg, j0 + chunk) - j0);
+    for (int j = threadIdx.x; j < nj; j += 256) sk[j] = keys[off + j0 + j];
+    if ((nj & 1) && threadIdx.x == 0) sk[nj] = ~0ull;   // pads the last pair (counted as larger)
+    __syncthreads();
+    const int i = i0 + int(threadIdx.x);
+    if (i >= nreg) return;
+    const unsigned long long ki = keys[off + i];
+    uint32_t c0 = 0, c1 = 0;
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sk);
+#pragma unroll 8
+    for (int j = 0; j < (nj + 1) / 2; ++j) {
+        const ulonglong2 v = s2[j];
+        c0 += v.x < ki;
+        c1 += v.y < ki;
+    }
+    part[size_t(blockIdx.y) * kHoSortCap + off + i] = c0 + c1;
+}
+
+__global__ void __launch_bounds__(256) ho_scatter_kernel(uint32_t* ctrl,
+                                                         const unsigned long long* __restrict__ keys,
+                                                         const uint32_t* __restrict__ part,
+                                                         unsigned long long* __restrict__ sel) {
+    int ngt, neq;
+    ho_regions(ctrl, ngt, neq);
+    const int slot = int(blockIdx.x) * 256 + int(threadIdx.x);
+    const bool tie = slot >= kHoKmax;
+    const int i = slot - (tie ? kHoKmax : 0);
+    if (i < (tie ? neq : ngt)) {
+        uint32_t r = tie ? uint32_t(ngt) : 0u;
+#pragma unroll
+        for (int y = 0; y < kHoRankSplit; ++y) r += part[size_t(y) * kHoSortCap + slot];
+        if (r < uint32_t(kHoKmax)) sel[r] = keys[slot];
+    }
+    if (slot == 0) ctrl[kCtrlNSel] = uint32_t(min(ngt + neq, kHoKmax));
 }
 
 // One warp.  Dynamic shared memory (when min_distance > 1): the kept
 // corners as linked lists per cell -- head[gw * gh], next[max_corners],
 // position[max_corners] -- with cells of `cell` >= ceil(min_distance) pixels,
 // so that any corner closer than min_distance lies in the 3 x 3 cells around.
+// Distances are compared as integers: for an integer d2, d2 < md2 (md2 =
+// min_distance^2 in FP64) exactly when d2 < ceil(md2) = t2, which the host
+// computes.  A group of 32 candidates is resolved in order: a lane that is
+// not blocked by a kept corner and has no earlier conflicting lane in its
+// group is kept outright, and the lanes with such conflicts are visited in
+// lane order, each kept when none of the lanes kept before it conflicts.
 __global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
                                                         const unsigned long long* __restrict__ sel,
-                                                        int W, double min_dist, int max_corners,
-                                                        int gw, int gh, int cell, int* corners,
+                                                        int W, int t2, int max_corners, int gw,
+                                                        int gh, int cell, int* corners,
                                                         float* cscore, float2* pts) {
     extern __shared__ int ssm[];
     const int lane = threadIdx.x;
     const uint32_t below = (1u << lane) - 1u;
     const int n = int(ctrl[kCtrlNSel]);
-    const double md2 = min_dist * min_dist;
-    const bool spaced = md2 > 1.0;   // distinct pixels are >= 1 apart
+    const bool spaced = t2 > 1;   // distinct pixels are >= 1 apart
     int* head = ssm;
     int* nxt = head + gw * gh;
     int* pos = nxt + max_corners;
@@ -435,29 +465,26 @@ __global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
                         const int qx = cx + dx, qy = cy + dy;
                         if (qx < 0 || qy < 0 || qx >= gw || qy >= gh) continue;
                         for (int e = head[qy * gw + qx]; e >= 0; e = nxt[e]) {
-                            const long long ddx = x - (pos[e] & 0xFFFF), ddy = y - (pos[e] >> 16);
-                            if (double(ddx * ddx + ddy * ddy) < md2) blocked = true;
+                            const int ddx = x - (pos[e] & 0xFFFF), ddy = y - (pos[e] >> 16);
+                            if (ddx * ddx + ddy * ddy < t2) blocked = true;
                         }
                     }
             }
+#pragma unroll 8
             for (int j = 0; j < 32; ++j) {
                 const int xj = __shfl_sync(0xffffffffu, x, j), yj = __shfl_sync(0xffffffffu, y, j);
-                const long long ddx = x - xj, ddy = y - yj;
-                if (j < lane && g + j < n && double(ddx * ddx + ddy * ddy) < md2) conf |= 1u << j;
+                const int ddx = x - xj, ddy = y - yj;
+                if (j < lane && g + j < n && ddx * ddx + ddy * ddy < t2) conf |= 1u << j;
             }
         }
-        uint32_t acc = 0;
-        if (__ballot_sync(0xffffffffu, conf != 0u) == 0u) {
-            // no conflict inside the group: the unblocked lanes, in order, up
-            // to the remaining count
-            acc = __ballot_sync(0xffffffffu, !blocked);
-            while (__popc(acc) > max_corners - count) acc &= ~(1u << (31 - __clz(acc)));
-        } else {
-            for (int i = 0; i < 32; ++i) {
-                const bool mine = !blocked && !(conf & acc) && count + __popc(acc) < max_corners;
-                acc |= uint32_t(__shfl_sync(0xffffffffu, mine ? 1 : 0, i)) << i;
-            }
+        const uint32_t cl = __ballot_sync(0xffffffffu, !blocked && conf != 0u);
+        uint32_t acc = __ballot_sync(0xffffffffu, !blocked) & ~cl;
+        for (uint32_t rem = cl; rem; rem &= rem - 1u) {
+            const int i = __ffs(rem) - 1;
+            if ((__shfl_sync(0xffffffffu, conf, i) & acc) == 0u) acc |= 1u << i;
         }
+        // the count cap keeps the first kept lanes
+        while (__popc(acc) > max_corners - count) acc &= ~(1u << (31 - __clz(acc)));
         if ((acc >> lane) & 1u) {
             const int p = count + __popc(acc & below);
             corners[2 * p] = x;
@@ -480,11 +507,12 @@ __global__ void __launch_bounds__(32) ho_spacing_kernel(uint32_t* ctrl,
 
 // ---------------------------------------------------------------- pyramid
 // 4 horizontally adjacent outputs per thread: a CTA covers 128 x 8 outputs.
-__global__ void __launch_bounds__(256) ho_pyr_kernel(const uint8_t* __restrict__ in0,
-                                                     const uint8_t* __restrict__ in1, int w, int h,
+// in0 / in1 NULL: the level below is the frame pair itself (the slot).
+__global__ void __launch_bounds__(256) ho_pyr_kernel(const uint8_t* in0, const uint8_t* in1,
+                                                     const uint8_t* const* frames, int w, int h,
                                                      uint8_t* __restrict__ out0,
                                                      uint8_t* __restrict__ out1, int w2, int h2) {
-    const uint8_t* in = blockIdx.z ? in1 : in0;
+    const uint8_t* __restrict__ in = in0 ? (blockIdx.z ? in1 : in0) : frames[blockIdx.z];
     uint8_t* out = blockIdx.z ? out1 : out0;
     const int xb = blockIdx.x * 128 + 4 * (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (xb >= w2 || y >= h2) return;
@@ -510,7 +538,8 @@ __global__ void __launch_bounds__(256) ho_pyr_kernel(const uint8_t* __restrict__
 
 // ---------------------------------------------------------------- tracking
 struct HoTrackArgs {
-    HoPyr P, Q;
+    HoPyr P, Q;                     // levels 1..; level 0 is the frame pair (the slot)
+    const uint8_t* const* frames;
     int levels, wh, max_iters, n_fixed;
     float eps2, min_eig;
     const float2* pts;
@@ -562,7 +591,7 @@ __device__ __forceinline__ float3 ho_csum3(float a, float b, float c, float* red
     return r;
 }
 
-constexpr int kTrackMargin = 2;   // pixels staged around the current frame's window
+constexpr int kTrackMargin = 4;   // pixels staged around the current frame's window
 
 // shared floats per tracking CTA: the window's samples (3 NS) and a pixel
 // patch (the previous frame's, side ws + 3; the current frame's, side
@@ -590,7 +619,7 @@ __global__ void __launch_bounds__(kTrackThreads) ho_track_kernel(const HoTrackAr
     for (int l = a.levels; l >= 0 && ok; --l) {
         const float sc = ldexpf(1.0f, -l);
         const float ux = u.x * sc, uy = u.y * sc;
-        const uint8_t* P = a.P.p[l];
+        const uint8_t* P = l ? a.P.p[l] : a.frames[0];
         const int w = a.P.w[l], h = a.P.h[l];
         const float fx0 = floorf(ux), fy0 = floorf(uy);
         const int ix = int(fx0), iy = int(fy0);
@@ -628,7 +657,7 @@ __global__ void __launch_bounds__(kTrackThreads) ho_track_kernel(const HoTrackAr
             ok = false;
             break;
         }
-        const uint8_t* Qp = a.Q.p[l];
+        const uint8_t* Qp = l ? a.Q.p[l] : a.frames[1];
         float vx = 0.f, vy = 0.f;
         int sx0 = 0, sy0 = 0;
         bool staged = false;
@@ -689,48 +718,54 @@ static int ho_check(cudaError_t e, const char* what) {
                 cudaGetErrorString(e));
 }
 
-static int ho_corner_launches(dmsgm_homog_ctx* h, const uint8_t* img, cudaStream_t s) {
+// The corners of the frame in slot 0.
+static int ho_corner_launches(dmsgm_homog_ctx* h, cudaStream_t s) {
     const int W = h->W, H = h->H;
     const dim3 grid((W + kScTX - 1) / kScTX, (H + kScTY - 1) / kScTY);
     switch (h->p.block_size) {
-        case 1: ho_score_kernel<1><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
-        case 3: ho_score_kernel<3><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
-        case 5: ho_score_kernel<5><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
-        default: ho_score_kernel<7><<<grid, 256, 0, s>>>(img, W, H, h->score, h->ctrl); break;
+        case 1: ho_score_kernel<1><<<grid, 256, 0, s>>>(h->fdev, W, H, h->lmax, h->ctrl); break;
+        case 3: ho_score_kernel<3><<<grid, 256, 0, s>>>(h->fdev, W, H, h->lmax, h->ctrl); break;
+        case 5: ho_score_kernel<5><<<grid, 256, 0, s>>>(h->fdev, W, H, h->lmax, h->ctrl); break;
+        default: ho_score_kernel<7><<<grid, 256, 0, s>>>(h->fdev, W, H, h->lmax, h->ctrl); break;
     }
     for (int mode = 0; mode < 3; ++mode) {
-        ho_cand_kernel<<<grid, 256, 0, s>>>(h->score, W, H, h->p.quality, mode, h->ctrl,
-                                             h->hist_hi, h->hist_lo, h->keys);
+        ho_cand_kernel<<<h->cand_ctas, 256, 0, s>>>(h->lmax, h->p.quality, mode, h->ctrl,
+                                                    h->hist_hi, h->hist_lo, h->keys);
         if (mode < 2) ho_select_kernel<<<1, 1024, 0, s>>>(mode, h->ctrl, h->hist_hi, h->hist_lo);
     }
-    ho_sort_kernel<<<1, 1024, ho_sort_smem(), s>>>(h->ctrl, h->keys, h->sel);
+    ho_rank_kernel<<<dim3(kRankCtasGt + kRankCtasEq, kHoRankSplit), 256, 0, s>>>(h->ctrl, h->keys,
+                                                                                  h->rank);
+    ho_scatter_kernel<<<kHoSortCap / 256, 256, 0, s>>>(h->ctrl, h->keys, h->rank, h->sel);
+    // d2 < min_distance^2 (FP64) <=> d2 < ceil(min_distance^2) for integer d2
+    const double md2 = h->p.min_distance * h->p.min_distance;
+    const int t2 = int(std::ceil(md2));
     ho_spacing_kernel<<<1, 32, ho_spacing_smem(h->gw, h->gh, h->p.max_corners), s>>>(
-        h->ctrl, h->sel, W, h->p.min_distance, h->p.max_corners, h->gw, h->gh, h->cell,
-        h->corners, h->cscore, h->pts_in);
+        h->ctrl, h->sel, W, t2, h->p.max_corners, h->gw, h->gh, h->cell, h->corners, h->cscore,
+        h->pts_in);
     return ho_check(cudaGetLastError(), "corner kernels");
 }
 
-static void ho_pyramids(const dmsgm_homog_ctx* h, const uint8_t* prev, const uint8_t* cur,
-                        HoPyr* P, HoPyr* Q) {
+static void ho_pyramids(const dmsgm_homog_ctx* h, HoPyr* P, HoPyr* Q) {
     for (int l = 0; l <= h->p.levels; ++l) {
         P->w[l] = Q->w[l] = h->lw[l];
         P->h[l] = Q->h[l] = h->lh[l];
-        P->p[l] = l ? h->pyr[0][l] : prev;
-        Q->p[l] = l ? h->pyr[1][l] : cur;
+        P->p[l] = l ? h->pyr[0][l] : nullptr;   // level 0: the slot's frames
+        Q->p[l] = l ? h->pyr[1][l] : nullptr;
     }
 }
 
-static int ho_track_launches(dmsgm_homog_ctx* h, const uint8_t* prev, const uint8_t* cur,
-                             int n_fixed, bool device_count, cudaStream_t s) {
+// Pyramids of the frame pair in the slot and the tracking of h->pts_in.
+static int ho_track_launches(dmsgm_homog_ctx* h, int n_fixed, bool device_count, cudaStream_t s) {
     for (int l = 1; l <= h->p.levels; ++l) {
         const dim3 grid((h->lw[l] + 127) / 128, (h->lh[l] + 7) / 8, 2);
-        ho_pyr_kernel<<<grid, 256, 0, s>>>(l > 1 ? h->pyr[0][l - 1] : prev,
-                                           l > 1 ? h->pyr[1][l - 1] : cur, h->lw[l - 1],
-                                           h->lh[l - 1], h->pyr[0][l], h->pyr[1][l], h->lw[l],
-                                           h->lh[l]);
+        ho_pyr_kernel<<<grid, 256, 0, s>>>(l > 1 ? h->pyr[0][l - 1] : nullptr,
+                                           l > 1 ? h->pyr[1][l - 1] : nullptr, h->fdev,
+                                           h->lw[l - 1], h->lh[l - 1], h->pyr[0][l], h->pyr[1][l],
+                                           h->lw[l], h->lh[l]);
     }
     HoTrackArgs a;
-    ho_pyramids(h, prev, cur, &a.P, &a.Q);
+    ho_pyramids(h, &a.P, &a.Q);
+    a.frames = h->fdev;
     a.levels = h->p.levels;
     a.wh = h->p.win_half;
     a.max_iters = h->p.max_iters;
@@ -774,18 +809,23 @@ void dmsgm_homog_default_params(dmsgm_homog_params* p) {
 int dmsgm_homog_destroy(dmsgm_homog_t h) {
     if (!h) return DMSGM_OK;
     cudaStreamSynchronize(0);
-    void* bufs[] = {h->score, h->zeroed, h->keys, h->sel, h->corners, h->cscore,
-                    h->pts_in, h->pts_out, h->status, h->src, h->dst, h->inl, h->hyp,
-                    h->hcount, h->rout};
+    void* bufs[] = {h->lmax, h->zeroed, h->keys, h->sel, h->rank, h->corners, h->cscore,
+                    h->pts_in, h->pts_out, h->status, h->src, h->dst, h->pf, h->inl, h->hyp, h->hypf,
+                    h->hcount, h->fitpart, h->rout};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 2; ++i)
         for (int l = 0; l <= kHoMaxLevels; ++l)
             if (h->pyr[i][l]) cudaFree(h->pyr[i][l]);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->fdev) cudaFree(h->fdev);
     if (h->host) cudaFreeHost(h->host);
+    if (h->fhost) cudaFreeHost(h->fhost);
     delete h;
     return DMSGM_OK;
 }
+
+static cudaError_t ho_capture(dmsgm_homog_ctx* h);
 
 int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_t* out) {
     clear_error();
@@ -810,6 +850,10 @@ int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_
     h->H = H;
     h->p = p;
     cudaGetDevice(&h->device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1)
+        sms = 1;
+    h->cand_ctas = 2 * sms;   // the list passes' grid-stride CTAs
     // spacing cells: at least ceil(min_distance) pixels, widened until the
     // per-cell lists fit the spacing kernel's shared memory
     const int c0 = p.min_distance > 1.0 ? int(std::ceil(p.min_distance)) : 1;
@@ -834,10 +878,11 @@ int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_
     auto al = [&](void** ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
     };
-    al(reinterpret_cast<void**>(&h->score), sizeof(float) * size_t(W) * H);
+    al(reinterpret_cast<void**>(&h->lmax), sizeof(unsigned long long) * size_t(W) * H);
     al(reinterpret_cast<void**>(&h->zeroed), sizeof(uint32_t) * zwords);
     al(reinterpret_cast<void**>(&h->keys), sizeof(unsigned long long) * kHoSortCap);
     al(reinterpret_cast<void**>(&h->sel), sizeof(unsigned long long) * kHoKmax);
+    al(reinterpret_cast<void**>(&h->rank), sizeof(uint32_t) * kHoRankSplit * kHoSortCap);
     al(reinterpret_cast<void**>(&h->corners), sizeof(int) * 2 * kHoMaxPts);
     al(reinterpret_cast<void**>(&h->cscore), sizeof(float) * kHoMaxPts);
     al(reinterpret_cast<void**>(&h->pts_in), sizeof(float2) * kHoMaxPts);
@@ -845,29 +890,35 @@ int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* pin, dmsgm_homog_
     al(reinterpret_cast<void**>(&h->status), kHoMaxPts);
     al(reinterpret_cast<void**>(&h->src), sizeof(double) * 2 * kHoMaxPts);
     al(reinterpret_cast<void**>(&h->dst), sizeof(double) * 2 * kHoMaxPts);
+    al(reinterpret_cast<void**>(&h->pf), sizeof(float4) * kHoMaxPts);
     al(reinterpret_cast<void**>(&h->inl), kHoMaxPts);
     al(reinterpret_cast<void**>(&h->hyp), sizeof(double) * 9 * size_t(p.ransac_iters));
     al(reinterpret_cast<void**>(&h->hcount), sizeof(int) * size_t(p.ransac_iters));
+    al(reinterpret_cast<void**>(&h->hypf), sizeof(float) * 10 * size_t(p.ransac_iters));
+    al(reinterpret_cast<void**>(&h->fitpart), sizeof(double) * kHoFitCtas * kHoFitTerms);
     al(reinterpret_cast<void**>(&h->rout), sizeof(HoRansacOut));
     for (int i = 0; i < 2; ++i)
         for (int l = 1; l <= p.levels; ++l)
             al(reinterpret_cast<void**>(&h->pyr[i][l]), size_t(h->lw[l]) * h->lh[l]);
+    al(reinterpret_cast<void**>(&h->fdev), 2 * sizeof(const uint8_t*));
     if (e == cudaSuccess) e = cudaMallocHost(&h->host, 256 * 1024);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   int(ho_sort_smem()));
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->fhost), 2 * sizeof(const uint8_t*));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_spacing_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    int(kHoSpaceMax));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ho_track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    int(ho_track_floats(15) * sizeof(float)));
+    if (e == cudaSuccess) {
+        h->ctrl = h->zeroed;
+        h->hist_hi = h->zeroed + kCtrlWords;
+        h->hist_lo = h->hist_hi + 65536;
+        e = ho_capture(h);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         dmsgm_homog_destroy(h);
         return fail(e == cudaErrorMemoryAllocation ? DMSGM_ERR_OOM : DMSGM_ERR_CUDA,
                     "homography handle: %s", cudaGetErrorString(e));
     }
-    h->ctrl = h->zeroed;
-    h->hist_hi = h->zeroed + kCtrlWords;
-    h->hist_lo = h->hist_hi + 65536;
     *out = h;
     return DMSGM_OK;
 }
@@ -876,12 +927,56 @@ static int ho_frame_ok(const dmsgm_homog_ctx* h, const uint8_t* f) {
     return f && reinterpret_cast<uintptr_t>(f) % 16 == 0;
 }
 
-// corners of img into the handle's buffers; counts in ctrl
-static int ho_corners_dev(dmsgm_homog_ctx* h, const uint8_t* img, cudaStream_t s) {
+// The frame pair into the device slot that the kernels read (a copy from
+// pinned staging, so that a captured graph serves any pair; every entry
+// point synchronises before it returns, so the staging is free again).
+static int ho_set_frames(dmsgm_homog_ctx* h, const uint8_t* prev, const uint8_t* cur,
+                         cudaStream_t s) {
+    h->fhost[0] = prev;
+    h->fhost[1] = cur;
+    return ho_check(cudaMemcpyAsync(h->fdev, h->fhost, 2 * sizeof(const uint8_t*),
+                                    cudaMemcpyHostToDevice, s), "frame slot");
+}
+
+// corners of the slot's first frame into the handle's buffers; counts in ctrl
+static int ho_corners_dev(dmsgm_homog_ctx* h, cudaStream_t s) {
     const size_t zbytes = sizeof(uint32_t) * (kCtrlWords + 2 * 65536);
     int rc = ho_check(cudaMemsetAsync(h->zeroed, 0, zbytes, s), "clear");
     if (rc) return rc;
-    return ho_corner_launches(h, img, s);
+    return ho_corner_launches(h, s);
+}
+
+// The whole estimate after the frame slot is set: corners, tracking, RANSAC
+// and the copies of the control words and the result into pinned memory.
+// Captured once per handle into a CUDA graph.
+static int ho_estimate_launches(dmsgm_homog_ctx* h, cudaStream_t s) {
+    int rc = ho_check(cudaMemcpyAsync(h->fdev, h->fhost, 2 * sizeof(const uint8_t*),
+                                      cudaMemcpyHostToDevice, s), "frame slot");
+    if (!rc) rc = ho_corners_dev(h, s);
+    if (!rc) rc = ho_track_launches(h, 0, true, s);
+    if (!rc) rc = ho_launch_ransac(h, true, s);
+    uint32_t* hc = static_cast<uint32_t*>(h->host);
+    HoRansacOut* ho = reinterpret_cast<HoRansacOut*>(hc + kCtrlWords);
+    if (!rc) rc = ho_check(cudaMemcpyAsync(hc, h->ctrl, sizeof(uint32_t) * kCtrlWords, cudaMemcpyDeviceToHost, s), "copy");
+    if (!rc) rc = ho_check(cudaMemcpyAsync(ho, h->rout, sizeof(HoRansacOut), cudaMemcpyDeviceToHost, s), "copy");
+    return rc;
+}
+
+static cudaError_t ho_capture(dmsgm_homog_ctx* h) {
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const int rc = ho_estimate_launches(h, cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess && rc) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return e;
 }
 
 int dmsgm_homog_corners(dmsgm_homog_t h, const uint8_t* img_dev, int* xy, float* scores, int* n,
@@ -891,7 +986,8 @@ int dmsgm_homog_corners(dmsgm_homog_t h, const uint8_t* img_dev, int* xy, float*
         return fail(DMSGM_ERR_INVALID_ARG, "NULL handle, output or misaligned frame");
     DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int rc = ho_corners_dev(h, img_dev, s);
+    int rc = ho_set_frames(h, img_dev, img_dev, s);
+    if (!rc) rc = ho_corners_dev(h, s);
     if (rc) return rc;
     uint32_t* hc = static_cast<uint32_t*>(h->host);
     int* hxy = reinterpret_cast<int*>(hc + kCtrlWords);
@@ -923,7 +1019,8 @@ int dmsgm_homog_track(dmsgm_homog_t h, const uint8_t* prev_dev, const uint8_t* c
     float* hp = static_cast<float*>(h->host);
     memcpy(hp, pts, sizeof(float) * 2 * n);
     int rc = ho_check(cudaMemcpyAsync(h->pts_in, hp, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, s), "copy");
-    if (!rc) rc = ho_track_launches(h, prev_dev, cur_dev, n, false, s);
+    if (!rc) rc = ho_set_frames(h, prev_dev, cur_dev, s);
+    if (!rc) rc = ho_track_launches(h, n, false, s);
     uint8_t* hs = reinterpret_cast<uint8_t*>(hp + 2 * kHoMaxPts);
     if (!rc) rc = ho_check(cudaMemcpyAsync(hp, h->pts_out, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost, s), "copy");
     if (!rc) rc = ho_check(cudaMemcpyAsync(hs, h->status, n, cudaMemcpyDeviceToHost, s), "copy");
@@ -991,13 +1088,11 @@ static int ho_estimate(dmsgm_homog_t h, const uint8_t* prev_dev, const uint8_t* 
         return fail(DMSGM_ERR_INVALID_ARG, "NULL handle or output, or misaligned frame");
     DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int rc = ho_corners_dev(h, prev_dev, s);
-    if (!rc) rc = ho_track_launches(h, prev_dev, cur_dev, 0, true, s);
-    if (!rc) rc = ho_launch_ransac(h, true, s);
-    uint32_t* hc = static_cast<uint32_t*>(h->host);
-    HoRansacOut* ho = reinterpret_cast<HoRansacOut*>(hc + kCtrlWords);
-    if (!rc) rc = ho_check(cudaMemcpyAsync(hc, h->ctrl, sizeof(uint32_t) * kCtrlWords, cudaMemcpyDeviceToHost, s), "copy");
-    if (!rc) rc = ho_check(cudaMemcpyAsync(ho, h->rout, sizeof(HoRansacOut), cudaMemcpyDeviceToHost, s), "copy");
+    h->fhost[0] = prev_dev;
+    h->fhost[1] = cur_dev;
+    int rc = ho_check(cudaGraphLaunch(h->graph, s), "homography graph");
+    const uint32_t* hc = static_cast<const uint32_t*>(h->host);
+    const HoRansacOut* ho = reinterpret_cast<const HoRansacOut*>(hc + kCtrlWords);
     if (!rc) rc = ho_check(cudaStreamSynchronize(s), "homography");
     if (rc) return rc;
     if (hc[kCtrlOverflow])

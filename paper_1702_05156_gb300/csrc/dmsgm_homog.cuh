@@ -14,6 +14,9 @@ constexpr int kHoTieCap = 4096;        // candidates tied at the selection cut h
 constexpr int kHoSortCap = kHoKmax + kHoTieCap;
 constexpr int kHoMaxPts = 4096;        // corners / pairs per call
 constexpr int kHoMaxLevels = 8;
+constexpr int kHoRankSplit = 8;        // key ranges per rank-sort region (partial counts)
+constexpr int kHoFitCtas = 128;        // refit CTAs: kHoMaxPts pairs, 32 each
+constexpr int kHoFitTerms = 44;        // normal-equation terms: upper triangle 36 + right side 8
 
 // Control block (device, zeroed per call): words of the corner selection and
 // the counts that pass between kernels without a host round trip.
@@ -31,6 +34,9 @@ enum HoCtrl {
     kCtrlNCorners,        // corners kept
     kCtrlNPts,            // points to track
     kCtrlNPairs,          // tracked pairs
+    kCtrlLocalMax,        // local maxima listed by the score kernel
+    kCtrlBestM,           // the best hypothesis (-1: none)
+    kCtrlBestC,           // its inlier count
     kCtrlWords = 16
 };
 
@@ -52,13 +58,15 @@ struct dmsgm_homog_ctx {
     int W, H, device;
     dmsgm_homog_params p;
     int gw, gh, cell;                 // spacing cells (`cell` pixels; none when gw == 0)
-    float* score;                     // W x H
+    int cand_ctas;                    // CTAs of the candidate passes over the listed maxima
+    unsigned long long* lmax;         // W x H: the listed local maxima (score key, index)
     uint32_t* zeroed;                 // one memset per call: ctrl, hist_hi, hist_lo
     uint32_t* ctrl;
     uint32_t* hist_hi;                // 65536
     uint32_t* hist_lo;                // 65536
     unsigned long long* keys;         // kHoSortCap: above-cut keys, then tie keys
     unsigned long long* sel;          // kHoKmax sorted keys
+    uint32_t* rank;                   // kHoRankSplit x kHoSortCap partial ranks
     int* corners;                     // kHoMaxPts x 2
     float* cscore;                    // kHoMaxPts
     float2* pts_in;                   // kHoMaxPts
@@ -66,13 +74,19 @@ struct dmsgm_homog_ctx {
     uint8_t* status;
     double* src;                      // kHoMaxPts x 2
     double* dst;
+    float4* pf;                       // kHoMaxPts: the pairs rounded to FP32 (the counts' pre-test)
     uint8_t* inl;                     // kHoMaxPts
     double* hyp;                      // ransac_iters x 9
+    float* hypf;                      // ransac_iters x 10: FP32 copies and their range flag
     int* hcount;                      // ransac_iters
+    double* fitpart;                  // kHoFitCtas x kHoFitTerms refit partial sums
     dmsgm::HoRansacOut* rout;
     uint8_t* pyr[2][dmsgm::kHoMaxLevels + 1];   // levels 1.. of the two images
     int lw[dmsgm::kHoMaxLevels + 1], lh[dmsgm::kHoMaxLevels + 1];
     void* host;                       // pinned staging of the results
+    const uint8_t** fdev;             // device slot: the frame pair the kernels read
+    const uint8_t** fhost;            // its pinned staging
+    cudaGraphExec_t graph;            // the whole estimate (corners, tracking, RANSAC)
 };
 
 namespace dmsgm {
