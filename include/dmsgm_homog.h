@@ -77,7 +77,8 @@ typedef struct {
 void dmsgm_homog_default_params(dmsgm_homog_params* p);
 
 /* A handle for W x H frames; p = NULL takes the defaults.  Allocates the
- * pyramids, the score map and the selection and RANSAC scratch. */
+ * pyramids, the list of local maxima, the selection and RANSAC scratch and
+ * a CUDA graph of the whole estimate. */
 int dmsgm_homog_create(int W, int H, const dmsgm_homog_params* p, dmsgm_homog_t* out);
 
 /* Steps 1-3: H3x3 (host, row-major) maps cur pixel centres to prev ones.

@@ -315,13 +315,21 @@ __device__ void ho_find_cut(const uint32_t* hist, uint32_t need, uint32_t* cut, 
     __syncthreads();
     const uint32_t before = (warp ? warp_sum[warp - 1] : 0u) + v - local;
     if (before < need && before + local >= need) {
+        // this thread's buckets again (16 independent loads), then from the top
+        uint4 r4[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) r4[q] = h4[q];
         uint32_t cum = before;
+        bool found = false;
+#pragma unroll
         for (int b = 0; b < 64; ++b) {
-            const uint32_t h = hist[top - b];
-            if (cum + h >= need) {
+            const uint4 q4 = r4[15 - b / 4];
+            const int e = 3 - b % 4;
+            const uint32_t h = e == 0 ? q4.x : e == 1 ? q4.y : e == 2 ? q4.z : q4.w;
+            if (!found && cum + h >= need) {
                 *cut = uint32_t(top - b);
                 *above = cum;
-                break;
+                found = true;
             }
             cum += h;
         }
@@ -571,48 +579,56 @@ __device__ __forceinline__ float ho_wsum(float v) {
     return v;
 }
 
-// CTA sums of three values, the same on every thread (a fixed order: warp
-// trees, then warps 0..3)
-__device__ __forceinline__ float3 ho_csum3(float a, float b, float c, float* red) {
-    a = ho_wsum(a);
-    b = ho_wsum(b);
-    c = ho_wsum(c);
+// CTA sums of N <= 3 values, the same on every thread (a fixed order: warp
+// trees, then warps 0..3).  red is one of two alternating 12-float slots:
+// consecutive calls use different slots, so one barrier per call suffices
+// (a slot is rewritten two calls later, after every thread has passed the
+// barrier of the call in between).
+template <int N>
+__device__ __forceinline__ void ho_csum(float (&v)[3], float* red) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = ho_wsum(v[i]);
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        red[3 * w] = a;
-        red[3 * w + 1] = b;
-        red[3 * w + 2] = c;
-    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[3 * w + i] = v[i];
     __syncthreads();
-    const float3 r = make_float3(((red[0] + red[3]) + red[6]) + red[9],
-                                 ((red[1] + red[4]) + red[7]) + red[10],
-                                 ((red[2] + red[5]) + red[8]) + red[11]);
-    __syncthreads();
-    return r;
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = ((red[i] + red[3 + i]) + red[6 + i]) + red[9 + i];
 }
 
 constexpr int kTrackMargin = 4;   // pixels staged around the current frame's window
+constexpr int kTrackQ = (31 * 31 + kTrackThreads - 1) / kTrackThreads;   // samples per thread (win_half <= 15)
 
-// shared floats per tracking CTA: the window's samples (3 NS) and a pixel
-// patch (the previous frame's, side ws + 3; the current frame's, side
-// ws + 1 + 2 margins, reused while the iterations stay inside it)
+// shared floats per tracking CTA: a pixel patch (the previous frame's, side
+// ws + 3; the current frame's, side ws + 1 + 2 margins, reused while the
+// iterations stay inside it)
 __host__ __device__ constexpr int ho_track_floats(int wh) {
-    return 3 * (2 * wh + 1) * (2 * wh + 1) + (2 * wh + 2 + 2 * kTrackMargin) * (2 * wh + 2 + 2 * kTrackMargin);
+    return (2 * wh + 2 + 2 * kTrackMargin) * (2 * wh + 2 + 2 * kTrackMargin);
 }
 
+// One CTA per point.  Thread t owns the window samples s = t + 128 q: their
+// offsets and, per level, the previous frame's intensity and gradients stay
+// in its registers; the iterations sum the mismatch over them in the order
+// of s, then across the CTA.
 __global__ void __launch_bounds__(kTrackThreads) ho_track_kernel(const HoTrackArgs a) {
-    extern __shared__ float tsm[];
-    __shared__ float red[12];
+    extern __shared__ float pt[];
+    __shared__ float red[2][12];
     const int tid = threadIdx.x;
     const int k = blockIdx.x;
     const int n = a.npts ? int(*a.npts) : a.n_fixed;
     if (k >= n) return;   // the whole CTA
     const int wh = a.wh, ws = 2 * wh + 1, NS = ws * ws;
     const int PS = ws + 3, QS = ws + 1 + 2 * kTrackMargin;
-    float* sI = tsm;
-    float* sX = sI + NS;
-    float* sY = sX + NS;
-    float* pt = sY + NS;
+    int sij[kTrackQ];   // (j << 16) | i of sample t + 128 q, -1 past the window
+#pragma unroll
+    for (int q = 0; q < kTrackQ; ++q) {
+        const int s = tid + kTrackThreads * q;
+        const int j = s / ws;
+        sij[q] = s < NS ? (j << 16) | (s - j * ws) : -1;
+    }
+    float sI[kTrackQ], sX[kTrackQ], sY[kTrackQ];
+    int rb = 0;
     const float2 u = a.pts[k];
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     bool ok = true;
@@ -630,27 +646,28 @@ __global__ void __launch_bounds__(kTrackThreads) ho_track_kernel(const HoTrackAr
             pt[q] = ho_px(P, w, h, ix - wh - 1 + c, iy - wh - 1 + r);
         }
         __syncthreads();
-        float ga = 0.f, gb = 0.f, gc = 0.f;
-        for (int s = tid; s < NS; s += kTrackThreads) {
-            const int j = s / ws, i = s - j * ws;
-            const float* b = pt + j * PS + i;   // pixel (x0 - 1, y0 - 1) of the sample
+        float G[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < kTrackQ; ++q) {
+            sI[q] = sX[q] = sY[q] = 0.f;
+            if (sij[q] < 0) continue;
+            const float* b = pt + (sij[q] >> 16) * PS + (sij[q] & 0xFFFF);   // pixel (x0 - 1, y0 - 1)
             const float v11 = b[PS + 1], v12 = b[PS + 2], v21 = b[2 * PS + 1], v22 = b[2 * PS + 2];
             const float I = ho_bil(v11, v12, v21, v22, fx, fy);
             const float Ix = ho_bil(0.5f * (v12 - b[PS]), 0.5f * (b[PS + 3] - v11),
                                     0.5f * (v22 - b[2 * PS]), 0.5f * (b[2 * PS + 3] - v21), fx, fy);
             const float Iy = ho_bil(0.5f * (v21 - b[1]), 0.5f * (v22 - b[2]),
                                     0.5f * (b[3 * PS + 1] - v11), 0.5f * (b[3 * PS + 2] - v12), fx, fy);
-            sI[s] = I;
-            sX[s] = Ix;
-            sY[s] = Iy;
-            ga += Ix * Ix;
-            gb += Ix * Iy;
-            gc += Iy * Iy;
+            sI[q] = I;
+            sX[q] = Ix;
+            sY[q] = Iy;
+            G[0] += Ix * Ix;
+            G[1] += Ix * Iy;
+            G[2] += Iy * Iy;
         }
-        const float3 G = ho_csum3(ga, gb, gc, red);   // also orders the samples' stores
-        ga = G.x;
-        gb = G.y;
-        gc = G.z;
+        ho_csum<3>(G, red[rb]);   // also: every thread is done with the patch
+        rb ^= 1;
+        const float ga = G[0], gb = G[1], gc = G[2];
         const float det = ga * gc - gb * gb;
         const float lmin = 0.5f * ((ga + gc) - sqrtf((ga - gc) * (ga - gc) + 4.0f * gb * gb));
         if (lmin / float(NS) < a.min_eig || det == 0.0f) {
@@ -679,18 +696,20 @@ __global__ void __launch_bounds__(kTrackThreads) ho_track_kernel(const HoTrackAr
                 staged = true;
             }
             const float* pw = pt + (jy - wh - sy0) * QS + (jx - wh - sx0);
-            float bx = 0.f, by = 0.f;
-            for (int s = tid; s < NS; s += kTrackThreads) {
-                const int j = s / ws, i = s - j * ws;
-                const float* b = pw + j * QS + i;
+            float bb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < kTrackQ; ++q) {
+                if (sij[q] < 0) continue;
+                const float* b = pw + (sij[q] >> 16) * QS + (sij[q] & 0xFFFF);
                 const float J = ho_bil(b[0], b[1], b[QS], b[QS + 1], qfx, qfy);
-                const float d = sI[s] - J;
-                bx += d * sX[s];
-                by += d * sY[s];
+                const float d = sI[q] - J;
+                bb[0] += d * sX[q];
+                bb[1] += d * sY[q];
             }
-            const float3 bb = ho_csum3(bx, by, 0.f, red);   // also frees the patch
-            const float ex = (gc * bb.x - gb * bb.y) / det;
-            const float ey = (ga * bb.y - gb * bb.x) / det;
+            ho_csum<2>(bb, red[rb]);   // also: every thread is done with the patch
+            rb ^= 1;
+            const float ex = (gc * bb[0] - gb * bb[1]) / det;
+            const float ey = (ga * bb[1] - gb * bb[0]) / det;
             vx += ex;
             vy += ey;
             if (ex * ex + ey * ey < a.eps2) break;
