@@ -806,6 +806,9 @@ __device__ __forceinline__ void store_pair(const StreamArgs& a, int k, const Com
 // Lane layout: warp w of the CTA takes strip rows w, w + NW, ...; lane l owns
 // pixel columns [tx0 + 8l, tx0 + 8l + 8) of its strip row, i.e. two 4x4
 // blocks (B = 4) or one 8x8 block (B = 8), and writes one mask byte per row.
+// B = 1 interleaves instead: lane l owns pixels tx0 + l + 32 j (j = 0..7),
+// so that a warp's gathers and stores of block j touch 32 consecutive
+// blocks, and mask word j of the row is one ballot.
 // A tile is kTileW x (NW * B * RPT) pixels, its pixels in shared memory with
 // row pitch kTileW.  A step runs tile_stats and tile_project (frame and
 // homography only), then tile_update (reads the previous state, writes the
@@ -835,11 +838,11 @@ __device__ __forceinline__ void tile_stats(const StreamArgs& a, const uint8_t* t
         const int s = warp + NW * r;
         const int vr = strip_rows<B>(a, ty0, s);
         if constexpr (B == 1) {
-            // one pixel per block: M = min = max = the pixel
-            const uint2 v = tile_words<B>(tile, s, lane);
+            // one pixel per block: M = min = max = the pixel (interleaved lanes)
+            const uint8_t* row = tile + s * kTileW + lane;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float f = byte_f(j < 4 ? v.x : v.y, j & 3);
+                const float f = float(row[32 * j]);
                 st[r][j] = Stats{f, f, f};
             }
         } else if constexpr (B == 2) {
@@ -924,6 +927,23 @@ __device__ __forceinline__ void tile_project(const StreamArgs& a, const Coef& k,
                                              Proj (&pj)[RPT][kLaneBlocks<B>]) {
     constexpr int BPL = kLaneBlocks<B>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (B == 1) {
+        // block j of the lane is tx0 + lane + 32 j, in half-warp strip j / 4:
+        // the same origin and distance from it as in the blocked layout
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int s = warp + NW * r;
+            const int by = ty0 + s;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int bx = tx0 + lane + 32 * j, half = j >> 2;
+                pj[r][j] = bx < a.W && by < a.Gy
+                               ? project<1>(a, k, bx, by, tx0 + 128 * half, orig[(s << 1) | half])
+                               : no_proj();
+            }
+        }
+        return;
+    }
     const int x = tx0 + kLanePx * lane;
     const int bx = x / B;
     const int half = lane >> 4;
@@ -971,6 +991,25 @@ __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, i
         Comp (&c)[BPL] = cc[r];
 #pragma unroll
         for (int j = 0; j < BPL; ++j) dual_mode_step(c[j], st[r][j], a);
+        if constexpr (B == 1) {
+            // interleaved blocks: one store per block, 32 consecutive per warp
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int bj = tx0 + lane + 32 * j;
+                bool sj = bj < a.W && by < a.Gy;
+                const int kj = by * a.Gx + bj;
+                if constexpr (CHECK) {
+                    if (sj && !(kj >= 0 && kj < a.Gx * a.Gy && bj < a.Gx)) {
+                        atomicOr(status, kStatusBounds);
+                        sj = false;
+                    }
+                }
+                if (sj) store_block<T>(a, kj, c[j]);
+                muA[r][j] = c[j].A.mu;
+                thr[r][j] = a.theta_d * c[j].A.var;
+            }
+            continue;
+        }
         bool store = xin && by < a.Gy;
         if constexpr (CHECK) {
             const int k = by * a.Gx + bx;
@@ -1041,6 +1080,30 @@ __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* ti
     for (int r = 0; r < RPT; ++r) {
         const int s = warp + NW * r;
         if (ty0 / B + s >= a.Gy) break;   // warp-uniform
+        if constexpr (B == 1) {
+            // interleaved pixels: the per-pixel FP32 test, then mask word j of
+            // the tile's row is the ballot of the lanes' pixel j
+            const int y = ty0 + s, w0 = tx0 >> 5;
+            const uint8_t* row = tile + s * kTileW + lane;
+            uint32_t mine = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float d = __fadd_rn(float(row[32 * j]), -muA[r][j]);
+                const bool fg = tx0 + lane + 32 * j < a.W && __fmul_rn(d, d) > thr[r][j];
+                const uint32_t wv = __ballot_sync(0xffffffffu, fg);
+                if (lane == j) mine = wv;
+            }
+            if (lane < 8 && w0 + lane < a.mask_words) {
+                if constexpr (CHECK) {
+                    if (y < 0 || y >= a.H) {
+                        atomicOr(status, kStatusBounds);
+                        continue;
+                    }
+                }
+                a.mask[size_t(y) * a.mask_words + w0 + lane] = mine;
+            }
+            continue;
+        }
         const int vr = strip_rows<B>(a, ty0, s);
         uint8_t* m = mcol + size_t(ty0 + B * s) * mrow;
         if constexpr (CHECK) {
