@@ -806,9 +806,9 @@ __device__ __forceinline__ void store_pair(const StreamArgs& a, int k, const Com
 // Lane layout: warp w of the CTA takes strip rows w, w + NW, ...; lane l owns
 // pixel columns [tx0 + 8l, tx0 + 8l + 8) of its strip row, i.e. two 4x4
 // blocks (B = 4) or one 8x8 block (B = 8), and writes one mask byte per row.
-// B = 1 interleaves instead: lane l owns pixels tx0 + l + 32 j (j = 0..7),
-// so that a warp's gathers and stores of block j touch 32 consecutive
-// blocks, and mask word j of the row is one ballot.
+// B = 1 and 2 interleave instead: lane l owns blocks tx0 / B + l + 32 j
+// (j < 8 / B), so that a warp's gathers and stores of block j touch 32
+// consecutive blocks, and the mask words of a row come from ballots.
 // A tile is kTileW x (NW * B * RPT) pixels, its pixels in shared memory with
 // row pitch kTileW.  A step runs tile_stats and tile_project (frame and
 // homography only), then tile_update (reads the previous state, writes the
@@ -846,35 +846,22 @@ __device__ __forceinline__ void tile_stats(const StreamArgs& a, const uint8_t* t
                 st[r][j] = Stats{f, f, f};
             }
         } else if constexpr (B == 2) {
-            // blocks 2h, 2h+1 are bytes (0, 1) and (2, 3) of word h of both rows;
-            // the 16-bit lanes of the min / max words hold one block each
-            uint32_t sum[4] = {0, 0, 0, 0}, lo[2] = {0x00FF00FFu, 0x00FF00FFu}, hi[2] = {0, 0};
+            // block j of the lane: bytes 2 (lane + 32 j), +1 of the strip's rows
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                if (i >= vr) break;
-                const uint2 v = tile_words<B>(tile, B * s + i, lane);
-                const uint32_t w[2] = {v.x, v.y};
+            for (int j = 0; j < 4; ++j) {
+                uint32_t sum = 0, mn = 255, mx = 0;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    sum[2 * h] = __dp4a(w[h], 0x00000101u, sum[2 * h]);
-                    sum[2 * h + 1] = __dp4a(w[h], 0x01010000u, sum[2 * h + 1]);
-                    const uint32_t e = w[h] & 0x00FF00FFu, o = (w[h] >> 8) & 0x00FF00FFu;
-                    lo[h] = __vimin3_u16x2(lo[h], e, o);
-                    hi[h] = __vimax3_u16x2(hi[h], e, o);
+                for (int i = 0; i < 2; ++i) {
+                    if (i >= vr) break;
+                    const uint32_t v = *reinterpret_cast<const uint16_t*>(
+                        tile + (B * s + i) * kTileW + 2 * (lane + 32 * j));
+                    const uint32_t p0 = v & 0xFFu, p1 = v >> 8;
+                    sum += p0 + p1;
+                    mn = min(mn, min(p0, p1));
+                    mx = max(mx, max(p0, p1));
                 }
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                // block 2h in the low 16-bit lane, block 2h+1 in the high one
-                const uint32_t l0 = lo[h] | 0x00FF0000u, h0 = hi[h] & 0xFFFFu;
-                const uint32_t l1 = (lo[h] >> 16) | 0x00FF0000u, h1 = hi[h] >> 16;
-                if (vr == 2) {
-                    st[r][2 * h] = stats_from<4>(sum[2 * h], l0, h0);
-                    st[r][2 * h + 1] = stats_from<4>(sum[2 * h + 1], l1, h1);
-                } else {
-                    st[r][2 * h] = stats_from<0>(sum[2 * h], l0, h0, 2 * vr);
-                    st[r][2 * h + 1] = stats_from<0>(sum[2 * h + 1], l1, h1, 2 * vr);
-                }
+                st[r][j] = vr == 2 ? stats_from<4>(sum, mn | 0x00FF0000u, mx)
+                                   : stats_from<0>(sum, mn | 0x00FF0000u, mx, 2 * vr);
             }
         } else {
             uint32_t lw[B], rw[B];
@@ -927,18 +914,19 @@ __device__ __forceinline__ void tile_project(const StreamArgs& a, const Coef& k,
                                              Proj (&pj)[RPT][kLaneBlocks<B>]) {
     constexpr int BPL = kLaneBlocks<B>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if constexpr (B == 1) {
-        // block j of the lane is tx0 + lane + 32 j, in half-warp strip j / 4:
-        // the same origin and distance from it as in the blocked layout
+    if constexpr (B <= 2) {
+        // block j of the lane is tx0 / B + lane + 32 j, in half-warp strip
+        // j / (4 / B): the same origin and distance from it as in the blocked
+        // layout
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             const int s = warp + NW * r;
-            const int by = ty0 + s;
+            const int by = ty0 / B + s;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int bx = tx0 + lane + 32 * j, half = j >> 2;
-                pj[r][j] = bx < a.W && by < a.Gy
-                               ? project<1>(a, k, bx, by, tx0 + 128 * half, orig[(s << 1) | half])
+            for (int j = 0; j < BPL; ++j) {
+                const int bx = tx0 / B + lane + 32 * j, half = j / (4 / B);
+                pj[r][j] = bx < a.Gx && by < a.Gy
+                               ? project<B>(a, k, bx, by, (tx0 + 128 * half) / B, orig[(s << 1) | half])
                                : no_proj();
             }
         }
@@ -991,12 +979,12 @@ __device__ __forceinline__ void tile_update_with(const StreamArgs& a, int tx0, i
         Comp (&c)[BPL] = cc[r];
 #pragma unroll
         for (int j = 0; j < BPL; ++j) dual_mode_step(c[j], st[r][j], a);
-        if constexpr (B == 1) {
+        if constexpr (B <= 2) {
             // interleaved blocks: one store per block, 32 consecutive per warp
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int bj = tx0 + lane + 32 * j;
-                bool sj = bj < a.W && by < a.Gy;
+            for (int j = 0; j < BPL; ++j) {
+                const int bj = tx0 / B + lane + 32 * j;
+                bool sj = bj < a.Gx && by < a.Gy;
                 const int kj = by * a.Gx + bj;
                 if constexpr (CHECK) {
                     if (sj && !(kj >= 0 && kj < a.Gx * a.Gy && bj < a.Gx)) {
@@ -1057,6 +1045,14 @@ __device__ __forceinline__ bool block_all_bg(const Stats& st, float mu, float th
     return q.x <= thr && q.y <= thr;
 }
 
+// Bit k of a 16-bit value to bit 2 k.
+__device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    return (x | (x << 1)) & 0x55555555u;
+}
+
 // Mask bytes of the lane's pixel rows from the final apparent models.  A
 // warp whose blocks are all background writes zero bytes without the
 // per-pixel test.  Lanes past the frame's right edge but inside the last
@@ -1101,6 +1097,41 @@ __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* ti
                     }
                 }
                 a.mask[size_t(y) * a.mask_words + w0 + lane] = mine;
+            }
+            continue;
+        }
+        if constexpr (B == 2) {
+            // interleaved blocks: per pixel row, ballots of the blocks' left
+            // and right pixels; mask word 2 j + h holds lanes 16 h .. 16 h + 15
+            // of block j, their bits interleaved (left, right)
+            const int vr2 = strip_rows<B>(a, ty0, s), w0 = tx0 >> 5;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i >= vr2) break;
+                const int y = ty0 + B * s + i;
+                uint32_t bl[4], br[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t v = *reinterpret_cast<const uint16_t*>(
+                        tile + (B * s + i) * kTileW + 2 * (lane + 32 * j));
+                    const bool in = tx0 / B + lane + 32 * j < a.Gx;
+                    const float d0 = __fadd_rn(float(v & 0xFFu), -muA[r][j]);
+                    const float d1 = __fadd_rn(float(v >> 8), -muA[r][j]);
+                    bl[j] = __ballot_sync(0xffffffffu, in && __fmul_rn(d0, d0) > thr[r][j]);
+                    br[j] = __ballot_sync(0xffffffffu, in && __fmul_rn(d1, d1) > thr[r][j]);
+                }
+                if (lane < 8 && w0 + lane < a.mask_words) {
+                    if constexpr (CHECK) {
+                        if (y < 0 || y >= a.H) {
+                            atomicOr(status, kStatusBounds);
+                            continue;
+                        }
+                    }
+                    const int j = lane >> 1, sh = 16 * (lane & 1);
+                    const uint32_t L = ((j == 0 ? bl[0] : j == 1 ? bl[1] : j == 2 ? bl[2] : bl[3]) >> sh) & 0xFFFFu;
+                    const uint32_t R = ((j == 0 ? br[0] : j == 1 ? br[1] : j == 2 ? br[2] : br[3]) >> sh) & 0xFFFFu;
+                    a.mask[size_t(y) * a.mask_words + w0 + lane] = spread_bits16(L) | (spread_bits16(R) << 1);
+                }
             }
             continue;
         }
