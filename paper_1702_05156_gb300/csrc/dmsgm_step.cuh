@@ -13,8 +13,13 @@ constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // 2 s: only a broken copy 
 
 // 8x8 blocks, one strip row per warp: 32 registers (full occupancy); two
 // rows per warp: 64.  4x4 blocks keep the compiler's choice.
+// CTAs per SM the kernel is compiled for.  Block 1 (4 warps, one strip row
+// each): 6, i.e. at most 80 registers instead of 96; at 3840x2160 that took
+// a frame from 113 to 107 us (7 and 8 spill, 131 and 135 us).
 template <int B, int NW, int RPT>
-constexpr int step_min_blocks() { return B == 8 ? (RPT == 1 ? 64 : 32) / NW : 1; }
+constexpr int step_min_blocks() {
+    return B == 8 ? (RPT == 1 ? 64 : 32) / NW : (B == 1 && NW == 4 && RPT == 1 ? 6 : 1);
+}
 
 template <int B, typename T, int NW, int RPT, bool SPREAD>
 __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))

@@ -149,6 +149,32 @@ def test_ransac_bit_exact(H, iters, thr, seed):
     assert np.abs(Hg - Hw).max() <= 1e-9 * np.abs(Hw).max()
 
 
+def test_ransac_counts_at_the_threshold(H):
+    """Pairs whose residual under the true motion is the threshold to within a
+    few parts in 1e9: for hypotheses drawn from the exact inliers the inlier
+    test sits on its threshold, where the counts' FP32 pre-test must leave the
+    decision to FP64.  Counts, winner and inlier set as the oracle's."""
+    rng = np.random.default_rng(11)
+    Ht = np.array([[0.995, 0.012, -6.25], [-0.01, 1.004, 3.5], [1.5e-5, -2e-5, 1.0]])
+    n = 1200
+    src = rng.uniform(0, 1, (n, 2)) * [640, 480]
+    src[: n // 4] = np.round(src[: n // 4]) + 0.5          # pixel centres
+    dst = _apply(Ht, src)
+    edge = rng.random(n) < 0.45
+    ang = rng.uniform(0, 2 * np.pi, n)
+    for thr in (1.0, 2.5):
+        r = thr * (1.0 + rng.integers(-3, 4, n) * 1e-9)
+        r[rng.random(n) < 0.2] = thr                        # exactly on the threshold
+        d = dst + edge[:, None] * (r[:, None] * np.c_[np.cos(ang), np.sin(ang)])
+        Hw, inlw, cw, bw = oracle.ransac(src, d, 640, 480, iters=500, thresh=thr, seed=9)
+        est = H.HomographyEstimator(640, 480, ransac_iters=500, thresh=thr, seed=9)
+        Hg, inlg, res = est.ransac(src, d)
+        assert res.inliers == cw and res.best == bw
+        assert np.array_equal(inlg, inlw)
+        assert np.abs(Hg - Hw).max() <= 1e-9 * np.abs(Hw).max()
+        est.close()
+
+
 def test_ransac_planted_outliers_and_degenerate(H):
     rng = np.random.default_rng(1)
     Ht = np.array([[1.01, -0.02, 4.5], [0.015, 0.99, -3.2], [2e-5, -1e-5, 1.0]])
