@@ -193,7 +193,7 @@ bool make_coef(const double m[9], int B, Coef* c, int* affine) {
         const double ay = m[3] / m[8], byy = m[4] / m[8] - 1.0;
         const double cx = 0.5 * ax + 0.5 * bxx + m[2] / (m[8] * B);
         const double cy = 0.5 * ay + 0.5 * byy + m[5] / (m[8] * B);
-        const double lim = 1.0 / 31.0;   // per-lane step stays exact to ~1e-7
+        const double lim = 1.0 / 31.0;   // per-lane step rounding below 4.8e-7 blocks (affine_origin)
         const double far = 1.0e6;
         if (std::fabs(ax) <= lim && std::fabs(ay) <= lim && std::fabs(bxx) < far &&
             std::fabs(byy) < far && std::fabs(cx) < far && std::fabs(cy) < far) {

@@ -25,7 +25,7 @@ constexpr float kVarInit = 255.0f;   // Sec. 2.3: reset variance
 constexpr float kVarFloor = 0.1f;    // appendix code: max(var, .1) in the match tests
 constexpr float kMinWeight = 1e-3f;  // in-grid weight below this: no source
 constexpr int kTileW = 256;          // pixels per tile row (one TMA box row)
-constexpr int kLanePx = 8;           // pixel columns a lane owns (one mask byte per row)
+constexpr int kLanePx = 8;           // pixel columns a lane owns for B >= 4 (one mask byte per row)
 
 // Blocks a lane owns: 8 / B for B <= 8; for B = 16 a pair of lanes shares one.
 template <int B>
@@ -346,9 +346,11 @@ __device__ __forceinline__ bool project_general(const Coef& k, float x, float y,
 // Affine form: the displacement at the first block bx0 of a half-warp's
 // strip (by), split into integer parts and fractions.  One thread per
 // origin computes it in double-float and publishes it in shared memory; a
-// lane then steps from bx0 to its own block (at most 31 blocks away) with
-// one FMA, whose rounding stays below 1.2e-7 blocks because the host admits
-// the affine form only when |d ex / d bx| * 31 <= 2.
+// lane then steps from bx0 to its own block (at most 128 / B - 1 blocks
+// away: 31 for B = 4, 127 for B = 1) with two FMAs.  The host admits the
+// affine form only when |d ex / d bx| <= 1/31, so the stepped value stays
+// below 2 (B >= 4), 3.1 (B = 2) or 5.1 (B = 1) in magnitude and its rounding
+// below 1.2e-7, 2.4e-7 or 4.8e-7 blocks.
 struct Origin {
     int nx, ny;
     float fx, fy;
@@ -1057,7 +1059,9 @@ __device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
 // warp whose blocks are all background writes zero bytes without the
 // per-pixel test.  Lanes past the frame's right edge but inside the last
 // mask word write zeros, so the padding bits are defined; rows past the
-// frame's bottom edge are not written.
+// frame's bottom edge are not written.  Blocks 1 and 2 (interleaved lanes)
+// run the per-pixel test and store whole words instead: ballots of the
+// lanes' pixels, lanes 0..7 writing the tile row's 8 words.
 // CHECK: every mask byte's row and column are checked (status: kStatusBounds).
 template <int B, int NW, int RPT, bool CHECK = false>
 __device__ __forceinline__ void tile_mask(const StreamArgs& a, const uint8_t* tile, int tx0,
