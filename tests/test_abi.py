@@ -111,3 +111,38 @@ def test_product_package_never_imports_oracle():
                     src = f.read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), fn
                 assert "dmsgm_oracle" not in src, fn
+
+
+def test_homography_defaults_and_validation(L):
+    """include/dmsgm_homog.h: the documented defaults, and every out-of-range
+    parameter, frame size or NULL handle refused with DMSGM_ERR_INVALID_ARG
+    before any device work (so on a machine without a GPU as well)."""
+    p = L.dmsgm_homog_default_params()
+    assert (p.block_size, p.max_corners, p.levels, p.win_half, p.max_iters, p.ransac_iters,
+            p.seed) == (3, 500, 5, 10, 30, 2000, 0)
+    assert (p.quality, p.min_distance, p.eps, p.min_eig, p.thresh) == (0.01, 10.0, 0.01, 1e-3, 3.0)
+    bad = [dict(block_size=2), dict(block_size=9), dict(quality=0.0), dict(quality=float("nan")),
+           dict(min_distance=-1.0), dict(min_distance=5000.0), dict(max_corners=0),
+           dict(max_corners=4097), dict(levels=-1), dict(levels=9), dict(win_half=0),
+           dict(win_half=16), dict(max_iters=0), dict(eps=-1.0), dict(min_eig=float("inf")),
+           dict(ransac_iters=0), dict(ransac_iters=65537), dict(thresh=0.0)]
+    for kw in bad:
+        q = L.dmsgm_homog_default_params()
+        for k, v in kw.items():
+            setattr(q, k, v)
+        with pytest.raises(L.DmsgmError) as e:
+            L.dmsgm_homog_create(640, 480, q)
+        assert e.value.code == L.DMSGM_ERR_INVALID_ARG, kw
+    for W, H in ((8, 480), (640, 8), (632, 480), (16400, 480), (640, 16400)):
+        with pytest.raises(L.DmsgmError) as e:
+            L.dmsgm_homog_create(W, H)
+        assert e.value.code == L.DMSGM_ERR_INVALID_ARG, (W, H)
+    calls = [lambda: L.dmsgm_homog_estimate(None, 0, 0),
+             lambda: L.dmsgm_homog_corners(None, 0, 8),
+             lambda: L.dmsgm_homog_track(None, 0, 0, [[1.0, 2.0]]),
+             lambda: L.dmsgm_homog_ransac(None, [[0.0, 0.0]], [[0.0, 0.0]])]
+    for call in calls:
+        with pytest.raises(L.DmsgmError) as e:
+            call()
+        assert e.value.code == L.DMSGM_ERR_INVALID_ARG
+    L.dmsgm_homog_destroy(None)
