@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DMSGM Mpix/s & %HBM peak (1080p, 4K); batched vs plain Mpix/s; p99 frame ms"
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the roofline's own peak is the measured copy rate)
 UNIT = "Mpix/s"
 
 
@@ -301,6 +302,8 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "nominal_gbs": NOMINAL_HBM_GBS,
+                         "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                          "bytes_per_launch": int(per_launch_bytes),
                          "bytes_per_pixel": bpp, "avg_launch_us": round(avg_launch_s * 1e6, 3),
                          "traffic": traffic, "kernel": "dmsgm_step_kernel"},
