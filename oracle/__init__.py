@@ -11,10 +11,14 @@ from .oracle import (  # noqa: F401
     HOMOG_DEFAULTS,
     corners,
     estimate_homography,
+    hypothesis,
+    inliers,
     pyr_down,
     ransac,
+    ransac_counts,
     sample4,
     score_map,
+    tensor_map,
     set_threads,
     splitmix64,
     track,

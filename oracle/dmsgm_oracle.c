@@ -438,19 +438,17 @@ int oracle_median3(int W, int H, const unsigned char* in, unsigned char* out)
     if (W <= 0 || H <= 0) return -1;
     for (int r = 0; r < H; ++r)
         for (int c = 0; c < W; ++c) {
-            unsigned char w[9];
-            int k = 0;
+            /* P4 (Sec. 2.1): the median of the 9 clamped neighbours is the
+             * intensity v of rank 5, i.e. the smallest v with at least 5 of
+             * the 9 values <= v.  Count the 9 values per intensity, then
+             * accumulate the counts upwards until they reach 5. */
+            int count[256] = {0};
             for (int i = -1; i <= 1; ++i)
                 for (int j = -1; j <= 1; ++j)
-                    w[k++] = in[(size_t)clampi(r + i, 0, H - 1) * W + clampi(c + j, 0, W - 1)];
-            /* insertion sort, then the middle element */
-            for (int a = 1; a < 9; ++a) {
-                unsigned char v = w[a];
-                int b = a - 1;
-                while (b >= 0 && w[b] > v) { w[b + 1] = w[b]; --b; }
-                w[b + 1] = v;
-            }
-            out[(size_t)r * W + c] = w[4];
+                    ++count[in[(size_t)clampi(r + i, 0, H - 1) * W + clampi(c + j, 0, W - 1)]];
+            int v = 0, le = count[0];
+            while (le < 5) le += count[++v];
+            out[(size_t)r * W + c] = (unsigned char)v;
         }
     return 0;
 }

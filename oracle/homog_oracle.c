@@ -15,14 +15,14 @@
  *
  * Readings (each listed in the design notes):
  *   M1 corner score: Shi-Tomasi's smaller eigenvalue of the structure tensor
- *      summed over a bs x bs window of 3 x 3 Sobel gradients (integers),
- *      coordinates clamped to the frame.  The score decides a discrete
- *      selection, so it is evaluated in FP32 in one fixed order of IEEE
- *      operations (the GPU's precision), and clamped to >= 0:
- *        s = max(0, 0.5 * ((A + C) - sqrt((A - C)^2 + 4 B^2))).
+ *      [A B; B C] summed over a bs x bs window of 3 x 3 Sobel gradients
+ *      (integers, so A, B, C are exact), coordinates clamped to the frame.
+ *      The eigenvalues of a symmetric 2 x 2 matrix are
+ *      ((A + C) -+ sqrt((A - C)^2 + 4 B^2)) / 2; the score is the smaller
+ *      one, evaluated in FP64 and clamped to >= 0 (the tensor is positive
+ *      semi-definite; rounding can only push the value below 0).
  *   M2 candidates: pixels with 1 <= x <= W-2, 1 <= y <= H-2, s > q * max s
- *      (max over all pixels, product in FP32) and s >= each of the 8
- *      neighbours' scores.
+ *      (max over all pixels) and s >= each of the 8 neighbours' scores.
  *   M3 order: score descending, then row-major index ascending; at most the
  *      first 8192 candidates in that order are considered.
  *   M4 greedy spacing: a candidate is accepted when every accepted corner
@@ -48,14 +48,16 @@
  *      x' = (x - W/2) * 2/max(W,H), by Gaussian elimination with partial
  *      pivoting (a pivot below 1e-12 rejects the hypothesis).  A pair is an
  *      inlier when it projects in front (w > 0) with reprojection error below
- *      thr, evaluated without a division: |(X, Y) - w dst|^2 < thr^2 w^2.
+ *      thr: with (X, Y, w) = Hp (x, y, 1), the pair is an inlier when
+ *      w > 0 and (X / w - dx)^2 + (Y / w - dy)^2 < thr^2.
  *      Best model: most inliers, ties to the lower index.  All of this in
- *      FP64, no contraction: the GPU evaluates the same operations.
+ *      FP64.
  *   M8 refit: least squares of the same DLT equations over the best model's
  *      inliers (normal equations, same elimination); the result has
  *      h33 = 1.
  *
- * Build: part of liboracle.so (gcc -O2 -std=c11 -ffp-contract=off).
+ * Build: part of liboracle.so (gcc -O2 -std=c11 -ffp-contract=off: no fused
+ * multiply-add, so x86 and Arm hosts compute the same FP64 values).
  */
 #include <math.h>
 #include <stddef.h>
@@ -69,8 +71,11 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 
 /* ---------------------------------------------------------------- corners */
 
-/* M1: the FP32 score of every pixel. */
-void ho_score_map(const uint8_t* img, int W, int H, int bs, float* score) {
+/* M1: the structure tensor of every pixel: A = sum gx^2, B = sum gx gy,
+ * C = sum gy^2 over the bs x bs window (exact integers, returned as
+ * doubles; any of the outputs may be NULL). */
+void ho_tensor_map(const uint8_t* img, int W, int H, int bs, double* outA, double* outB,
+                   double* outC) {
     int* gx = (int*)malloc(sizeof(int) * (size_t)W * H);
     int* gy = (int*)malloc(sizeof(int) * (size_t)W * H);
 #define P(xx, yy) ((int)img[(size_t)clampi(yy, 0, H - 1) * W + clampi(xx, 0, W - 1)])
@@ -93,22 +98,33 @@ void ho_score_map(const uint8_t* img, int W, int H, int bs, float* score) {
                     B += (long long)gx[k] * gy[k];
                     C += (long long)gy[k] * gy[k];
                 }
-            const float fa = (float)A, fb = (float)B, fc = (float)C;
-            const float t = fa + fc;
-            const float d = fa - fc;
-            const float e = d * d;
-            const float f = fb * fb;
-            const float g = 4.0f * f;
-            const float rr = sqrtf(e + g);
-            const float s = 0.5f * (t - rr);
-            score[(size_t)y * W + x] = s > 0.0f ? s : 0.0f;
+            const size_t o = (size_t)y * W + x;
+            if (outA) outA[o] = (double)A;
+            if (outB) outB[o] = (double)B;
+            if (outC) outC[o] = (double)C;
         }
     free(gx);
     free(gy);
 }
 
+/* M1: the score of every pixel, the smaller eigenvalue of its tensor. */
+void ho_score_map(const uint8_t* img, int W, int H, int bs, double* score) {
+    const size_t n = (size_t)W * H;
+    double* A = (double*)malloc(sizeof(double) * n);
+    double* B = (double*)malloc(sizeof(double) * n);
+    double* C = (double*)malloc(sizeof(double) * n);
+    ho_tensor_map(img, W, H, bs, A, B, C);
+    for (size_t k = 0; k < n; ++k) {
+        const double lmin = ((A[k] + C[k]) - sqrt((A[k] - C[k]) * (A[k] - C[k]) + 4.0 * B[k] * B[k])) / 2.0;
+        score[k] = lmin > 0.0 ? lmin : 0.0;
+    }
+    free(A);
+    free(B);
+    free(C);
+}
+
 typedef struct {
-    float s;
+    double s;
     int idx;
 } Cand;
 
@@ -122,18 +138,18 @@ static int cand_cmp(const void* a, const void* b) {
 /* M2-M4: the corners (pixel indices), strongest first.  Returns their
  * number; *n_cand receives the number of candidates (before the cap). */
 int ho_corners(const uint8_t* img, int W, int H, int bs, double quality, double min_dist,
-               int max_corners, int* xy, float* sc, int* n_cand) {
+               int max_corners, int* xy, double* sc, int* n_cand) {
     if (W < 3 || H < 3 || bs < 1 || bs % 2 == 0 || max_corners < 1) return -1;
-    float* s = (float*)malloc(sizeof(float) * (size_t)W * H);
+    double* s = (double*)malloc(sizeof(double) * (size_t)W * H);
     ho_score_map(img, W, H, bs, s);
-    float mx = 0.0f;
+    double mx = 0.0;
     for (size_t k = 0; k < (size_t)W * H; ++k) mx = s[k] > mx ? s[k] : mx;
-    const float thr = (float)quality * mx;
+    const double thr = quality * mx;
     size_t cap = 1024, n = 0;
     Cand* c = (Cand*)malloc(sizeof(Cand) * cap);
     for (int y = 1; y <= H - 2; ++y)
         for (int x = 1; x <= W - 2; ++x) {
-            const float v = s[(size_t)y * W + x];
+            const double v = s[(size_t)y * W + x];
             if (!(v > thr)) continue;
             int peak = 1;
             for (int j = -1; j <= 1 && peak; ++j)
@@ -403,16 +419,80 @@ static int model4(const double* src, const double* dst, const int* idx, Norm t, 
     return 0;
 }
 
-/* pair k is an inlier of Hp (M7): it projects in front (Z > 0) and within
- * thr of its partner, |(X, Y) - Z dst|^2 < thr^2 Z^2 */
-static int inlier(const double* Hp, const double* src, const double* dst, int k, double t2) {
+/* pair k is an inlier of Hp (M7): it projects in front (w > 0) and its
+ * reprojection lands within thr of its partner,
+ * (X / w - dx)^2 + (Y / w - dy)^2 < thr^2 */
+static double reproj_err2(const double* Hp, const double* src, const double* dst, int k, int* front) {
     const double x = src[2 * k], y = src[2 * k + 1];
     const double X = Hp[0] * x + Hp[1] * y + Hp[2];
     const double Y = Hp[3] * x + Hp[4] * y + Hp[5];
-    const double Z = Hp[6] * x + Hp[7] * y + Hp[8];
-    if (!(Z > 0.0)) return 0;
-    const double ex = X - dst[2 * k] * Z, ey = Y - dst[2 * k + 1] * Z;
-    return ex * ex + ey * ey < t2 * Z * Z;
+    const double w = Hp[6] * x + Hp[7] * y + Hp[8];
+    *front = w > 0.0;
+    if (!*front) return 0.0;
+    const double ex = X / w - dst[2 * k], ey = Y / w - dst[2 * k + 1];
+    return ex * ex + ey * ey;
+}
+
+static int inlier(const double* Hp, const double* src, const double* dst, int k, double t2) {
+    int front;
+    const double e2 = reproj_err2(Hp, src, dst, k, &front);
+    return front && e2 < t2;
+}
+
+/* The inlier decisions of model Hp (M7) over n pairs: inl[k] = 1 for an
+ * inlier; near[k] = 1 when the pair is in front of the model and its squared
+ * reprojection error lies within band * thr^2 of thr^2 (either may be NULL).
+ * Returns the inlier count. */
+int ho_inliers(const double* Hp, const double* src, const double* dst, int n, double thr,
+               double band, uint8_t* inl, uint8_t* near) {
+    const double t2 = thr * thr;
+    int cnt = 0;
+    for (int k = 0; k < n; ++k) {
+        int front;
+        const double e2 = reproj_err2(Hp, src, dst, k, &front);
+        const int in = front && e2 < t2;
+        cnt += in;
+        if (inl) inl[k] = (uint8_t)in;
+        if (near) near[k] = (uint8_t)(front && fabs(e2 - t2) <= band * t2);
+    }
+    return cnt;
+}
+
+/* The model of hypothesis m over the pairs src -> dst (M7): 0, or -1 when
+ * its sample or its DLT system gives none. */
+int ho_hypothesis(const double* src, const double* dst, int n, int W, int H, uint64_t seed, int m,
+                  double* Hp) {
+    if (n < 4 || m < 0) return -1;
+    int idx[4];
+    if (ho_sample4(seed, m, n, idx)) return -1;
+    return model4(src, dst, idx, norm_of(W, H), Hp);
+}
+
+/* Per hypothesis m < iters: counts[m] = its inlier count (-1: no model) and
+ * near[m] = how many of the pairs in front of it have a squared
+ * reprojection error within band * thr^2 of thr^2 (the decisions that a
+ * computation rounding differently may take the other way). */
+int ho_ransac_counts(const double* src, const double* dst, int n, int W, int H, int iters,
+                     double thr, uint64_t seed, double band, int* counts, int* near) {
+    if (n < 4 || iters < 1) return -1;
+    const double t2 = thr * thr;
+    for (int m = 0; m < iters; ++m) {
+        double Hp[9];
+        counts[m] = -1;
+        near[m] = 0;
+        if (ho_hypothesis(src, dst, n, W, H, seed, m, Hp)) continue;
+        int cnt = 0, nb = 0;
+        for (int k = 0; k < n; ++k) {
+            int front;
+            const double e2 = reproj_err2(Hp, src, dst, k, &front);
+            if (!front) continue;
+            cnt += e2 < t2;
+            nb += fabs(e2 - t2) <= band * t2;
+        }
+        counts[m] = cnt;
+        near[m] = nb;
+    }
+    return 0;
 }
 
 /* M7-M8: the homography src -> dst (both n x 2, pixel coordinates of a W x H
@@ -426,9 +506,8 @@ int ho_ransac(const double* src, const double* dst, int n, int W, int H, int ite
     int bestc = -1, bm = -1;
     double Hb[9];
     for (int m = 0; m < iters; ++m) {
-        int idx[4];
         double Hp[9];
-        if (ho_sample4(seed, m, n, idx) || model4(src, dst, idx, t, Hp)) continue;
+        if (ho_hypothesis(src, dst, n, W, H, seed, m, Hp)) continue;
         int cnt = 0;
         for (int k = 0; k < n; ++k) cnt += inlier(Hp, src, dst, k, t2);
         if (cnt > bestc) {
@@ -467,7 +546,7 @@ int ho_estimate(const uint8_t* prev, const uint8_t* cur, int W, int H, int bs, d
                 double min_eig, int iters, double thr, uint64_t seed, double* Hout,
                 int* n_corners, int* n_tracked) {
     int* xy = (int*)malloc(sizeof(int) * 2 * (size_t)max_corners);
-    float* sc = (float*)malloc(sizeof(float) * (size_t)max_corners);
+    double* sc = (double*)malloc(sizeof(double) * (size_t)max_corners);
     int ncand = 0;
     const int m = ho_corners(prev, W, H, bs, quality, min_dist, max_corners, xy, sc, &ncand);
     *n_corners = m < 0 ? 0 : m;

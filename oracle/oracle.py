@@ -207,6 +207,8 @@ def prefilter(frame: np.ndarray, *, gauss_size: int = 5, sigma: float = 1.0,
 
 def _homog_sigs(lib):
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ho_tensor_map.restype = None
+    lib.ho_tensor_map.argtypes = [P, I, I, I, P, P, P]
     lib.ho_score_map.restype = None
     lib.ho_score_map.argtypes = [P, I, I, I, P]
     lib.ho_corners.restype = I
@@ -221,6 +223,12 @@ def _homog_sigs(lib):
     lib.ho_sample4.argtypes = [ctypes.c_uint64, I, I, P]
     lib.ho_ransac.restype = I
     lib.ho_ransac.argtypes = [P, P, I, I, I, I, D, ctypes.c_uint64, P, P, P]
+    lib.ho_hypothesis.restype = I
+    lib.ho_hypothesis.argtypes = [P, P, I, I, I, ctypes.c_uint64, I, P]
+    lib.ho_inliers.restype = I
+    lib.ho_inliers.argtypes = [P, P, P, I, D, D, P, P]
+    lib.ho_ransac_counts.restype = I
+    lib.ho_ransac_counts.argtypes = [P, P, I, I, I, I, D, ctypes.c_uint64, D, P, P]
     lib.ho_estimate.restype = I
     lib.ho_estimate.argtypes = [P, P, I, I, I, D, D, I, I, I, I, D, D, I, D, ctypes.c_uint64,
                                 P, P, P]
@@ -246,12 +254,23 @@ HOMOG_DEFAULTS = dict(block_size=3, quality=0.01, min_distance=10.0, max_corners
                       thresh=3.0, seed=0)
 
 
-def score_map(img: np.ndarray, block_size: int = 3) -> np.ndarray:
-    """M1: the FP32 Shi-Tomasi score of every pixel."""
+def tensor_map(img: np.ndarray, block_size: int = 3):
+    """M1: the structure tensor (A, B, C) of every pixel, exact integers as
+    float64 arrays."""
     lib = _hlib()
     img = np.ascontiguousarray(img, dtype=np.uint8)
     h, w = img.shape
-    out = np.empty((h, w), dtype=np.float32)
+    A, B, C = (np.empty((h, w), dtype=np.float64) for _ in range(3))
+    lib.ho_tensor_map(_ptr(img), w, h, int(block_size), _ptr(A), _ptr(B), _ptr(C))
+    return A, B, C
+
+
+def score_map(img: np.ndarray, block_size: int = 3) -> np.ndarray:
+    """M1: the FP64 Shi-Tomasi score (smaller tensor eigenvalue) of every pixel."""
+    lib = _hlib()
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    h, w = img.shape
+    out = np.empty((h, w), dtype=np.float64)
     lib.ho_score_map(_ptr(img), w, h, int(block_size), _ptr(out))
     return out
 
@@ -264,7 +283,7 @@ def corners(img: np.ndarray, block_size: int = 3, quality: float = 0.01,
     img = np.ascontiguousarray(img, dtype=np.uint8)
     h, w = img.shape
     xy = np.zeros((max_corners, 2), dtype=np.int32)
-    sc = np.zeros(max_corners, dtype=np.float32)
+    sc = np.zeros(max_corners, dtype=np.float64)
     nc = ctypes.c_int(0)
     m = lib.ho_corners(_ptr(img), w, h, int(block_size), float(quality), float(min_distance),
                        int(max_corners), _ptr(xy), _ptr(sc), ctypes.byref(nc))
@@ -327,6 +346,47 @@ def ransac(src: np.ndarray, dst: np.ndarray, width: int, height: int, iters: int
     if cnt < 0:
         return None, inl[:n], 0, -1
     return Hm.reshape(3, 3), inl[:n].astype(bool), cnt, best.value
+
+
+def hypothesis(src: np.ndarray, dst: np.ndarray, width: int, height: int, seed: int, m: int):
+    """M7: the model (3x3) of hypothesis m over the pairs src -> dst, or None."""
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    dst = np.ascontiguousarray(dst, dtype=np.float64).reshape(-1, 2)
+    Hm = np.zeros(9)
+    rc = _hlib().ho_hypothesis(_ptr(src), _ptr(dst), len(src), int(width), int(height),
+                               ctypes.c_uint64(seed), int(m), _ptr(Hm))
+    return None if rc else Hm.reshape(3, 3)
+
+
+def inliers(Hm: np.ndarray, src: np.ndarray, dst: np.ndarray, thresh: float, band: float = 1e-6):
+    """M7: the inlier mask of model Hm over the pairs src -> dst, and the mask
+    of pairs whose squared reprojection error lies within band * thresh^2 of
+    thresh^2."""
+    Hm = np.ascontiguousarray(Hm, dtype=np.float64).reshape(9)
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    dst = np.ascontiguousarray(dst, dtype=np.float64).reshape(-1, 2)
+    n = len(src)
+    inl = np.zeros(max(n, 1), dtype=np.uint8)
+    near = np.zeros(max(n, 1), dtype=np.uint8)
+    _hlib().ho_inliers(_ptr(Hm), _ptr(src), _ptr(dst), n, float(thresh), float(band), _ptr(inl),
+                       _ptr(near))
+    return inl[:n].astype(bool), near[:n].astype(bool)
+
+
+def ransac_counts(src: np.ndarray, dst: np.ndarray, width: int, height: int, iters: int = 2000,
+                  thresh: float = 3.0, seed: int = 0, band: float = 1e-6):
+    """M7: per hypothesis its inlier count (-1: no model) and the number of
+    pairs whose squared reprojection error lies within band * thresh^2 of
+    thresh^2."""
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    dst = np.ascontiguousarray(dst, dtype=np.float64).reshape(-1, 2)
+    counts = np.zeros(iters, dtype=np.int32)
+    near = np.zeros(iters, dtype=np.int32)
+    if _hlib().ho_ransac_counts(_ptr(src), _ptr(dst), len(src), int(width), int(height),
+                                int(iters), float(thresh), ctypes.c_uint64(seed), float(band),
+                                _ptr(counts), _ptr(near)):
+        raise ValueError("invalid RANSAC arguments")
+    return counts, near
 
 
 def estimate_homography(prev: np.ndarray, cur: np.ndarray, **kw):

@@ -27,8 +27,9 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 
 
 # Per-unit flags: the RANSAC unit evaluates FP64 expressions exactly as
-# written (no fused multiply-add), so its inlier counts equal the reference
-# evaluation of the same operations.
+# written (no fused multiply-add), so its models and inlier counts are the
+# values of the written operations, reproducible by any IEEE evaluation of
+# the same expressions.
 UNIT_FLAGS = {"dmsgm_homog_ransac.cu": ["-fmad=false"]}
 
 

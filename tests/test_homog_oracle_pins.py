@@ -51,6 +51,42 @@ def test_score_of_a_corner_exceeds_its_edges():
     assert s[25, 15] == 0 and s[15, 25] == 0
 
 
+def _sobel_tensor_bruteforce(img, bs):
+    """Structure tensor by explicit edge-padded Sobel filtering and window
+    sums (numpy, independent of the oracle's loops)."""
+    p = np.pad(img.astype(np.int64), 1, mode="edge")
+    h, w = img.shape
+    sh = lambda dy, dx: p[1 + dy:1 + dy + h, 1 + dx:1 + dx + w]  # noqa: E731
+    gx = (sh(-1, 1) + 2 * sh(0, 1) + sh(1, 1)) - (sh(-1, -1) + 2 * sh(0, -1) + sh(1, -1))
+    gy = (sh(1, -1) + 2 * sh(1, 0) + sh(1, 1)) - (sh(-1, -1) + 2 * sh(-1, 0) + sh(-1, 1))
+    r = bs // 2
+    out = []
+    for q in (gx * gx, gx * gy, gy * gy):
+        qp = np.pad(q, r, mode="edge")
+        acc = np.zeros_like(q)
+        for j in range(bs):
+            for i in range(bs):
+                acc += qp[j:j + h, i:i + w]
+        out.append(acc.astype(np.float64))
+    return out
+
+
+@pytest.mark.parametrize("bs", [1, 3, 5, 7])
+def test_tensor_and_score_are_the_smaller_eigenvalue(bs):
+    """M1: A, B, C equal an independent edge-padded Sobel filtering and window
+    sum, and the score is the smaller eigenvalue of [A B; B C] as LAPACK's
+    symmetric eigen-solver gives it (clamped at 0)."""
+    rng = np.random.default_rng(bs)
+    img = rng.integers(0, 256, (23, 31)).astype(np.uint8)
+    A, B, C = oracle.tensor_map(img, bs)
+    bA, bB, bC = _sobel_tensor_bruteforce(img, bs)
+    assert np.array_equal(A, bA) and np.array_equal(B, bB) and np.array_equal(C, bC)
+    ev = np.linalg.eigvalsh(np.stack([np.stack([A, B], -1), np.stack([B, C], -1)], -2))[..., 0]
+    s = oracle.score_map(img, bs)
+    assert np.all(s >= 0)
+    assert np.allclose(s, np.maximum(ev, 0), rtol=0, atol=1e-9 * (A + C).max())
+
+
 # ------------------------------------------------------------- M2-M4 corners
 def _squares(h, w, boxes):
     img = np.full((h, w), 30, np.uint8)
@@ -166,6 +202,40 @@ def test_ransac_recovers_an_exact_homography_among_outliers():
     assert cnt == (~out).sum()
     assert np.array_equal(inl, ~out)
     assert np.abs(Hm - H).max() < 1e-9 * np.abs(H).max()
+
+
+def test_inlier_test_is_the_reprojection_distance():
+    """M7: pairs placed at known reprojection distances r from the exact
+    model: inliers are exactly those with r < thr; a model that sends a
+    point behind the camera (w <= 0) never counts it; the band marks the
+    pairs whose r^2 is within band * thr^2 of thr^2."""
+    rng = np.random.default_rng(4)
+    H = np.array([[1.02, 0.01, -3.0], [-0.015, 0.98, 2.5], [1e-5, 2e-5, 1.0]])
+    src = rng.uniform(0, 1, (400, 2)) * [640, 480]
+    r = rng.choice([0.0, 0.5, 0.99, 1.01, 2.0, 5.0], 400)
+    ang = rng.uniform(0, 2 * np.pi, 400)
+    dst = _apply(H, src) + r[:, None] * np.c_[np.cos(ang), np.sin(ang)]
+    inl, near = oracle.inliers(H, src, dst, 1.0, band=0.05)
+    assert np.array_equal(inl, r < 1.0)
+    assert np.array_equal(near, np.abs(r * r - 1.0) <= 0.05 + 1e-12)
+    behind = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, -1.0]])
+    inl, _ = oracle.inliers(behind, src, -src, 1.0)
+    assert not inl.any()
+    counts, nearc = oracle.ransac_counts(src, dst, 640, 480, iters=50, thresh=1.0, seed=2)
+    Hm = oracle.hypothesis(src, dst, 640, 480, 2, int(np.argmax(counts)))
+    assert counts.max() == oracle.inliers(Hm, src, dst, 1.0)[0].sum()
+
+
+def test_hypothesis_of_exact_pairs_is_the_model():
+    """M7: any 4 distinct pairs of an exact homography in general position
+    give back that homography (h33 = 1)."""
+    rng = np.random.default_rng(8)
+    H = np.array([[0.99, -0.03, 7.0], [0.02, 1.01, -4.0], [-2e-5, 1e-5, 1.0]])
+    src = rng.uniform(0, 1, (30, 2)) * [320, 240]
+    dst = _apply(H, src)
+    for m in range(10):
+        Hm = oracle.hypothesis(src, dst, 320, 240, 5, m)
+        assert Hm is not None and np.abs(Hm - H).max() < 1e-9
 
 
 def test_ransac_four_points_and_degenerate_data():
