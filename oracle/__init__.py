@@ -16,6 +16,7 @@ from .oracle import (  # noqa: F401
     pyr_down,
     ransac,
     ransac_counts,
+    refit,
     sample4,
     score_map,
     tensor_map,

@@ -495,6 +495,30 @@ int ho_ransac_counts(const double* src, const double* dst, int n, int W, int H, 
     return 0;
 }
 
+/* M8: the least-squares fit of the DLT equations of the pairs with inl[k]
+ * set (normal equations, the same elimination); 0, or -1 when fewer than 4
+ * pairs are marked or the system is singular. */
+int ho_refit(const double* src, const double* dst, const uint8_t* inl, int n, int W, int H,
+             double* Hout) {
+    const Norm t = norm_of(W, H);
+    double N[64] = {0}, r[8] = {0}, h[8];
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!inl[k]) continue;
+        ++m;
+        double r0[8], r1[8], b[2];
+        dlt_rows((src[2 * k] - t.ox) * t.s, (src[2 * k + 1] - t.oy) * t.s,
+                 (dst[2 * k] - t.ox) * t.s, (dst[2 * k + 1] - t.oy) * t.s, r0, r1, b);
+        for (int i = 0; i < 8; ++i) {
+            for (int j = 0; j < 8; ++j) N[i * 8 + j] += r0[i] * r0[j] + r1[i] * r1[j];
+            r[i] += r0[i] * b[0] + r1[i] * b[1];
+        }
+    }
+    if (m < 4 || solve(N, r, 8, h)) return -1;
+    denorm(h, t, Hout);
+    return 0;
+}
+
 /* M7-M8: the homography src -> dst (both n x 2, pixel coordinates of a W x H
  * frame).  Returns the inlier count of the best hypothesis (inl[k] = 1 for
  * its inliers) or -1 when no hypothesis gives a model; *best = its index. */
@@ -519,23 +543,8 @@ int ho_ransac(const double* src, const double* dst, int n, int W, int H, int ite
     if (bm < 0) return -1;
     *best = bm;
     for (int k = 0; k < n; ++k) inl[k] = (uint8_t)inlier(Hb, src, dst, k, t2);
-    /* M8: normal equations over the inliers */
-    double N[64] = {0}, r[8] = {0}, h[8];
-    for (int k = 0; k < n; ++k) {
-        if (!inl[k]) continue;
-        double r0[8], r1[8], b[2];
-        dlt_rows((src[2 * k] - t.ox) * t.s, (src[2 * k + 1] - t.oy) * t.s,
-                 (dst[2 * k] - t.ox) * t.s, (dst[2 * k + 1] - t.oy) * t.s, r0, r1, b);
-        for (int i = 0; i < 8; ++i) {
-            for (int j = 0; j < 8; ++j) N[i * 8 + j] += r0[i] * r0[j] + r1[i] * r1[j];
-            r[i] += r0[i] * b[0] + r1[i] * b[1];
-        }
-    }
-    if (bestc >= 4 && solve(N, r, 8, h) == 0) {
-        denorm(h, t, Hout);
-    } else {
-        memcpy(Hout, Hb, sizeof Hb);
-    }
+    /* M8: the least-squares refit over the inliers */
+    if (bestc < 4 || ho_refit(src, dst, inl, n, W, H, Hout)) memcpy(Hout, Hb, sizeof Hb);
     return bestc;
 }
 

@@ -225,6 +225,8 @@ def _homog_sigs(lib):
     lib.ho_ransac.argtypes = [P, P, I, I, I, I, D, ctypes.c_uint64, P, P, P]
     lib.ho_hypothesis.restype = I
     lib.ho_hypothesis.argtypes = [P, P, I, I, I, ctypes.c_uint64, I, P]
+    lib.ho_refit.restype = I
+    lib.ho_refit.argtypes = [P, P, P, I, I, I, P]
     lib.ho_inliers.restype = I
     lib.ho_inliers.argtypes = [P, P, P, I, D, D, P, P]
     lib.ho_ransac_counts.restype = I
@@ -371,6 +373,17 @@ def inliers(Hm: np.ndarray, src: np.ndarray, dst: np.ndarray, thresh: float, ban
     _hlib().ho_inliers(_ptr(Hm), _ptr(src), _ptr(dst), n, float(thresh), float(band), _ptr(inl),
                        _ptr(near))
     return inl[:n].astype(bool), near[:n].astype(bool)
+
+
+def refit(src: np.ndarray, dst: np.ndarray, inl: np.ndarray, width: int, height: int):
+    """M8: the least-squares homography of the marked pairs, or None."""
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    dst = np.ascontiguousarray(dst, dtype=np.float64).reshape(-1, 2)
+    m = np.ascontiguousarray(inl, dtype=np.uint8).reshape(-1)
+    Hm = np.zeros(9)
+    rc = _hlib().ho_refit(_ptr(src), _ptr(dst), _ptr(m), len(src), int(width), int(height),
+                          _ptr(Hm))
+    return None if rc else Hm.reshape(3, 3)
 
 
 def ransac_counts(src: np.ndarray, dst: np.ndarray, width: int, height: int, iters: int = 2000,

@@ -272,33 +272,6 @@ static SeqShape pick_shape(const dmsgm_ctx* h, int sms) {
     return best;
 }
 
-// Largest block-unit displacement (|ex|, |ey|) of any block under H, or
-// false if some block has no well-defined projection (then every tile is a
-// neighbour).  Affine maps reach their extremes at the grid corners; for a
-// projective H a 17 x 17 sample of block centres is taken with a margin.
-static bool max_displacement(const double* m, int W, int H, int B, double& ex, double& ey) {
-    const bool affine = m[6] == 0.0 && m[7] == 0.0;
-    const int n = affine ? 2 : 17;
-    ex = ey = 0.0;
-    for (int iy = 0; iy < n; ++iy)
-        for (int ix = 0; ix < n; ++ix) {
-            const double cx = (0.5 + (W / B - 1) * double(ix) / (n - 1)) * B;
-            const double cy = (0.5 + (H / B - 1) * double(iy) / (n - 1)) * B;
-            const double Z = m[6] * cx + m[7] * cy + m[8];
-            if (!(Z > 0.0)) return false;
-            const double px = (m[0] * cx + m[1] * cy + m[2]) / Z;
-            const double py = (m[3] * cx + m[4] * cy + m[5]) / Z;
-            if (!std::isfinite(px) || !std::isfinite(py)) return false;
-            ex = std::max(ex, std::fabs(px - cx) / B);
-            ey = std::max(ey, std::fabs(py - cy) / B);
-        }
-    if (!affine) {
-        ex = ex * 1.25 + 1.0;
-        ey = ey * 1.25 + 1.0;
-    }
-    return true;
-}
-
 static int seq_map(dmsgm_ctx* h, const uint8_t* frames, int T, int rows, CUtensorMap* out) {
     auto enc = encode_fn();
     if (!enc) return fail(DMSGM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
@@ -339,14 +312,16 @@ int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* Hs,
         bool bounded = true;
         for (int k = 0; k < n && bounded; ++k) {
             double fx, fy;
-            if (!max_displacement(Hs + 9 * size_t(c0 + k), h->W, h->H, h->B, fx, fy)) bounded = false;
+            if (!displacement_bound(Hs + 9 * size_t(c0 + k), h->W, h->H, h->B, &fx, &fy)) bounded = false;
             ex = std::max(ex, fx);
             ey = std::max(ey, fy);
         }
         int rx = tiles_x, ry = tiles_y;
         if (bounded) {
-            rx = std::min<double>(tiles_x, std::ceil((ex + 1.0) / (kTileW / h->B)));
-            ry = std::min<double>(tiles_y, std::ceil((ey + 1.0) / (th / h->B)));
+            // a source block lies within ceil(|e|) + 1 blocks, one more for
+            // the kernel's FP32 rounding of the floor
+            rx = std::min<double>(tiles_x, std::ceil((std::ceil(ex) + 2.0) / (kTileW / h->B)));
+            ry = std::min<double>(tiles_y, std::ceil((std::ceil(ey) + 2.0) / (th / h->B)));
         }
         for (int k = 0; k < n; ++k) {
             int affine = 0;
@@ -391,6 +366,7 @@ int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* Hs,
             return fail(DMSGM_ERR_CUDA, "multi-frame kernel launch failed: %s", cudaGetErrorString(e));
         h->parity = (h->parity + n) & 1;
         h->initialized = true;
+        h->last.step = false;
         h->frames += n;
     }
     return DMSGM_OK;
@@ -409,24 +385,57 @@ namespace dmsgm {
 constexpr int kNoAllocCounters = 4096;
 static __device__ __align__(256) int g_noalloc_counters[kNoAllocCounters];
 
-// Device address of the array on the current device.  Host code must not
-// hand the symbol itself to a kernel (on the host it only stands in for the
-// device object), so the address is looked up once per device, with that
-// device current, and cached.
-static int noalloc_counters(int device, int** out) {
-    static std::mutex mu;
-    static int* addr[64] = {nullptr};
-    std::lock_guard<std::mutex> g(mu);
-    if (device < 0 || device >= 64) return fail(DMSGM_ERR_UNSUPPORTED, "device %d out of range", device);
-    if (!addr[device]) {
+// Device address of the array in the current CUDA context.  Host code must
+// not hand the symbol itself to a kernel (on the host it only stands in for
+// the device object), and an address is valid only in the context where it
+// was looked up, so it is looked up once per context -- keyed by the
+// context's unique ID, which is never reused, not even after a device reset
+// -- with that context current, and cached.
+static int noalloc_counters(int** out) {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_counters);
-        if (e != cudaSuccess || !p)
-            return fail(DMSGM_ERR_CUDA, "cudaGetSymbolAddress of the counter array failed: %s",
-                        cudaGetErrorString(e));
-        addr[device] = static_cast<int*>(p);
-    }
-    *out = addr[device];
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+    });
+    // make the device's primary context current if no context is yet
+    DMSGM_CUDA_TRY(cudaFree(nullptr));
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return fail(DMSGM_ERR_CUDA, "cannot identify the current CUDA context");
+    struct Entry {
+        unsigned long long id;
+        int* addr;
+    };
+    static std::mutex mu;
+    static Entry cache[16] = {};
+    static int next = 0;
+    std::lock_guard<std::mutex> g(mu);
+    for (const Entry& e : cache)
+        if (e.addr && e.id == id) {
+            *out = e.addr;
+            return DMSGM_OK;
+        }
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_counters);
+    if (e != cudaSuccess || !p)
+        return fail(DMSGM_ERR_CUDA, "cudaGetSymbolAddress of the counter array failed: %s",
+                    cudaGetErrorString(e));
+    cache[next] = Entry{id, static_cast<int*>(p)};
+    next = (next + 1) % 16;
+    *out = static_cast<int*>(p);
     return DMSGM_OK;
 }
 
@@ -455,11 +464,20 @@ extern "C" int dmsgm_process_seq_noalloc(int W, int H, int B, int precision, flo
         return fail(DMSGM_ERR_INVALID_ARG, "frames must be 16-byte and masks 4-byte aligned");
     for (long i = 0; i < 9L * n; ++i)
         if (!std::isfinite(Hs[i])) return fail(DMSGM_ERR_INVALID_ARG, "homography %ld is not finite", i / 9);
+    if (!((B == 4 || B == 8) && H % B == 0))
+        return fail(DMSGM_ERR_UNSUPPORTED, "the multi-frame kernel takes blocks 4 and 8 on whole block rows");
+    {
+        // even the tallest tile (256 rows) needs more counters than the array holds
+        const long least = long((W + kTileW - 1) / kTileW) * ((H + 255) / 256);
+        if (least > kNoAllocCounters)
+            return fail(DMSGM_ERR_INVALID_ARG, "a %dx%d frame needs at least %ld progress counters, "
+                        "the array holds %d", W, H, least, kNoAllocCounters);
+    }
     if (n == 0) return DMSGM_OK;
     int dev = 0;
     DMSGM_CUDA_TRY(cudaGetDevice(&dev));
     int* counters = nullptr;
-    int rc = noalloc_counters(dev, &counters);
+    int rc = noalloc_counters(&counters);
     if (rc) return rc;
     // a handle description on the stack over the caller's memory
     dmsgm_ctx h{};
@@ -479,8 +497,6 @@ extern "C" int dmsgm_process_seq_noalloc(int W, int H, int B, int precision, flo
     // the counters this launch needs must fit the array
     int sms = 0;
     DMSGM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (!((B == 4 || B == 8) && H % B == 0))
-        return fail(DMSGM_ERR_UNSUPPORTED, "the multi-frame kernel takes blocks 4 and 8 on whole block rows");
     const SeqShape sh = pick_shape(&h, sms);
     if (!sh.nw)
         return fail(DMSGM_ERR_UNSUPPORTED, "the %dx%d frame's tiles cannot all be resident on this GPU", W, H);

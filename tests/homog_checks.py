@@ -256,8 +256,12 @@ def check_ransac(src, dst, W, H, iters, thr, seed, gH, ginl, gbest, gcount, corn
     assert not np.any(diff & ~bnear), "inlier decisions outside the band differ"
     corners = np.array([[0, 0], [W, 0], [0, H], [W, H]], float)
     q = lambda M, p: (np.c_[p, np.ones(len(p))] @ np.asarray(M).T)  # noqa: E731
-    a, b = q(gH, corners), q(oH, corners)
-    err = float(np.abs(a[:, :2] / a[:, 2:] - b[:, :2] / b[:, 2:]).max())
+    at = lambda M: (lambda v: v[:, :2] / v[:, 2:])(q(M, corners))  # noqa: E731
+    # the refit (M8) of the GPU's own inlier set, as the oracle computes it
+    Hr = oracle.refit(src, dst, np.asarray(ginl, bool), W, H) if gcount >= 4 else None
+    if Hr is not None:
+        assert float(np.abs(at(gH) - at(Hr)).max()) < 1e-6
+    err = float(np.abs(at(gH) - at(oH)).max())
     if gbest == obest and not diff.any():
         assert err < 1e-6, err                      # same inliers: the same least squares
     else:

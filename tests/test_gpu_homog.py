@@ -181,7 +181,12 @@ def test_ransac_counts_at_the_threshold(H):
         eb, ec, einl, _ = emu_ransac(src, d, 640, 480, 500, thr, 9)
         assert res.best == eb and res.inliers == ec
         assert np.array_equal(inlg, einl)
-        st = check_ransac(src, d, 640, 480, 500, thr, 9, Hg, inlg, res.best, res.inliers)
+        # half the pairs sit on the threshold: which of them count moves the
+        # refit by up to the threshold itself, so the estimates are compared
+        # there only within thr (the refit of the GPU's own inliers is
+        # compared to rounding)
+        st = check_ransac(src, d, 640, 480, 500, thr, 9, Hg, inlg, res.best, res.inliers,
+                          corner_tol=thr)
         assert st["near_pairs"] > 0
         est.close()
 

@@ -104,6 +104,6 @@ def test_pairs_on_the_threshold_pass_the_banded_check():
     r[rng.random(n) < 0.2] = 1.0
     d = dst + edge[:, None] * (r[:, None] * np.c_[np.cos(ang), np.sin(ang)])
     best, cnt, inl, _ = emu_ransac(src, d, 640, 480, 200, 1.0, 9)
-    Hm, _, _, _ = oracle.ransac(src, d, 640, 480, iters=200, thresh=1.0, seed=9)
-    st = check_ransac(src, d, 640, 480, 200, 1.0, 9, Hm, inl, best, cnt)
+    Hm = oracle.refit(src, d, inl, 640, 480)
+    st = check_ransac(src, d, 640, 480, 200, 1.0, 9, Hm, inl, best, cnt, corner_tol=1.0)
     assert st["near_pairs"] > 0

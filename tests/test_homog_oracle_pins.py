@@ -238,6 +238,32 @@ def test_hypothesis_of_exact_pairs_is_the_model():
         assert Hm is not None and np.abs(Hm - H).max() < 1e-9
 
 
+def test_refit_is_the_least_squares_of_the_marked_pairs():
+    """M8: exact pairs give back the homography; the RANSAC result is the
+    refit of its own inlier set; noisy pairs give the model whose normal
+    equations' residual vanishes (checked by an independent numpy lstsq of
+    the same normalised DLT rows)."""
+    rng = np.random.default_rng(13)
+    H = np.array([[1.01, 0.02, -5.0], [-0.01, 0.99, 3.0], [1e-5, -2e-5, 1.0]])
+    src = rng.uniform(0, 1, (200, 2)) * [640, 480]
+    dst = _apply(H, src)
+    assert np.abs(oracle.refit(src, dst, np.ones(200, bool), 640, 480) - H).max() < 1e-9
+    noisy = dst + rng.normal(0, 0.3, dst.shape)
+    Hr, inl, _, _ = oracle.ransac(src, noisy, 640, 480, iters=100, thresh=1.0, seed=1)
+    assert np.array_equal(Hr, oracle.refit(src, noisy, inl, 640, 480))
+    s, ox, oy = 2.0 / 640, 320.0, 240.0
+    x, y = (src[inl, 0] - ox) * s, (src[inl, 1] - oy) * s
+    X, Y = (noisy[inl, 0] - ox) * s, (noisy[inl, 1] - oy) * s
+    z, o = np.zeros_like(x), np.ones_like(x)
+    A = np.r_[np.c_[x, y, o, z, z, z, -x * X, -y * X], np.c_[z, z, z, x, y, o, -x * Y, -y * Y]]
+    h = np.linalg.lstsq(A, np.r_[X, Y], rcond=None)[0]
+    T = np.array([[s, 0, -s * ox], [0, s, -s * oy], [0, 0, 1.0]])
+    Hl = np.linalg.inv(T) @ np.r_[h, 1.0].reshape(3, 3) @ T
+    Hl /= Hl[2, 2]
+    assert np.abs(Hr - Hl).max() < 1e-9 * np.abs(Hl).max()
+    assert oracle.refit(src[:3], dst[:3], np.ones(3, bool), 640, 480) is None
+
+
 def test_ransac_four_points_and_degenerate_data():
     src = np.array([[10, 10], [300, 20], [290, 230], [15, 220]], float)
     dst = np.array([[12, 9], [305, 25], [280, 240], [20, 215]], float)
