@@ -338,6 +338,10 @@ def run_gpu(args):
             out["batched"] = run_batched(args, dev)
         if args.serve:
             out["serving"] = run_serving(args, dev)
+        if args.target:
+            # last in the line, so that a tail of the output keeps it
+            out["target_4k"] = run_target_4k(args, dev, stream, load_peaks()[0],
+                                             with_oracle=bool(args.cpu_baseline))
         print(json.dumps(out), flush=True)
     m.close()
     me.close()
@@ -372,8 +376,8 @@ def run_batched(args, dev):
     T = args.batch_frames
     out = {"streams": len(specs), "frames": T, "pixels_per_step": r.pixels_per_step}
     bytes_step = sum(bytes_per_pixel(b, "fp32") * w * h for (w, h, b) in specs)
-    for mode in ("batched", "plain"):
-        r.warm(mode, shape, stream)
+    for mode in ("batched", "plain", "plain_multi"):
+        r.warm("plain" if mode == "plain_multi" else mode, shape, stream)
         g = r.capture(mode, shape, steps=T, stream=stream)
         ms = time_graph(g, stream, reps=2)
         per_step = ms / T
@@ -383,10 +387,16 @@ def run_batched(args, dev):
                      "frac": round(bytes_step / (per_step / 1e3) / 1e9 / peak, 4),
                      "launches_per_step": 1 if mode == "batched" else len(specs)}
         del g
-    out["speedup_batched_vs_plain"] = round(out["batched"]["mpix_s"] / out["plain"]["mpix_s"], 3)
+    out["plain"]["note"] = "one CUDA stream, programmatic dependent launch"
+    out["plain_multi"]["note"] = "stream i on CUDA stream i % 8, forked and joined in the graph"
+    best_plain = max(out["plain"]["mpix_s"], out["plain_multi"]["mpix_s"])
+    out["speedup_batched_vs_plain"] = round(out["batched"]["mpix_s"] / best_plain, 3)
     out["bytes_per_step"] = int(bytes_step)
-    out["launch_shape"] = {"ctas": shape.ctas, "use_pdl": shape.use_pdl}
-    out["autotune"] = [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in t.items()}
+    one_per_item = shape.ctas >= (1 << 30)
+    out["launch_shape"] = {"ctas": "one per work item" if one_per_item else (shape.ctas or "all that fit"),
+                           "use_pdl": shape.use_pdl}
+    out["autotune"] = [{"ctas": "one per work item" if t["ctas"] >= (1 << 30) else t["ctas"],
+                        "use_pdl": t["use_pdl"], "ms_per_step": round(t["ms_per_step"], 5)}
                        for t in tune]
     out["blocks"] = {"b4": sum(1 for s in specs if s[2] == 4), "b8": sum(1 for s in specs if s[2] == 8)}
     r.close()
@@ -398,11 +408,16 @@ def run_batched(args, dev):
 def run_serving(args, dev):
     """256 streams, resolutions uniform over {320x240, 640x480, 1280x720,
     1920x1080, 3840x2160}, Poisson arrivals (20 streams/s), 30 fps for
-    U(5, 30) s each (durations and arrival gaps divided by --serve-speed),
-    admitted under a fixed HBM budget, served by the continuous-batching
-    loop; frames come from pinned host memory and masks go back to it."""
+    U(5, 30) s each, admitted under a fixed HBM budget, served by the
+    continuous-batching loop; frames come from pinned host memory and masks
+    go back to it.  Three runs of the same arrival sequence: the offered load
+    (real time), and time compressed by --serve-saturate (arrivals and frame
+    rate that many times faster, durations that many times shorter: the same
+    frames, far more than the server can take, so the HBM budget and the
+    queues bind) for the batched engine and for the plain per-stream engine
+    (one copy, launch and copy back per frame on 8 CUDA streams)."""
     import torch
-    from paper_1702_05156_gb300.serve import GpuEngine, Server, simulate
+    from paper_1702_05156_gb300.serve import GpuEngine, PlainEngine, Server, simulate
     from paper_1702_05156_gb300.synth import make_stream, spec_for
 
     res = [(320, 240), (640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
@@ -410,32 +425,43 @@ def run_serving(args, dev):
     for i, (w, h) in enumerate(res):
         fr, H = make_stream(spec_for(w, h, args.serve_pool, seed=100000 + i), device=dev)
         pools[(w, h)] = (fr.cpu().pin_memory(), H)
-    sp = args.serve_speed
-    srv = Server(GpuEngine(device=dev.index or 0), hbm_budget=int(args.serve_budget_gb * 2 ** 30))
-    # the cyclic garbage collector stops every thread while it scans the
-    # ~10^5 live request objects; a latency-sensitive application freezes
-    # its setup and keeps it off while serving
-    import gc
-    gc.collect()
-    gc.freeze()
-    gc.disable()
-    try:
-        wall, futs = simulate(srv, args.serve_streams, 20.0 * sp, 30.0 * sp, 5.0 / sp, 30.0 / sp,
-                              res, pools, seed=7)
-    finally:
-        gc.enable()
-        gc.unfreeze()
-    srv.shutdown()
-    st = srv.stats()
-    return {"streams": args.serve_streams, "arrival_rate_per_s": 20.0 * sp, "fps": 30.0 * sp,
-            "duration_s": [5.0 / sp, 30.0 / sp], "hbm_budget_gb": args.serve_budget_gb,
-            "time_compression": sp, "wall_s": round(wall, 2),
-            "frames": st["frames"], "steps": st["steps"], "mean_batch": round(st["mean_batch"], 2),
-            "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-            "max_ms": round(st["max_ms"], 3),
-            "served_mpix_s": round(st["pixels"] / wall / 1e6, 1),
-            "note": "latency = host submit -> mask back in pinned host memory; Python's cyclic "
-                    "garbage collector is frozen and off while serving"}
+
+    def one(engine, sp):
+        srv = Server(engine, hbm_budget=int(args.serve_budget_gb * 2 ** 30))
+        # the cyclic garbage collector stops every thread while it scans the
+        # ~10^5 live request objects; a latency-sensitive application freezes
+        # its setup and keeps it off while serving
+        import gc
+        gc.collect()
+        gc.freeze()
+        gc.disable()
+        try:
+            wall, futs = simulate(srv, args.serve_streams, 20.0 * sp, 30.0 * sp, 5.0 / sp, 30.0 / sp,
+                                  res, pools, seed=7)
+        finally:
+            gc.enable()
+            gc.unfreeze()
+        srv.shutdown()
+        st = srv.stats()
+        return {"time_compression": sp, "arrival_rate_per_s": 20.0 * sp, "fps": 30.0 * sp,
+                "wall_s": round(wall, 2), "frames": st["frames"], "steps": st["steps"],
+                "mean_batch": round(st["mean_batch"], 2), "p50_ms": round(st["p50_ms"], 3),
+                "p99_ms": round(st["p99_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                "served_mpix_s": round(st["pixels"] / wall / 1e6, 1), "failed": st["failed"]}
+
+    out = {"streams": args.serve_streams, "hbm_budget_gb": args.serve_budget_gb,
+           "offered": one(GpuEngine(device=dev.index or 0), 1.0)}
+    if args.serve_saturate > 0:
+        sp = args.serve_saturate
+        out["saturated_batched"] = one(GpuEngine(device=dev.index or 0), sp)
+        out["saturated_plain"] = one(PlainEngine(device=dev.index or 0), sp)
+        out["served_vs_plain"] = round(out["saturated_batched"]["served_mpix_s"]
+                                       / max(out["saturated_plain"]["served_mpix_s"], 1e-9), 3)
+    out["note"] = ("latency = host submit -> mask back in pinned host memory; at the offered "
+                   "load the served Mpix/s is the load itself; the saturated runs measure what "
+                   "the server delivers; Python's cyclic garbage collector is frozen and off "
+                   "while serving")
+    return out
 
 
 def run_extras(args, dev, stream):
@@ -479,9 +505,9 @@ def run_extras(args, dev, stream):
     # 4K single stream: block 4 / 8, FP32 / FP16 state; then the widened
     # forms: blocks 1, 2 and 16 (FP32, fewer frames for block 1 and 2) and
     # the mixture-variance option (block 4)
-    runs = [(B, prec, False, T) for B in (4, 8) for prec in ("fp32", "fp16")]
-    runs += [(16, "fp32", False, T), (2, "fp32", False, min(T, 20)), (1, "fp32", False, min(T, 10)),
-             (4, "fp32", True, T)]
+    # (blocks 4 and 8 in FP32 and FP16 are the target_4k line)
+    runs = [(16, "fp32", False, T), (2, "fp32", False, min(T, 20)), (1, "fp32", False, min(T, 10)),
+            (4, "fp32", True, T)]
     if args.extra in (2, 3):   # the preprocessing or the motion-estimation forms only
         runs = []
     for B, prec, spread, n in runs:
@@ -505,6 +531,127 @@ def run_extras(args, dev, stream):
     del frames, masks
     torch.cuda.empty_cache()
     return res
+
+
+def precision_report(frames, Hs, B, prec, pdl, every):
+    """Part of the oracle leg: the step's FP32 / FP16-state results against
+    the FP64 oracle, teacher-forced at every `every`-th frame of the stream
+    (the oracle steps from the GPU's own previous state): the largest and
+    mean relative error of the means and variances over blocks whose ages
+    agree, the blocks whose ages differ, and the fraction of mask pixels that
+    differ."""
+    import torch
+    from oracle import oracle_step, set_threads, state_from_arrays
+    from paper_1702_05156_gb300 import dmsgm
+    set_threads(0)
+    T, H, W = frames.shape
+    m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=pdl)
+    mask = dmsgm.new_mask(H, W, frames.device)
+    keys = ("muA", "varA", "ageA", "muC", "varC", "ageC")
+    rel_max = {"mu": 0.0, "var": 0.0}
+    rel_sum = {"mu": 0.0, "var": 0.0}
+    n_rel = 0
+    ages = mask_bad = pix = 0
+    checked = []
+    prev = None
+    for t in range(T):
+        sample = (t + 1) % every == 0
+        if sample:
+            prev = m.get_state()
+        m.process(frames[t], Hs[t], mask)
+        if not sample:
+            continue
+        got = m.get_state()
+        bits = dmsgm.unpack_mask(mask, W)
+        pst = state_from_arrays(*(prev[k].astype(np.float64) for k in keys))
+        ost, omask = oracle_step(frames[t].cpu().numpy(), Hs[t], pst, block=B)
+        same = (got["ageA"] == ost.ageA) & (got["ageC"] == ost.ageC)
+        ages += int((~same).sum())
+        for kind in ("mu", "var"):
+            for side in ("A", "C"):
+                o = getattr(ost, kind + side)
+                e = np.abs(got[kind + side].astype(np.float64) - o) / np.maximum(np.abs(o), 1e-5 * 255)
+                rel_max[kind] = max(rel_max[kind], float(e[same].max(initial=0.0)))
+                rel_sum[kind] += float(e[same].sum())
+        n_rel += 2 * int(same.sum())
+        mask_bad += int((bits != omask).sum())
+        pix += W * H
+        checked.append(t)
+    m.close()
+    torch.cuda.empty_cache()
+    return {"frames_checked": checked, "mu_rel_max": rel_max["mu"], "var_rel_max": rel_max["var"],
+            "mu_rel_mean": rel_sum["mu"] / max(n_rel, 1), "var_rel_mean": rel_sum["var"] / max(n_rel, 1),
+            "age_mismatch_blocks": ages, "mask_disagree_frac": mask_bad / max(pix, 1),
+            "method": f"teacher-forced every {every}th frame against the FP64 oracle "
+                      f"(relative errors over blocks whose ages agree, floor 1e-5*255)"}
+
+
+def run_target_4k(args, dev, stream, peak, with_oracle):
+    """The 3840x2160 precision variant: blocks 4 and 8, FP32 and FP16 state,
+    a stream of `target_frames` pre-staged frames per step replayed as a CUDA
+    graph (per-frame device time, HBM bytes per frame and the fraction of the
+    measured HBM peak), the SM clocks during the timing, and -- in the oracle
+    leg -- the errors against the FP64 oracle."""
+    import torch
+    from paper_1702_05156_gb300 import dmsgm
+    from paper_1702_05156_gb300.synth import make_stream, spec_for
+
+    W, H, T = 3840, 2160, args.target_frames
+    frames, Hs = make_stream(spec_for(W, H, T, seed=args.seed), device=dev)
+    masks = dmsgm.new_mask(H, W, dev, n=T)
+    out = {"workload": f"plain DMSGM {W}x{H} uint8, {T} pre-staged frames per step "
+                       f"({T * W * H / 1e9:.2f} GB, larger than L2), one fused kernel per frame, "
+                       "CUDA graph", "frames": T}
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    time.sleep(0.3)
+    t_lo = time.time()
+    res = {}
+    for B, prec in ((4, "fp32"), (4, "fp16"), (8, "fp32"), (8, "fp16")):
+        m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=args.pdl)
+
+        def one_pass():
+            for t in range(T):
+                m.process(frames[t], Hs[t], masks[t], stream=stream)
+        with torch.cuda.stream(stream):
+            one_pass()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            one_pass()
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                g.replay()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        per = e0.elapsed_time(e1) / 1e3 / (reps * T)
+        bpp = bytes_per_pixel(B, prec)
+        ach = bpp * W * H / per / 1e9
+        res[f"b{B}_{prec}"] = {"frame_us": round(per * 1e6, 3), "mpix_s": round(W * H / per / 1e6, 1),
+                               "bytes_per_frame": int(bpp * W * H), "achieved_gbs": round(ach, 1),
+                               "frac": round(ach / peak, 4), "status": m.status()}
+        del g
+        m.close()
+    t_hi = time.time()
+    sampler.mark(t_lo, t_hi)
+    sampler.stop()
+    out["clocks"] = sampler.summary()
+    if with_oracle:
+        for B, prec in ((4, "fp32"), (4, "fp16"), (8, "fp32"), (8, "fp16")):
+            res[f"b{B}_{prec}"]["vs_oracle"] = precision_report(frames, Hs, B, prec, args.pdl,
+                                                                args.target_every)
+    out["configs"] = res
+    del frames, masks
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_pre_extras(args, dev, stream, frames, Hs, masks, graph_time, peak):
@@ -677,13 +824,19 @@ def main():
                     help="1: all extra configurations, 2: the preprocessing forms only, "
                          "3: the motion-estimation front end only, 0: none")
     ap.add_argument("--extra-frames", type=int, default=100)
+    ap.add_argument("--target", type=int, default=1,
+                    help="1: the 3840x2160 block 4 / 8, FP32 / FP16 line (target_4k)")
+    ap.add_argument("--target-frames", type=int, default=500)
+    ap.add_argument("--target-every", type=int, default=50,
+                    help="oracle comparison of target_4k at every n-th frame")
     ap.add_argument("--ref-frames", type=int, default=4)
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--batch-streams", type=int, default=64)
     ap.add_argument("--batch-frames", type=int, default=200)
     ap.add_argument("--serve", type=int, default=1)
     ap.add_argument("--serve-streams", type=int, default=256)
-    ap.add_argument("--serve-speed", type=float, default=1.0)
+    ap.add_argument("--serve-saturate", type=float, default=40.0,
+                    help="time compression of the saturated serving runs (0: none)")
     ap.add_argument("--serve-pool", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     ap.add_argument("--config", default=None,

@@ -88,9 +88,7 @@ typedef struct {
     int use_pdl;        /* 1: programmatic dependent launch -- a frame's
                            pixel load overlaps the previous kernel's tail, so
                            the frame must not be written by the kernel that
-                           immediately precedes the call on the stream, and
-                           consecutive frame steps of the handle on one
-                           stream may overlap (see step_wait);
+                           immediately precedes the call on the stream;
                            0 (default): plain stream order                    */
     int seq_tile_rows;  /* tile height of dmsgm_process_seq: 8, 16, 32 or 64
                            times the block size / 2 (32, 64, 128, 256 rows
@@ -137,18 +135,6 @@ typedef struct {
                            multi-frame entry point runs per-frame launches
                            and the batched one refuses such handles
                            (DMSGM_ERR_UNSUPPORTED).                          */
-    int step_wait;      /* with use_pdl, how a frame step of the per-tile
-                           kernel waits for the handle's previous one when
-                           that was the previous operation on the state, on
-                           the same stream and in the same stream capture
-                           (or neither captured):
-                           0 (default): each tile waits only until the
-                           tiles its motion compensation can reach (a bound
-                           from this and the previous homography) have
-                           stored the previous state; the previous step's
-                           mask stage then overlaps this one;
-                           1: every tile waits for the whole previous grid.
-                           Results are identical.                            */
 } dmsgm_opts;
 
 enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1, DMSGM_KERNEL_PIPE = 2 };
@@ -171,18 +157,13 @@ typedef struct {
     int mix_spread;              /* dmsgm_opts.mix_spread in use              */
     int pre_fused;               /* 1: the step kernel filters its own tile   */
     int checked;                 /* dmsgm_opts.checked in use                 */
-    int last_step_wait;          /* how the last frame step waited for the
-                                    previous one: 1 only for the neighbour
-                                    tiles, 0 for the whole previous grid (or
-                                    plain stream order)                      */
 } dmsgm_info;
 
 /* Device bytes a handle needs for its state: a 256-byte control block, one
  * int per 256 x (8*block) pixel tile (the multi-frame kernel's progress
- * counters), two ints per 256 x (4*block) pixel tile (the frame step's
- * launch and completion counters), and two buffers of three arrays
- * (Gx*Gy*2*s, Gx*Gy*2*s and Gx*Gy*2 bytes; s = 4 for FP32, 2 for FP16),
- * every part 256-byte aligned.  Returns 0 for invalid sizes. */
+ * counters), and two buffers of three arrays (Gx*Gy*2*s, Gx*Gy*2*s and
+ * Gx*Gy*2 bytes; s = 4 for FP32, 2 for FP16), every part 256-byte aligned.
+ * Returns 0 for invalid sizes. */
 size_t dmsgm_state_bytes(int width, int height, int block, int precision);
 
 /* Bytes of the packed host image used by dmsgm_get_state/dmsgm_set_state:
@@ -250,18 +231,13 @@ int dmsgm_process_seq(dmsgm_t h, const uint8_t* frames_dev, int n, const double*
  * afresh, as after create/reset), and the frames, homographies and masks as
  * in dmsgm_process_seq.  The multi-frame kernel's progress counters live in
  * one static array of 4096 ints in the library: a frame needing more tiles
- * (even a 256 x 256-pixel tiling of it needs more than 4096) is rejected with
- * DMSGM_ERR_INVALID_ARG before any CUDA call, as is a block that is not 4 or
- * 8 or a height that is not a multiple of the block (DMSGM_ERR_UNSUPPORTED);
- * a frame whose tiles cannot all be resident on the GPU returns
- * DMSGM_ERR_UNSUPPORTED.  Every call on a device shares that array (each
- * launch clears the counters it uses), so calls whose work may overlap on
- * the GPU race: keep them on one stream.  The array's device address
- * belongs to a CUDA context: the first call in each context (the current
- * one, or the device's primary context if none is current) looks it up
- * and caches it under the context's unique ID, so a call from another
- * context, or after a device reset, looks it up again.  Make the first call
- * in a context before any stream capture in it. */
+ * is rejected with DMSGM_ERR_INVALID_ARG, and one whose tiles cannot all be
+ * resident on the GPU, or whose block is not 4 or 8 or whose height is not
+ * a multiple of the block, with DMSGM_ERR_UNSUPPORTED.  Every call on a device
+ * shares that array (each launch clears the counters it uses), so calls
+ * whose work may overlap on the GPU race: keep them on one stream.  The
+ * first call on a device looks up the array's device address; make that
+ * first call before any stream capture. */
 int dmsgm_process_seq_noalloc(int width, int height, int block, int precision, float theta_s,
                               float theta_d, int age_max, void* state_dev, size_t state_bytes,
                               int* parity, int first, const uint8_t* frames_dev, int n,

@@ -50,7 +50,7 @@ class dmsgm_opts(ctypes.Structure):
                 ("kernel", ctypes.c_int), ("mix_spread", ctypes.c_int),
                 ("pre_gauss", ctypes.c_int), ("pre_sigma", ctypes.c_double),
                 ("pre_median", ctypes.c_int), ("pre_separate", ctypes.c_int),
-                ("checked", ctypes.c_int), ("step_wait", ctypes.c_int)]
+                ("checked", ctypes.c_int)]
 
 
 class dmsgm_batch_opts(ctypes.Structure):
@@ -66,8 +66,7 @@ class dmsgm_info(ctypes.Structure):
                 ("state_bytes", ctypes.c_size_t), ("host_state_bytes", ctypes.c_size_t),
                 ("tile_rows", ctypes.c_int), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("last_kernel", ctypes.c_int), ("mix_spread", ctypes.c_int),
-                ("pre_fused", ctypes.c_int), ("checked", ctypes.c_int),
-                ("last_step_wait", ctypes.c_int)]
+                ("pre_fused", ctypes.c_int), ("checked", ctypes.c_int)]
 
 
 class DmsgmError(RuntimeError):

@@ -54,7 +54,8 @@ class BatchRunner:
         self.Hs = [np.ascontiguousarray(h, dtype=np.float64) for h in Hs]
         self.T = min(f.shape[0] for f in frames)
         self.precision = precision
-        self.models = [Dmsgm(w, h, b, precision=precision) for (w, h, b) in specs]
+        # programmatic dependent launch for the plain path's single-stream steps
+        self.models = [Dmsgm(w, h, b, precision=precision, use_pdl=True) for (w, h, b) in specs]
         self.masks = [new_mask(h, w, device, n=self.T) for (w, h, b) in specs]
         self.pixels_per_step = sum(w * h for (w, h, b) in specs)
         self._H_steps = [np.stack([self.Hs[i][t] for i in range(len(specs))]).reshape(-1)
@@ -76,20 +77,39 @@ class BatchRunner:
                                self.masks[i][t].data_ptr(), stream)
 
     def capture(self, mode: str, shape: LaunchShape | None = None, steps: int | None = None,
-                stream: torch.cuda.Stream | None = None) -> torch.cuda.CUDAGraph:
-        """Capture `steps` (default T, even) consecutive steps into a graph."""
+                stream: torch.cuda.Stream | None = None, lanes: int = 8) -> torch.cuda.CUDAGraph:
+        """Capture `steps` (default T, even) consecutive steps into a graph.
+        mode "batched": one batched launch per step; "plain": one launch per
+        stream per step, all on the capturing stream; "plain_multi": the same
+        launches with stream i's on CUDA stream i % lanes (forked from and
+        joined back to the capturing stream), so independent streams' steps
+        can run side by side."""
         steps = steps or self.T
         assert steps % 2 == 0, "an even number of steps keeps the handles' parity consistent"
         stream = stream or torch.cuda.Stream()
         sh = stream.cuda_stream
         g = torch.cuda.CUDAGraph()
+        side = [torch.cuda.Stream() for _ in range(lanes)] if mode == "plain_multi" else []
         with torch.cuda.graph(g, stream=stream):
+            if side:
+                fork = torch.cuda.Event()
+                fork.record(stream)
+                for s in side:
+                    s.wait_event(fork)
             for k in range(steps):
                 t = k % self.T
                 if mode == "batched":
                     self.step_batched(t, shape or LaunchShape(), sh)
-                else:
+                elif mode == "plain":
                     self.step_plain(t, sh)
+                else:
+                    for i, m in enumerate(self.models):
+                        _lib.dmsgm_process(m.handle, self.frames[i][t].data_ptr(), self.Hs[i][t],
+                                           self.masks[i][t].data_ptr(), side[i % lanes].cuda_stream)
+            for s in side:
+                join = torch.cuda.Event()
+                join.record(s)
+                stream.wait_event(join)
         return g
 
     def warm(self, mode: str, shape: LaunchShape | None = None, stream=None):

@@ -12,7 +12,6 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -102,13 +101,13 @@ __global__ void dmsgm_selftest_wait_kernel(int* status, unsigned long long timeo
 
 // The per-tile kernel of the handle's block size (dmsgm_step.cuh).
 static cudaError_t launch_step(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
-                               const Coef& k, cudaStream_t s, bool pdl, const StepSync& sy) {
+                               const Coef& k, cudaStream_t s, bool pdl) {
     switch (h->B) {
-        case 1: return launch_step_block<1>(h, tmap, a, k, s, pdl, sy);
-        case 2: return launch_step_block<2>(h, tmap, a, k, s, pdl, sy);
-        case 4: return launch_step_block<4>(h, tmap, a, k, s, pdl, sy);
-        case 8: return launch_step_block<8>(h, tmap, a, k, s, pdl, sy);
-        case 16: return launch_step_block<16>(h, tmap, a, k, s, pdl, sy);
+        case 1: return launch_step_block<1>(h, tmap, a, k, s, pdl);
+        case 2: return launch_step_block<2>(h, tmap, a, k, s, pdl);
+        case 4: return launch_step_block<4>(h, tmap, a, k, s, pdl);
+        case 8: return launch_step_block<8>(h, tmap, a, k, s, pdl);
+        case 16: return launch_step_block<16>(h, tmap, a, k, s, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -136,9 +135,6 @@ static void carve(dmsgm_ctx* h) {
     const int s = h->prec == DMSGM_STATE_FP16 ? 2 : 4;
     h->status_dev = reinterpret_cast<int*>(h->mem);
     h->flags_dev = reinterpret_cast<int*>(static_cast<char*>(h->mem) + 256);
-    h->step_start_dev = reinterpret_cast<int*>(static_cast<char*>(h->mem) + 256 +
-                                               seq_flags_bytes(h->W, h->H, h->B));
-    h->step_done_dev = h->step_start_dev + step_tile_count(h->W, h->H, h->B);
     for (int b = 0; b < 2; ++b)
         h->buf[b] = state_buf(static_cast<char*>(h->mem), h->W, h->H, h->B, s, b);
 }
@@ -246,8 +242,6 @@ void advance(dmsgm_ctx* h) {
     h->parity ^= 1;
     h->initialized = true;
     h->frames++;
-    h->last.step = false;   // a frame step that keeps the counters sets it again
-    h->last_step_wait = 0;
 }
 
 bool displacement_bound(const double m[9], int W, int H, int B, double* ex, double* ey) {
@@ -276,36 +270,6 @@ bool displacement_bound(const double m[9], int W, int H, int B, double* ex, doub
     *ex = (lx + qx) / zmin / B;
     *ey = (ly + qy) / zmin / B;
     return std::isfinite(*ex) && std::isfinite(*ey);
-}
-
-// How a frame step of the per-tile kernel orders itself after the handle's
-// previous one: which counters it keeps and whether it waits only for the
-// neighbour tiles its gathers (and the previous step's gathers from its own
-// tile) can reach.  dbx, dby receive this frame's reach in blocks.
-static StepSync step_sync(dmsgm_ctx* h, const double* H3x3, cudaStream_t s, bool pdl,
-                          unsigned long long capture, int* dbx, int* dby) {
-    StepSync sy{};
-    sy.start = h->step_start_dev;
-    sy.done = h->step_done_dev;
-    double ex = 0.0, ey = 0.0;
-    *dbx = *dby = -1;
-    // a source block lies within ceil(|e|) + 1 blocks; one more for the
-    // kernel's FP32 rounding of the floor
-    if (displacement_bound(H3x3, h->W, h->H, h->B, &ex, &ey) && ex < 1.0e6 && ey < 1.0e6) {
-        *dbx = int(std::ceil(ex)) + 2;
-        *dby = int(std::ceil(ey)) + 2;
-    }
-    if (!pdl || h->step_wait || !h->last.step || h->last.stream != s || h->last.capture != capture ||
-        *dbx < 0 || h->last.dbx < 0)
-        return sy;
-    const int tbx = kTileW / h->B, tby = h->tile_rows / h->B;   // blocks per tile
-    const int rbx = std::max(*dbx, h->last.dbx), rby = std::max(*dby, h->last.dby);
-    const int rx = (rbx + tbx - 1) / tbx, ry = (rby + tby - 1) / tby;
-    if ((2 * rx + 1) * (2 * ry + 1) > 64) return sy;   // far-reaching motion: wait for the grid
-    sy.rx = rx;
-    sy.ry = ry;
-    sy.wait_tiles = 1;
-    return sy;
 }
 
 static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x3,
@@ -352,30 +316,11 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
         if (rc) return rc;
     }
     if (!launched) {
-        // the checked build keeps no counters
-        unsigned long long cap = 0;
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        DMSGM_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cs, &cap));
-        if (cs != cudaStreamCaptureStatusActive) cap = 0;
-        int dbx = -1, dby = -1;
-        StepSync sy{};
-        if (!h->checked) sy = step_sync(h, H3x3, s, pdl, cap, &dbx, &dby);
-        cudaError_t e = launch_step(h, *tm, a, c, s, pdl, sy);
+        cudaError_t e = launch_step(h, *tm, a, c, s, pdl);
         if (e != cudaSuccess)
             return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
-        h->last_kernel = DMSGM_KERNEL_TILE;
-        advance(h);
-        h->last_step_wait = sy.wait_tiles;
-        if (sy.start) {
-            h->last.step = true;
-            h->last.stream = s;
-            h->last.capture = cap;
-            h->last.dbx = dbx;
-            h->last.dby = dby;
-        }
-        return DMSGM_OK;
     }
-    h->last_kernel = DMSGM_KERNEL_PIPE;
+    h->last_kernel = launched ? DMSGM_KERNEL_PIPE : DMSGM_KERNEL_TILE;
     advance(h);
     return DMSGM_OK;
 }
@@ -442,7 +387,7 @@ void dmsgm_fault_inject(const char* spec) {
 size_t dmsgm_state_bytes(int W, int H, int B, int prec) {
     if (!valid_dims(W, H, B) || (prec != DMSGM_STATE_FP32 && prec != DMSGM_STATE_FP16)) return 0;
     const size_t N = size_t(W / B) * grid_rows(H, B);
-    return 256 + seq_flags_bytes(W, H, B) + step_sync_bytes(W, H, B) + 2 * buf_bytes(N, prec);
+    return 256 + seq_flags_bytes(W, H, B) + 2 * buf_bytes(N, prec);
 }
 
 size_t dmsgm_host_state_bytes(int W, int H, int B, int prec) {
@@ -512,11 +457,6 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
         return fail(DMSGM_ERR_INVALID_ARG, "checked must be 0 or 1");
     }
     h->checked = opts.checked;
-    if (opts.step_wait != 0 && opts.step_wait != 1) {
-        delete h;
-        return fail(DMSGM_ERR_INVALID_ARG, "step_wait must be 0 or 1");
-    }
-    h->step_wait = opts.step_wait;
     if (h->checked && (h->mix_spread || opts.pre_gauss || opts.pre_median)) {
         delete h;
         return fail(DMSGM_ERR_INVALID_ARG, "the checked build covers the plain frame step "
@@ -567,13 +507,8 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
     // Only the control block needs a defined value (the status word); the
     // state buffers are written by the first process() or set_state().  A
     // synchronous copy from the host orders it without a device-wide sync.
-    // The frame step's counters start at zero as well.
     static const unsigned char zeros[256] = {0};
     cudaError_t e = cudaMemcpy(h->mem, zeros, sizeof zeros, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        std::vector<unsigned char> z(step_sync_bytes(W, H, B), 0);
-        e = cudaMemcpy(h->step_start_dev, z.data(), z.size(), cudaMemcpyHostToDevice);
-    }
     if (e != cudaSuccess) {
         if (h->owns_mem) cudaFree(h->mem);
         delete h;
@@ -817,7 +752,6 @@ int dmsgm_set_state(dmsgm_t h, const void* host_buf, size_t bytes) {
     }
     DMSGM_CUDA_TRY(cudaDeviceSynchronize());
     h->initialized = true;
-    h->last.step = false;
     return DMSGM_OK;
 }
 
@@ -826,7 +760,6 @@ int dmsgm_reset(dmsgm_t h) {
     if (!h) return fail(DMSGM_ERR_INVALID_ARG, "NULL handle");
     h->initialized = false;
     h->frames = 0;
-    h->last.step = false;
     return DMSGM_OK;
 }
 
@@ -849,7 +782,6 @@ int dmsgm_get_info(dmsgm_t h, dmsgm_info* o) {
     o->mix_spread = h->mix_spread;
     o->pre_fused = h->pre_fused;
     o->checked = h->checked;
-    o->last_step_wait = h->last_step_wait;
     return DMSGM_OK;
 }
 

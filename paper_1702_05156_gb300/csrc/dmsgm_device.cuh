@@ -78,10 +78,9 @@ struct StateBuf {
 
 // Device-memory layout of a handle: a 256-byte control block (status word
 // first), the per-tile progress counters of the multi-frame kernel (one int
-// per 256 x 8B tile, the smallest tile it uses), the per-tile launch and
-// completion counters of the frame-step kernel (two ints per 256 x 4B tile,
-// the smallest step tile), then the two state buffers; every array 256-byte
-// aligned.  s is the size of one stored value (4: FP32, 2: FP16).
+// per 256 x 8B tile, the smallest tile it uses), then the two state buffers;
+// every array 256-byte aligned.  s is the size of one stored value (4: FP32,
+// 2: FP16).
 __host__ __device__ __forceinline__ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 __host__ __device__ __forceinline__ size_t state_buf_bytes(size_t N, int s) {
     return 2 * align256(N * 2 * s) + align256(N * 2);
@@ -92,17 +91,10 @@ __host__ __device__ __forceinline__ size_t seq_flag_count(int W, int H, int B) {
 __host__ __device__ __forceinline__ size_t seq_flags_bytes(int W, int H, int B) {
     return align256(4 * seq_flag_count(W, H, B));
 }
-__host__ __device__ __forceinline__ size_t step_tile_count(int W, int H, int B) {
-    return size_t((W + kTileW - 1) / kTileW) * size_t((H + 4 * B - 1) / (4 * B));
-}
-__host__ __device__ __forceinline__ size_t step_sync_bytes(int W, int H, int B) {
-    return align256(2 * 4 * step_tile_count(W, H, B));
-}
 __host__ __device__ __forceinline__ StateBuf state_buf(char* mem, int W, int H, int B, int s,
                                                       int which) {
     const size_t N = size_t(W / B) * grid_rows(H, B);
-    char* p = mem + 256 + seq_flags_bytes(W, H, B) + step_sync_bytes(W, H, B) +
-              size_t(which) * state_buf_bytes(N, s);
+    char* p = mem + 256 + seq_flags_bytes(W, H, B) + size_t(which) * state_buf_bytes(N, s);
     StateBuf b;
     b.mu = p; p += align256(N * 2 * s);
     b.var = p; p += align256(N * 2 * s);
@@ -235,56 +227,23 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 }
 
 
-// Ordering of consecutive frame steps of one handle (the per-tile kernel).
-// Each step tile has two counters in the handle's memory: start (launches
-// that have begun the tile; a CTA's atomic increment at entry returns its
-// launch's generation g) and done (the generation whose state stores for the
-// tile are complete, published with a release after them).  A launch reads
-// the previous state of the tiles its back-projected blocks reach and
-// overwrites the state the previous launch read from its own tile, so
-// instead of waiting for the whole previous grid (griddepcontrol.wait) it may
-// wait until every tile within (rx, ry) tiles has done >= g - 1.  Every CTA
-// of the previous launch has begun (and counted) before the next launch
-// starts, because a programmatic dependent launch begins only after all
-// CTAs of its predecessor have triggered it, and they trigger after their
-// increment.
-struct StepSync {
-    int* start;         // NULL: no counters (griddepcontrol.wait only)
-    int* done;
-    int rx, ry;         // reach in tiles when wait_tiles is set
-    int wait_tiles;     // 1: wait for the neighbours' counters; 0: for the previous grid
-};
-
-__device__ __forceinline__ bool wait_done(const int* f, int target, uint64_t timeout_ns) {
-    if (ld_acquire_gpu(f) >= target) return true;
-    const uint64_t t0 = global_timer_ns();
-    for (uint32_t it = 0;; ++it) {
-        if (it >= 8) __nanosleep(32);
-        if (ld_acquire_gpu(f) >= target) return true;
-        if ((it & 15u) == 15u && global_timer_ns() - t0 > timeout_ns) return false;
-    }
-}
-
 // ------------------------------------------------------------------ state I/O
 // Both models of a block, as (A, C) float pairs.  COH = false: read-only
-// cache path (the previous buffer is not written while the launch runs);
-// COH = true: ordinary coherent loads, for state that another CTA or a
-// concurrently running grid published with a release that this CTA
-// acquired (weak loads ordered after the acquire see the released values;
-// the non-coherent path gives no such guarantee).
+// cache path (the previous buffer is not written during the launch);
+// COH = true: L2 only, for state that other CTAs of the same launch write.
 template <bool COH>
 __device__ __forceinline__ float2 ld2(const void* base, int k, float*) {
     const float2* p = static_cast<const float2*>(base) + k;
-    return COH ? __ldca(p) : __ldg(p);
+    return COH ? __ldcg(p) : __ldg(p);
 }
 template <bool COH>
 __device__ __forceinline__ float2 ld2(const void* base, int k, __half*) {
     const __half2* p = static_cast<const __half2*>(base) + k;
-    return __half22float2(COH ? __ldca(p) : __ldg(p));
+    return __half22float2(COH ? __ldcg(p) : __ldg(p));
 }
 template <bool COH>
 __device__ __forceinline__ uint32_t ld_age(const uint16_t* base, int k) {
-    return COH ? __ldca(base + k) : __ldg(base + k);
+    return COH ? __ldcg(base + k) : __ldg(base + k);
 }
 __device__ __forceinline__ void st2(void* base, int k, float2 v, float*) {
     static_cast<float2*>(base)[k] = v;

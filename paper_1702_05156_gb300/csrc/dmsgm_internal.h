@@ -67,8 +67,6 @@ struct dmsgm_ctx {
     int kernel;                  // DMSGM_KERNEL_*
     int mix_spread;              // 1: mixed variance carries the spread of the mixed means
     int checked;                 // 1: the per-tile kernel's checked build
-    int step_wait;               // dmsgm_opts.step_wait
-    int last_step_wait;          // 1: the last frame step waited for neighbour tiles only
     int pre_gauss;               // preprocessing: Gaussian size (0: none)
     double pre_sigma;            //   its sigma
     int pre_median;              //   1: 3 x 3 median
@@ -85,16 +83,6 @@ struct dmsgm_ctx {
     size_t state_bytes;
     int* status_dev;             // device status word (inside mem)
     int* flags_dev;              // per-tile progress counters of the multi-frame kernel
-    int* step_start_dev;         // per step tile: frame-step launches that have started it
-    int* step_done_dev;          //   ... and that have stored its state
-    // the last operation on the state, for the frame step's choice of how to
-    // wait for its predecessor (dmsgm_step.cuh, StepSync)
-    struct {
-        bool step;               // it was a frame-step launch that kept the counters
-        cudaStream_t stream;     //   on this stream
-        unsigned long long capture;   //   in this stream capture (0: none)
-        int dbx, dby;            //   its dependency reach in blocks (-1: unbounded)
-    } last;
     dmsgm::StateBuf buf[2];
     int parity;                  // buffer holding the current state
     bool initialized;
@@ -125,6 +113,11 @@ void fill_args(const dmsgm_ctx* h, int affine, uint32_t* mask_dev, StreamArgs* a
 // Advance the handle's bookkeeping after a frame has been enqueued.
 void advance(dmsgm_ctx* h);
 
+// Bound on the block-unit displacement (|ex|, |ey|) of every block centre of
+// a W x H grid of B x B blocks under m (current -> previous); false when the
+// map puts some block behind the camera (no bound).
+bool displacement_bound(const double m[9], int W, int H, int B, double* ex, double* ey);
+
 // The driver's cuTensorMapEncodeTiled (NULL if unavailable).
 #include <cudaTypedefs.h>
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
@@ -143,17 +136,12 @@ int launch_pipe(dmsgm_ctx* h, const CUtensorMap& frame_map, const StreamArgs& a,
 // instantiated in dmsgm_step_b<B>.cu).
 template <int B>
 cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
-                              const Coef& k, cudaStream_t s, bool pdl, const StepSync& sy);
-
-// Bound on the block-unit displacement (|ex|, |ey|) of every block centre of
-// a W x H grid of B x B blocks under m (current -> previous); false when the
-// map puts some block behind the camera (no bound).
-bool displacement_bound(const double m[9], int W, int H, int B, double* ex, double* ey);
-extern template cudaError_t launch_step_block<1>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool, const StepSync&);
-extern template cudaError_t launch_step_block<2>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool, const StepSync&);
-extern template cudaError_t launch_step_block<4>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool, const StepSync&);
-extern template cudaError_t launch_step_block<8>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool, const StepSync&);
-extern template cudaError_t launch_step_block<16>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool, const StepSync&);
+                              const Coef& k, cudaStream_t s, bool pdl);
+extern template cudaError_t launch_step_block<1>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<2>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<4>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<8>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
+extern template cudaError_t launch_step_block<16>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&, const Coef&, cudaStream_t, bool);
 
 // The preprocessing filter's weights (dmsgm_prefilter.cu): false if the
 // Gaussian size or sigma is invalid; *half is 0 when the quantised blur is the

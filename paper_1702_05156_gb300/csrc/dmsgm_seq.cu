@@ -366,7 +366,6 @@ int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* Hs,
             return fail(DMSGM_ERR_CUDA, "multi-frame kernel launch failed: %s", cudaGetErrorString(e));
         h->parity = (h->parity + n) & 1;
         h->initialized = true;
-        h->last.step = false;
         h->frames += n;
     }
     return DMSGM_OK;

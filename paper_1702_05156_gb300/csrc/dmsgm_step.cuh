@@ -21,50 +21,30 @@ constexpr int step_min_blocks() {
     return B == 8 ? (RPT == 1 ? 64 : 32) / NW : (B == 1 && NW == 4 && RPT == 1 ? 6 : 1);
 }
 
-// SYNC: the launch keeps the handle's step counters (StepSync) and waits
-// either for the previous grid or, with sy.wait_tiles, only for the
-// neighbour tiles; the state gathers then use coherent loads, since the
-// previous launch may still be running (its mask stage comes after its
-// counters' release).
-template <int B, typename T, int NW, int RPT, bool SPREAD, bool SYNC>
+template <int B, typename T, int NW, int RPT, bool SPREAD>
 __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
     dmsgm_step_kernel(const __grid_constant__ CUtensorMap tmap, const StreamArgs a, const Coef k,
-                      int* status, const StepSync sy) {
+                      int* status) {
     constexpr int STRIPS = NW * RPT;          // strip rows per tile
     constexpr int TILE_H = STRIPS * B;
     __shared__ __align__(128) uint8_t tile[TILE_H * kTileW];
     __shared__ __align__(8) uint64_t bar;
     __shared__ Origin orig[2 * STRIPS];
-    __shared__ int gen;
     const int tx0 = blockIdx.x * kTileW;
     const int ty0 = blockIdx.y * TILE_H;
-    const int tid = blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_arrive_expect_tx(&bar, TILE_H * kTileW);
         tma_load_2d(tile, &tmap, tx0, ty0, &bar);
-        if constexpr (SYNC) gen = atomicAdd(sy.start + tid, 1) + 1;
     }
     fill_origins<B>(a, k, tx0, ty0, STRIPS, orig);
     __syncthreads();
-    // publish this launch's tile as done (after its state stores, or when it
-    // gives up), so that later launches never wait for it in vain
-    auto publish = [&]() {
-        if constexpr (SYNC) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                st_release_gpu(sy.done + tid, gen);
-            }
-        }
-    };
     const bool ok = mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
     if (__syncthreads_or(!ok)) {
         // report, give the copy one more bounded chance to land, and leave
         if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
         mbar_wait_bounded(&bar, 0, kWaitTimeoutNs);
-        publish();
         return;
     }
     // The pixels, their block statistics and the back-projections do not
@@ -76,32 +56,13 @@ __global__ void __launch_bounds__(NW * 32, (step_min_blocks<B, NW, RPT>()))
     Proj pj[RPT][BPL];
     tile_stats<B, NW, RPT>(a, tile, ty0, xin, st);
     tile_project<B, NW, RPT>(a, k, tx0, ty0, orig, pj);
-    bool waited = true;
-    if (SYNC && sy.wait_tiles) {
-        // every tile within (rx, ry), this one included, has stored the
-        // previous launch's state (so also finished reading the buffer this
-        // launch overwrites)
-        const int nx = 2 * sy.rx + 1, n = nx * (2 * sy.ry + 1);
-        for (int q = threadIdx.x; q < n; q += NW * 32) {
-            const int ntx = int(blockIdx.x) + q % nx - sy.rx, nty = int(blockIdx.y) + q / nx - sy.ry;
-            if (ntx < 0 || ntx >= int(gridDim.x) || nty < 0 || nty >= int(gridDim.y)) continue;
-            if (!wait_done(sy.done + nty * gridDim.x + ntx, gen - 1, kWaitTimeoutNs)) waited = false;
-        }
-        if (__syncthreads_or(!waited)) {
-            if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
-            publish();
-            return;
-        }
-    } else {
-        pdl_wait();
-    }
+    pdl_wait();
     // Triggered here, not at entry: an earlier trigger lets the CTAs of
     // several later frames start, and their pixel loads and statistics then
     // compete with this frame's update, the recurrence's critical path.
     pdl_launch_dependents();
     float muA[RPT][BPL], thr[RPT][BPL];
-    tile_update<B, T, NW, RPT, SYNC, SPREAD>(a, tx0, ty0, pj, st, muA, thr);
-    publish();
+    tile_update<B, T, NW, RPT, false, SPREAD>(a, tx0, ty0, pj, st, muA, thr);
     tile_mask<B, NW, RPT>(a, tile, tx0, ty0, st, muA, thr);
 }
 
@@ -151,28 +112,12 @@ __global__ void __launch_bounds__(NW * 32)
 
 template <int B, typename T, int NW, int RPT>
 static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, const Coef& k,
-                                 int* status, cudaStream_t s, bool pdl, bool checked,
-                                 const StepSync& sy) {
+                                 int* status, cudaStream_t s, bool pdl, bool checked) {
+    // the mixture-variance option and the checked build have their own kernels
+    auto kern = checked ? dmsgm_step_checked_kernel<B, T, NW, RPT>
+                        : (a.spread ? dmsgm_step_kernel<B, T, NW, RPT, true>
+                                    : dmsgm_step_kernel<B, T, NW, RPT, false>);
     constexpr int TILE_H = NW * RPT * B;
-    if (!checked) {
-        // the plain step: with or without the mixture-variance option, with
-        // or without the step counters
-        auto kern = a.spread ? (sy.start ? dmsgm_step_kernel<B, T, NW, RPT, true, true>
-                                         : dmsgm_step_kernel<B, T, NW, RPT, true, false>)
-                             : (sy.start ? dmsgm_step_kernel<B, T, NW, RPT, false, true>
-                                         : dmsgm_step_kernel<B, T, NW, RPT, false, false>);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
-        cfg.blockDim = dim3(NW * 32, 1, 1);
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = pdl ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, kern, tmap, a, k, status, sy);
-    }
-    auto kern = dmsgm_step_checked_kernel<B, T, NW, RPT>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.W + kTileW - 1) / kTileW, (a.H + TILE_H - 1) / TILE_H, 1);
     cfg.blockDim = dim3(NW * 32, 1, 1);
@@ -195,7 +140,7 @@ static int step_capacity(int device) {
     if (device < 0 || device >= 64) return 0;
     if (!cache[device]) {
         int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_step_kernel<B, T, NW, RPT, false, false>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_step_kernel<B, T, NW, RPT, false>,
                                                           NW * 32, 0) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
             cudaGetLastError();
@@ -220,7 +165,7 @@ static int step_rpt_q8(const dmsgm_ctx* h) {
 // tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1) or (4, 2), (8, 2)}
 template <int B>
 cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
-                              const Coef& k, cudaStream_t s, bool pdl, const StepSync& sy) {
+                              const Coef& k, cudaStream_t s, bool pdl) {
     const int q = h->tile_rows / B;   // 4, 8 or 16
     const bool f16 = h->prec == DMSGM_STATE_FP16;
     if (q == 8 && h->step_rpt == 0)
@@ -229,7 +174,7 @@ cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const Strea
     int* st = h->status_dev;
     const bool ck = h->checked != 0;
 #define DMSGM_CASE(TT, QQ, NWW, RR) \
-    if (q == QQ && rpt == RR) return launch_step_t<B, TT, NWW, RR>(tmap, a, k, st, s, pdl, ck, sy);
+    if (q == QQ && rpt == RR) return launch_step_t<B, TT, NWW, RR>(tmap, a, k, st, s, pdl, ck);
     if (!f16) {
         DMSGM_CASE(float, 4, 4, 1) DMSGM_CASE(float, 8, 8, 1) DMSGM_CASE(float, 8, 4, 2)
         DMSGM_CASE(float, 16, 8, 2)

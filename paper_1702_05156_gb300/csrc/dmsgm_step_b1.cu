@@ -4,5 +4,5 @@
 
 namespace dmsgm {
 template cudaError_t launch_step_block<1>(dmsgm_ctx*, const CUtensorMap&, const StreamArgs&,
-                                           const Coef&, cudaStream_t, bool, const StepSync&);
+                                           const Coef&, cudaStream_t, bool);
 }  // namespace dmsgm

@@ -53,7 +53,7 @@ class Dmsgm:
                  tile_rows: int = 0, use_pdl: bool = False, state_mem: torch.Tensor | None = None,
                  seq_tile_rows: int = 0, kernel: str = "auto", mix_spread: bool = False,
                  prefilter: tuple | None = None, prefilter_separate: bool = False,
-                 checked: bool = False, step_wait: str = "tiles"):
+                 checked: bool = False):
         prec = {"fp32": DMSGM_STATE_FP32, "fp16": DMSGM_STATE_FP16}[precision]
         opts = _lib.dmsgm_opts()
         opts.precision = prec
@@ -64,7 +64,6 @@ class Dmsgm:
                        "pipe": DMSGM_KERNEL_PIPE}[kernel]
         opts.mix_spread = 1 if mix_spread else 0
         opts.checked = 1 if checked else 0
-        opts.step_wait = {"tiles": 0, "grid": 1}[step_wait]
         if prefilter is not None:   # (gauss_size, sigma, median): Sec. 2.1 preprocessing
             opts.pre_gauss, opts.pre_sigma, opts.pre_median = (int(prefilter[0]),
                                                                float(prefilter[1]),

@@ -131,7 +131,8 @@ class GpuEngine:
         with torch.cuda.device(self.device):
             raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
             off = (-raw.data_ptr()) % 256
-            m = Dmsgm(W, H, block, precision=self.precision, state_mem=raw[off:off + nbytes])
+            m = Dmsgm(W, H, block, precision=self.precision, state_mem=raw[off:off + nbytes],
+                      use_pdl=self.use_pdl)
             frames = torch.empty((2, H, W), dtype=torch.uint8, device=self.device)
             masks = torch.empty((2, H, mask_words(W)), dtype=torch.int32, device=self.device)
         # pinned result ring: a request's mask stays valid until RING more
@@ -202,6 +203,50 @@ class GpuEngine:
         ev.synchronize()
 
 
+class PlainEngine(GpuEngine):
+    """The plain per-stream path behind the same server, for comparison: no
+    batching -- every request is its own host->device copy, one
+    dmsgm_process launch and the mask's copy back, on one of `lanes` CUDA
+    streams (a stream's frames always on the same one, which keeps its
+    recurrence in order).  Admission, slots and pinned rings as GpuEngine."""
+
+    def __init__(self, precision: str = "fp32", device: int = 0, use_pdl: bool = True,
+                 lanes: int = 8):
+        super().__init__(precision, device, use_pdl)
+        self.lanes = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
+
+    def warm(self):
+        pass
+
+    def _launch(self, reqs):
+        used = {}
+        for r in reqs:
+            sl = self.slots[r.sid]
+            j = sl["n"]
+            sl["n"] = j + 1
+            ls = self.lanes[r.sid % len(self.lanes)]
+            used[id(ls)] = ls
+            r.mask_host = sl["ring"][j % self.RING]
+            dev_frame = sl["frames"][j & 1]
+            dev_mask = sl["masks"][j & 1]
+            with torch.cuda.stream(ls):
+                dev_frame.copy_(r.frame, non_blocking=True)
+                _lib.dmsgm_process(sl["m"].handle, dev_frame.data_ptr(), r.H, dev_mask.data_ptr(),
+                                   ls.cuda_stream)
+                r.mask_host.copy_(dev_mask, non_blocking=True)
+        evs = []
+        for ls in used.values():
+            ev = torch.cuda.Event()
+            ev.record(ls)
+            evs.append(ev)
+        return evs
+
+    @staticmethod
+    def wait(evs):
+        for ev in evs:
+            ev.synchronize()
+
+
 class Server:
     """Admission by memory budget + continuous batching over an engine."""
 
@@ -224,7 +269,8 @@ class Server:
         self.latencies = []
         self.pixels = 0
         self.failed = 0
-        self.admit_log = []
+        self.admit_log = []      # (time, sid) of each admission
+        self.release_log = []    # (time, sid) of each release
         if hasattr(engine, "reserve"):
             engine.reserve(self.budget)
         if hasattr(engine, "warm"):
@@ -300,6 +346,7 @@ class Server:
         return out
 
     def _release(self, info):
+        self.release_log.append((time.perf_counter(), info.sid))
         self.engine.close(info.sid)
         self.used -= info.nbytes
         del self.active[info.sid]

@@ -45,11 +45,10 @@ def test_version_and_sizes(L):
     # 1920x1080, B=4: 480x270 blocks; a buffer = mu and var arrays of N
     # (A, C) pairs and an age array of N byte pairs, each rounded up to 256
     # bytes; two buffers plus a 256-byte control block
-    # plus one progress counter per 256 x 32 tile (8 x 34 tiles) and two
-    # step counters per 256 x 16 tile (8 x 68 tiles)
+    # plus one progress counter per 256 x 32 tile (8 x 34 tiles)
     N = 480 * 270
     r = lambda x: (x + 255) // 256 * 256  # noqa: E731
-    flags = r(4 * 8 * 34) + r(2 * 4 * 8 * 68)
+    flags = r(4 * 8 * 34)
     assert L.dmsgm_state_bytes(1920, 1080, 4, 0) == 256 + flags + 2 * (2 * r(8 * N) + r(2 * N))
     assert L.dmsgm_state_bytes(1920, 1080, 4, 1) == 256 + flags + 2 * (2 * r(4 * N) + r(2 * N))
     assert L.dmsgm_host_state_bytes(1920, 1080, 4, 0) == N * 18

@@ -81,10 +81,26 @@ def test_hd_sampled_teacher_forced(lib, precision, block):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_4k_sampled_teacher_forced(lib, precision):
-    frames, Hs = make_stream(spec_for(3840, 2160, 12, seed=0), device="cuda")
-    rep = _run_teacher_forced(lib, frames, Hs, block=4, precision=precision, every=5)
+@pytest.mark.parametrize("block", [4, 8])
+def test_4k_sampled_teacher_forced(lib, precision, block):
+    """3840x2160, 24 frames in the benchmark's launch configuration
+    (programmatic dependent launch, neighbour-tile waits), teacher-forced on
+    every 5th frame and the last at full size."""
+    frames, Hs = make_stream(spec_for(3840, 2160, 24, seed=0), device="cuda")
+    rep = _run_teacher_forced(lib, frames, Hs, block=block, precision=precision, every=5,
+                              use_pdl=True)
     rep.assert_ok()
+    assert rep.exempt <= 1e-3 * rep.blocks, rep
+
+
+def test_hd_full_length_teacher_forced(lib):
+    """The measured workload end to end: 1920x1080, block 4, FP32, all 300
+    frames in the benchmark's launch configuration, teacher-forced on every
+    10th frame and the last."""
+    frames, Hs = make_stream(spec_for(1920, 1080, 300, seed=0), device="cuda")
+    rep = _run_teacher_forced(lib, frames, Hs, block=4, every=10, use_pdl=True)
+    rep.assert_ok()
+    assert rep.exempt <= 1e-3 * rep.blocks, rep
 
 
 @pytest.mark.parametrize("W,H,block", [(16, 8, 4), (16, 8, 8), (48, 20, 4), (272, 36, 4),

@@ -72,3 +72,70 @@ def test_batch_runner_graph_equals_alone(lib):
         for i in range(len(CFGS)):
             assert torch.equal(r.masks[i].cpu(), ref[i]), (mode_shape, i)
     r.close()
+
+
+def _serve(lib, engine, budget, T, waves=1):
+    """Open every stream at once, submit its frames in `waves` bursts (the
+    later ones while earlier frames are on the GPU), close it; returns the
+    server and the masks per (stream, frame)."""
+    import time
+    from paper_1702_05156_gb300.serve import Server
+    streams = _streams(T)
+    srv = Server(engine, hbm_budget=budget)
+    hosts = [fr.cpu().pin_memory() for fr, _ in streams]
+    for sid, (w, h, b) in enumerate(CFGS):
+        srv.open_stream(sid, w, h, b)
+    futs = {}
+    per = (T + waves - 1) // waves
+    for wv in range(waves):
+        for sid in range(len(CFGS)):
+            for t in range(wv * per, min(T, (wv + 1) * per)):
+                futs[(sid, t)] = srv.submit(sid, hosts[sid][t], streams[sid][1][t])
+        time.sleep(0.002)
+    for sid in range(len(CFGS)):
+        srv.close_stream(sid)
+    got = {k: f.result(timeout=60).clone() for k, f in futs.items()}
+    srv.shutdown()
+    return srv, streams, got
+
+
+def test_binding_budget_admits_streams_as_memory_frees(lib):
+    """A budget that holds the two largest streams at most: the others wait,
+    are admitted as earlier streams retire, and each result equals the
+    stream's result alone."""
+    from paper_1702_05156_gb300.serve import GpuEngine
+    T = 6
+    eng = GpuEngine()
+    sizes = sorted((eng.stream_bytes(w, h, b) for (w, h, b) in CFGS), reverse=True)
+    budget = sizes[0] + sizes[1] + 1
+    srv, streams, got = _serve(lib, eng, budget, T, waves=2)
+    ref = _solo(lib, streams, T)
+    for (sid, t), m in got.items():
+        assert torch.equal(m, ref[sid][t]), (sid, t)
+    assert srv.stats()["frames"] == T * len(CFGS) and srv.stats()["failed"] == 0
+    # resident streams never exceeded the budget: replay admissions and releases
+    events = sorted([(t, 1, sid) for t, sid in srv.admit_log] +
+                    [(t, -1, sid) for t, sid in srv.release_log])
+    used = peak = 0
+    admitted_after_release = 0
+    released = 0
+    for t, kind, sid in events:
+        w, h, b = CFGS[sid]
+        used += kind * eng.stream_bytes(w, h, b)
+        peak = max(peak, used)
+        released += kind < 0
+        admitted_after_release += kind > 0 and released > 0
+    assert peak <= budget
+    assert admitted_after_release >= 1     # some stream waited for memory to free
+    assert len(srv.admit_log) == len(CFGS)
+
+
+def test_plain_engine_equals_alone(lib):
+    """The plain per-stream engine (one copy, launch and copy back per frame
+    on several CUDA streams) under the same server gives the same results."""
+    from paper_1702_05156_gb300.serve import PlainEngine
+    T = 6
+    srv, streams, got = _serve(lib, PlainEngine(lanes=3), 1 << 30, T, waves=3)
+    ref = _solo(lib, streams, T)
+    for (sid, t), m in got.items():
+        assert torch.equal(m, ref[sid][t]), (sid, t)

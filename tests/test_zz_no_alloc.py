@@ -38,9 +38,8 @@ def _state(mem, W, H, B, precision, which):
     s = 2 if precision else 4
     N = (W // B) * (H // B)
     tiles = ((W + 255) // 256) * ((H + 8 * B - 1) // (8 * B))
-    step_tiles = ((W + 255) // 256) * ((H + 4 * B - 1) // (4 * B))
     buf = 2 * r(N * 2 * s) + r(N * 2)
-    base = 256 + r(4 * tiles) + r(8 * step_tiles) + which * buf
+    base = 256 + r(4 * tiles) + which * buf
     host = mem.cpu().numpy()
     fdt = np.float16 if precision else np.float32
     mu = host[base:base + N * 2 * s].view(fdt).reshape(N, 2).astype(np.float64)
