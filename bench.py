@@ -536,24 +536,25 @@ def run_extras(args, dev, stream):
 def precision_report(frames, Hs, B, prec, pdl, every):
     """Part of the oracle leg: the step's FP32 / FP16-state results against
     the FP64 oracle, teacher-forced at every `every`-th frame of the stream
-    (the oracle steps from the GPU's own previous state): the largest and
-    mean relative error of the means and variances over blocks whose ages
-    agree, the blocks whose ages differ, and the fraction of mask pixels that
-    differ."""
+    (the oracle steps from the GPU's own previous state), with the parity
+    tests' bands (tests/parity_util.py): blocks whose decisions sit within
+    FP32 reach of a threshold are exempt and counted; over the others, the
+    largest relative error of the means and variances (floor 1e-5 * 255),
+    the blocks whose ages differ, and the mask pixels that differ (and how
+    many of them lie outside the 1e-4 threshold band)."""
     import torch
-    from oracle import oracle_step, set_threads, state_from_arrays
+    from oracle import set_threads
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_util import StepReport, compare_step
     from paper_1702_05156_gb300 import dmsgm
     set_threads(0)
     T, H, W = frames.shape
     m = dmsgm.Dmsgm(W, H, B, precision=prec, use_pdl=pdl)
     mask = dmsgm.new_mask(H, W, frames.device)
-    keys = ("muA", "varA", "ageA", "muC", "varC", "ageC")
-    rel_max = {"mu": 0.0, "var": 0.0}
-    rel_sum = {"mu": 0.0, "var": 0.0}
-    n_rel = 0
-    ages = mask_bad = pix = 0
+    rep = StepReport()
     checked = []
     prev = None
+    rel = 1e-5 if prec == "fp32" else 6e-4
     for t in range(T):
         sample = (t + 1) % every == 0
         if sample:
@@ -562,28 +563,18 @@ def precision_report(frames, Hs, B, prec, pdl, every):
         if not sample:
             continue
         got = m.get_state()
-        bits = dmsgm.unpack_mask(mask, W)
-        pst = state_from_arrays(*(prev[k].astype(np.float64) for k in keys))
-        ost, omask = oracle_step(frames[t].cpu().numpy(), Hs[t], pst, block=B)
-        same = (got["ageA"] == ost.ageA) & (got["ageC"] == ost.ageC)
-        ages += int((~same).sum())
-        for kind in ("mu", "var"):
-            for side in ("A", "C"):
-                o = getattr(ost, kind + side)
-                e = np.abs(got[kind + side].astype(np.float64) - o) / np.maximum(np.abs(o), 1e-5 * 255)
-                rel_max[kind] = max(rel_max[kind], float(e[same].max(initial=0.0)))
-                rel_sum[kind] += float(e[same].sum())
-        n_rel += 2 * int(same.sum())
-        mask_bad += int((bits != omask).sum())
-        pix += W * H
+        rep.add(compare_step(prev, got, dmsgm.unpack_mask(mask, W), frames[t].cpu().numpy(), Hs[t],
+                             block=B, rel=rel))
         checked.append(t)
     m.close()
     torch.cuda.empty_cache()
-    return {"frames_checked": checked, "mu_rel_max": rel_max["mu"], "var_rel_max": rel_max["var"],
-            "mu_rel_mean": rel_sum["mu"] / max(n_rel, 1), "var_rel_mean": rel_sum["var"] / max(n_rel, 1),
-            "age_mismatch_blocks": ages, "mask_disagree_frac": mask_bad / max(pix, 1),
-            "method": f"teacher-forced every {every}th frame against the FP64 oracle "
-                      f"(relative errors over blocks whose ages agree, floor 1e-5*255)"}
+    return {"frames_checked": checked, "blocks": rep.blocks, "exempt_blocks": rep.exempt,
+            "mu_rel_max": rep.max_rel_mu, "var_rel_max": rep.max_rel_var,
+            "age_mismatch_blocks": rep.age_mismatch, "state_out_of_tolerance": rep.state_out_of_tol,
+            "tolerance_rel": rel, "mask_disagree_frac": rep.mask_mismatch / max(rep.pixels, 1),
+            "mask_out_of_band": rep.mask_out_of_band,
+            "method": f"teacher-forced every {every}th frame against the FP64 oracle, "
+                      "bands of the parity tests"}
 
 
 def run_target_4k(args, dev, stream, peak, with_oracle):

@@ -159,6 +159,37 @@ __device__ __forceinline__ bool run_single(const BatchItem& it, int t, const Ori
     return true;
 }
 
+// One work item per CTA, in a kernel of its own: one pixel stage in dynamic
+// shared memory sized for the batch's largest block (8 KB when every stream
+// has 4x4 blocks, 16 KB with 8x8 ones), and no persistent loop, so more CTAs
+// fit an SM.
+template <int CAP, bool SPREAD>
+__global__ void __launch_bounds__(kBatchWarps * 32, 5)
+    dmsgm_batch_single_kernel(const __grid_constant__ BatchParams<CAP> p) {
+    extern __shared__ __align__(128) uint8_t stage[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int meta[2];
+    __shared__ Origin orig[2 * kBatchWarps];
+    const int t = blockIdx.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) stage_item<CAP>(p, t, meta, orig, stage, &bar);
+    __syncthreads();           // the item's stream and origins are visible
+    const BatchItem& it = p.item[meta[0]];
+    const int kind = (it.B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
+    bool ok;
+    switch (kind) {
+        case 0: ok = run_single<4, float, SPREAD>(it, t, orig, stage, &bar); break;
+        case 1: ok = run_single<4, __half, SPREAD>(it, t, orig, stage, &bar); break;
+        case 2: ok = run_single<8, float, SPREAD>(it, t, orig, stage, &bar); break;
+        default: ok = run_single<8, __half, SPREAD>(it, t, orig, stage, &bar); break;
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(reinterpret_cast<int*>(it.mem), kStatusWaitTimeout);
+}
+
 // SPREAD: built to honour the streams' mixture-variance option (each item
 // still follows its own flag); without it the option's code is compiled out.
 template <int CAP, bool SPREAD>
@@ -222,16 +253,20 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4)
 }
 
 template <int CAP, bool SPREAD>
-static cudaError_t launch_t(const BatchParams<CAP>& p, int ctas, cudaStream_t s, bool pdl) {
+static cudaError_t launch_t(const BatchParams<CAP>& p, int ctas, cudaStream_t s, bool pdl,
+                            int max_block) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas, 1, 1);
     cfg.blockDim = dim3(kBatchWarps * 32, 1, 1);
     cfg.stream = s;
+    const bool single = ctas >= p.total;
+    if (single) cfg.dynamicSmemBytes = size_t(kBatchWarps) * max_block * kTileW;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
+    if (single) return cudaLaunchKernelEx(&cfg, dmsgm_batch_single_kernel<CAP, SPREAD>, p);
     return cudaLaunchKernelEx(&cfg, dmsgm_batch_kernel<CAP, SPREAD>, p);
 }
 
@@ -257,9 +292,20 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
                    uint32_t* const* masks, const dmsgm_batch_opts& o, cudaStream_t s) {
     if (o.reserved != 0) return fail(DMSGM_ERR_INVALID_ARG, "dmsgm_batch_opts.reserved must be 0");
     static thread_local BatchParams<CAP> p;   // ~CAP*120 bytes: keep it off the stack
-    int total = 0;
+    // the work list holds the streams grouped by kind (block, precision), so
+    // that the CTAs resident on an SM mostly run the same code
+    int order[DMSGM_MAX_BATCH];
+    int m = 0;
+    for (int kind = 0; kind < 4; ++kind)
+        for (int i = 0; i < n; ++i)
+            if (((hs[i]->B == 8 ? 2 : 0) | (hs[i]->prec == DMSGM_STATE_FP16 ? 1 : 0)) == kind)
+                order[m++] = i;
+    for (int i = 0; i < n; ++i)   // blocks other than 4 and 8 are refused below
+        if (hs[i]->B != 4 && hs[i]->B != 8) order[m++] = i;
+    int total = 0, max_block = 4;
     bool spread = false;
-    for (int i = 0; i < n; ++i) {
+    for (int q = 0; q < n; ++q) {
+        const int i = order[q];
         const dmsgm_ctx* h = hs[i];
         if (h->W > 65535 || h->H > 65535)
             return fail(DMSGM_ERR_INVALID_ARG, "batched streams must be at most 65535 px wide/high");
@@ -270,7 +316,8 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
             return fail(DMSGM_ERR_UNSUPPORTED, "batched streams take no preprocessing (stream %d)", i);
         if (h->checked)
             return fail(DMSGM_ERR_UNSUPPORTED, "batched streams take no checked handles (stream %d)", i);
-        BatchItem& it = p.item[i];
+        BatchItem& it = p.item[q];
+        max_block = std::max(max_block, h->B);
         it.frame = frames[i];
         it.mask = masks[i];
         it.mem = static_cast<char*>(h->mem);
@@ -300,8 +347,8 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
     // one another, so more than fit at once is fine: one item each at most)
     int ctas = o.ctas > 0 ? o.ctas : resident_ctas<CAP>(hs[0]->device);
     ctas = std::max(1, std::min(ctas, total));
-    cudaError_t e = spread ? launch_t<CAP, true>(p, ctas, s, o.use_pdl > 0)
-                           : launch_t<CAP, false>(p, ctas, s, o.use_pdl > 0);
+    cudaError_t e = spread ? launch_t<CAP, true>(p, ctas, s, o.use_pdl > 0, max_block)
+                           : launch_t<CAP, false>(p, ctas, s, o.use_pdl > 0, max_block);
     if (e != cudaSuccess)
         return fail(DMSGM_ERR_CUDA, "batch kernel launch failed: %s", cudaGetErrorString(e));
     for (int i = 0; i < n; ++i) advance(hs[i]);
