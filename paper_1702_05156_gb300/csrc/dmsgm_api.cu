@@ -153,13 +153,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Tensor map of a W x H uint8 frame with a kTileW x tile_rows box.
-static int encode_frame_map(const dmsgm_ctx* h, const void* frame, CUtensorMap* out) {
+// Tensor map of a W x H uint8 frame with a kTileW x rows box (rows 0: the
+// handle's tile_rows).
+static int encode_frame_map(const dmsgm_ctx* h, const void* frame, CUtensorMap* out, int rows = 0) {
     auto enc = encode_fn();
     if (!enc) return fail(DMSGM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     cuuint64_t dims[2] = {cuuint64_t(h->W), cuuint64_t(h->H)};
     cuuint64_t strides[1] = {cuuint64_t(h->W)};
-    cuuint32_t box[2] = {cuuint32_t(kTileW), cuuint32_t(h->tile_rows)};
+    cuuint32_t box[2] = {cuuint32_t(kTileW), cuuint32_t(rows ? rows : h->tile_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(frame), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -179,6 +180,19 @@ static int frame_map(dmsgm_ctx* h, const void* frame, const CUtensorMap** out) {
     if (rc) return rc;
     h->tmap[slot].ptr = frame;
     *out = &h->tmap[slot].map;
+    return DMSGM_OK;
+}
+
+int batch_frame_map(dmsgm_ctx* h, const void* frame, CUtensorMap* out) {
+    for (int i = 0; i < 4; ++i)
+        if (h->bmap[i].ptr == frame) { *out = h->bmap[i].map; return DMSGM_OK; }
+    const int slot = h->bmap_next;
+    h->bmap_next = (h->bmap_next + 1) % 4;
+    h->bmap[slot].ptr = nullptr;
+    int rc = encode_frame_map(h, frame, &h->bmap[slot].map, 8 * h->B);
+    if (rc) return rc;
+    h->bmap[slot].ptr = frame;
+    *out = h->bmap[slot].map;
     return DMSGM_OK;
 }
 

@@ -32,13 +32,26 @@ struct BatchItem {
 };
 static_assert(sizeof(BatchItem) == 120, "BatchItem layout");
 
-template <int CAP>
+// Batches of up to kMapCap streams also carry one 2-D tensor map per
+// stream's frame (box kTileW x 8B rows), so a tile arrives in one TMA copy;
+// larger batches stage their tiles by 1-D bulk copies, one per pixel row.
+constexpr int kMapCap = 64;
+
+template <int CAP, bool MAPS = (CAP <= kMapCap)>
 struct BatchParams {
     int n;
     int total;           // work-list length
     BatchItem item[CAP];
 };
+template <int CAP>
+struct BatchParams<CAP, true> {
+    CUtensorMap map[CAP];
+    int n;
+    int total;
+    BatchItem item[CAP];
+};
 static_assert(sizeof(BatchParams<DMSGM_MAX_BATCH>) <= 32764, "kernel parameter limit");
+static_assert(sizeof(BatchParams<kMapCap>) <= 32764, "kernel parameter limit");
 
 // Stage setup (one warp): locate the item's stream, describe it in shared
 // memory, and start the bulk copies of its pixel rows.
@@ -78,15 +91,25 @@ __device__ __forceinline__ void stage_item(const BatchParams<CAP>& p, int t, int
     const int W = it.W, H = it.H, B = it.B;
     int tx0, ty0;
     item_origin(it, t, tx0, ty0);
-    const int rows = min(kBatchWarps * B, H - ty0);
-    const uint32_t wbytes = static_cast<uint32_t>(min(kTileW, W - tx0));
-    if (lane == 0) {
-        meta[0] = si;
-        mbar_arrive_expect_tx(bar, wbytes * rows);
+    if constexpr (CAP <= kMapCap) {
+        // one 2-D copy of the whole box (rows and columns past the frame
+        // arrive as zeros and count as transferred bytes)
+        if (lane == 0) {
+            meta[0] = si;
+            mbar_arrive_expect_tx(bar, kTileW * kBatchWarps * B);
+            tma_load_2d(tile, &p.map[si], tx0, ty0, bar);
+        }
+    } else {
+        const int rows = min(kBatchWarps * B, H - ty0);
+        const uint32_t wbytes = static_cast<uint32_t>(min(kTileW, W - tx0));
+        if (lane == 0) {
+            meta[0] = si;
+            mbar_arrive_expect_tx(bar, wbytes * rows);
+        }
+        __syncwarp();
+        for (int r = lane; r < rows; r += 32)
+            bulk_load_1d(tile + r * kTileW, it.frame + size_t(ty0 + r) * W + tx0, wbytes, bar);
     }
-    __syncwarp();
-    for (int r = lane; r < rows; r += 32)
-        bulk_load_1d(tile + r * kTileW, it.frame + size_t(ty0 + r) * W + tx0, wbytes, bar);
     if (it.affine && !it.first && lane < 2 * kBatchWarps)   // the tile's affine origins
         orig[lane] = affine_origin(it.coef, (tx0 + 128 * (lane & 1)) / B, ty0 / B + (lane >> 1));
 }
@@ -318,6 +341,10 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
             return fail(DMSGM_ERR_UNSUPPORTED, "batched streams take no checked handles (stream %d)", i);
         BatchItem& it = p.item[q];
         max_block = std::max(max_block, h->B);
+        if constexpr (CAP <= kMapCap) {
+            const int rc = batch_frame_map(const_cast<dmsgm_ctx*>(h), frames[i], &p.map[q]);
+            if (rc) return rc;
+        }
         it.frame = frames[i];
         it.mask = masks[i];
         it.mem = static_cast<char*>(h->mem);

@@ -92,6 +92,11 @@ struct dmsgm_ctx {
         CUtensorMap map;
     } tmap[dmsgm::kTmapCache];
     int tmap_next;
+    struct {                     // frame tensor maps of the batched kernel (box 256 x 8B rows)
+        const void* ptr;
+        CUtensorMap map;
+    } bmap[4];
+    int bmap_next;
     struct {                     // 3-D tensor map of the last frame sequence
         const void* ptr;
         int frames, rows;
@@ -112,6 +117,10 @@ void fill_args(const dmsgm_ctx* h, int affine, uint32_t* mask_dev, StreamArgs* a
 
 // Advance the handle's bookkeeping after a frame has been enqueued.
 void advance(dmsgm_ctx* h);
+
+// Tensor map of one of the handle's frames with the batched kernel's box
+// (kTileW x 8B rows), from a small per-handle cache keyed by the frame.
+int batch_frame_map(dmsgm_ctx* h, const void* frame, CUtensorMap* out);
 
 // Bound on the block-unit displacement (|ex|, |ey|) of every block centre of
 // a W x H grid of B x B blocks under m (current -> previous); false when the
