@@ -183,13 +183,14 @@ static int frame_map(dmsgm_ctx* h, const void* frame, const CUtensorMap** out) {
     return DMSGM_OK;
 }
 
-int batch_frame_map(dmsgm_ctx* h, const void* frame, CUtensorMap* out) {
+int batch_frame_map(dmsgm_ctx* h, const void* frame, int rows, CUtensorMap* out) {
     for (int i = 0; i < 4; ++i)
-        if (h->bmap[i].ptr == frame) { *out = h->bmap[i].map; return DMSGM_OK; }
+        if (h->bmap[i].ptr == frame && h->bmap[i].rows == rows) { *out = h->bmap[i].map; return DMSGM_OK; }
     const int slot = h->bmap_next;
     h->bmap_next = (h->bmap_next + 1) % 4;
     h->bmap[slot].ptr = nullptr;
-    int rc = encode_frame_map(h, frame, &h->bmap[slot].map, 8 * h->B);
+    h->bmap[slot].rows = rows;
+    int rc = encode_frame_map(h, frame, &h->bmap[slot].map, rows);
     if (rc) return rc;
     h->bmap[slot].ptr = frame;
     *out = h->bmap[slot].map;

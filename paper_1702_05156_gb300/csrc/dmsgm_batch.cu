@@ -57,7 +57,7 @@ static_assert(sizeof(BatchParams<kMapCap>) <= 32764, "kernel parameter limit");
 // memory, and start the bulk copies of its pixel rows.
 // Work items are tiles of kTileW x (8 * B) pixels: 8 warps, one strip row
 // each.  The stage buffers are sized for B = 8.
-constexpr int kBatchWarps = 8;
+constexpr int kBatchWarps = 4;
 constexpr int kStageRows = kBatchWarps * 8;
 
 // Stream whose work items contain t (the last with tile_begin <= t).
@@ -187,7 +187,7 @@ __device__ __forceinline__ bool run_single(const BatchItem& it, int t, const Ori
 // has 4x4 blocks, 16 KB with 8x8 ones), and no persistent loop, so more CTAs
 // fit an SM.
 template <int CAP, bool SPREAD>
-__global__ void __launch_bounds__(kBatchWarps * 32, 5)
+__global__ void __launch_bounds__(kBatchWarps * 32, 10)
     dmsgm_batch_single_kernel(const __grid_constant__ BatchParams<CAP> p) {
     extern __shared__ __align__(128) uint8_t stage[];
     __shared__ __align__(8) uint64_t bar;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 5)
 // SPREAD: built to honour the streams' mixture-variance option (each item
 // still follows its own flag); without it the option's code is compiled out.
 template <int CAP, bool SPREAD>
-__global__ void __launch_bounds__(kBatchWarps * 32, 4)
+__global__ void __launch_bounds__(kBatchWarps * 32, 8)
     dmsgm_batch_kernel(const __grid_constant__ BatchParams<CAP> p) {
     __shared__ __align__(128) uint8_t tile[2][kStageRows * kTileW];
     __shared__ __align__(8) uint64_t bar[2];
@@ -229,22 +229,6 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4)
     }
     __syncthreads();
     int t = blockIdx.x;
-    if (gridDim.x >= p.total) {   // one work item per CTA (the launch is uniform in this)
-        if (t >= p.total) return;
-        if (threadIdx.x < 32) stage_item<CAP>(p, t, meta[0], orig[0], tile[0], &bar[0]);
-        __syncthreads();           // the item's stream and origins are visible
-        const BatchItem& it = p.item[meta[0][0]];
-        const int kind = (it.B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
-        bool ok;
-        switch (kind) {
-            case 0: ok = run_single<4, float, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
-            case 1: ok = run_single<4, __half, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
-            case 2: ok = run_single<8, float, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
-            default: ok = run_single<8, __half, SPREAD>(it, t, orig[0], tile[0], &bar[0]); break;
-        }
-        if (!ok && threadIdx.x == 0) atomicOr(reinterpret_cast<int*>(it.mem), kStatusWaitTimeout);
-        return;
-    }
     // the first tile's pixels do not depend on the previous step
     if (t < p.total && threadIdx.x < 32) stage_item<CAP>(p, t, meta[0], orig[0], tile[0], &bar[0]);
     pdl_wait();
@@ -342,7 +326,8 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
         BatchItem& it = p.item[q];
         max_block = std::max(max_block, h->B);
         if constexpr (CAP <= kMapCap) {
-            const int rc = batch_frame_map(const_cast<dmsgm_ctx*>(h), frames[i], &p.map[q]);
+            const int rc = batch_frame_map(const_cast<dmsgm_ctx*>(h), frames[i], kBatchWarps * h->B,
+                                           &p.map[q]);
             if (rc) return rc;
         }
         it.frame = frames[i];

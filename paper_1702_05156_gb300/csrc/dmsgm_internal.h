@@ -76,6 +76,7 @@ struct dmsgm_ctx {
     uint8_t* pre_buf;            //   two scratch frames of the separate pass (NULL: none)
     int last_kernel;             // kernel of the last dmsgm_process step
     int step_rpt;                // strip rows per warp of the per-tile kernel at tile_rows = 8 B (0: not chosen yet)
+    int step_narrow;             // block 4, 32-row tiles: 1 one block per lane, -1 two (0: not chosen yet)
     int pipe_maps;               // state tensor maps of the pipelined kernel: 0 not yet, 1 ok, -1 unsupported
     CUtensorMap smap[2][3];      // (mu, var, age) of each state buffer
     void* mem;                   // control block + two state buffers
@@ -92,8 +93,9 @@ struct dmsgm_ctx {
         CUtensorMap map;
     } tmap[dmsgm::kTmapCache];
     int tmap_next;
-    struct {                     // frame tensor maps of the batched kernel (box 256 x 8B rows)
+    struct {                     // frame tensor maps of the batched kernel (box 256 x rows)
         const void* ptr;
+        int rows;
         CUtensorMap map;
     } bmap[4];
     int bmap_next;
@@ -119,8 +121,8 @@ void fill_args(const dmsgm_ctx* h, int affine, uint32_t* mask_dev, StreamArgs* a
 void advance(dmsgm_ctx* h);
 
 // Tensor map of one of the handle's frames with the batched kernel's box
-// (kTileW x 8B rows), from a small per-handle cache keyed by the frame.
-int batch_frame_map(dmsgm_ctx* h, const void* frame, CUtensorMap* out);
+// (kTileW x rows), from a small per-handle cache keyed by the frame.
+int batch_frame_map(dmsgm_ctx* h, const void* frame, int rows, CUtensorMap* out);
 
 // Bound on the block-unit displacement (|ex|, |ey|) of every block centre of
 // a W x H grid of B x B blocks under m (current -> previous); false when the

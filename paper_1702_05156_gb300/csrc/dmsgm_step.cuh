@@ -110,6 +110,12 @@ __global__ void __launch_bounds__(NW * 32)
     tile_mask<B, NW, RPT, true>(a, tile, tx0, ty0, st, muA, thr, status);
 }
 
+}  // namespace dmsgm
+
+#include "dmsgm_step_narrow.cuh"
+
+namespace dmsgm {
+
 template <int B, typename T, int NW, int RPT>
 static cudaError_t launch_step_t(const CUtensorMap& tmap, const StreamArgs& a, const Coef& k,
                                  int* status, cudaStream_t s, bool pdl, bool checked) {
@@ -162,12 +168,32 @@ static int step_rpt_q8(const dmsgm_ctx* h) {
     return (cap > 0 && ctas > cap) ? 2 : 1;
 }
 
-// tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1) or (4, 2), (8, 2)}
+// tile_rows = NW * B * RPT with (NW, RPT) in {(4, 1), (8, 1) or (4, 2), (8, 2)};
+// block 4 with 32-row tiles takes the one-block-per-lane kernel
+// (dmsgm_step_narrow.cuh) for frames of at most one tile per SM.
 template <int B>
 cudaError_t launch_step_block(dmsgm_ctx* h, const CUtensorMap& tmap, const StreamArgs& a,
                               const Coef& k, cudaStream_t s, bool pdl) {
     const int q = h->tile_rows / B;   // 4, 8 or 16
     const bool f16 = h->prec == DMSGM_STATE_FP16;
+    if constexpr (B == 4) {
+        if (q == 8 && !h->checked) {
+            if (h->step_narrow == 0) {
+                // measured: 320 x 240 2.41 instead of 2.64 us per frame;
+                // 1920 x 1080 (272 tiles) 3.60 instead of 3.45 us, so only
+                // frames of at most one tile per SM take it
+                const int ctas = ((h->W + kTileW - 1) / kTileW) * ((h->H + kNarrowRows - 1) / kNarrowRows);
+                int sms = 0;
+                if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+                    sms = 0;
+                const int cap = f16 ? narrow_capacity<__half>(h->device) : narrow_capacity<float>(h->device);
+                h->step_narrow = (cap > 0 && ctas <= cap && ctas <= sms) ? 1 : -1;
+            }
+            if (h->step_narrow > 0)
+                return f16 ? launch_narrow_t<__half>(tmap, a, k, h->status_dev, s, pdl)
+                           : launch_narrow_t<float>(tmap, a, k, h->status_dev, s, pdl);
+        }
+    }
     if (q == 8 && h->step_rpt == 0)
         h->step_rpt = f16 ? step_rpt_q8<B, __half>(h) : step_rpt_q8<B, float>(h);
     const int rpt = q == 8 ? h->step_rpt : (q == 16 ? 2 : 1);
