@@ -95,14 +95,9 @@ typedef struct {
                            for block 4; 64, 128, 256 for block 8); 0 = the
                            built-in choice                                    */
     int kernel;         /* frame-step kernel of dmsgm_process and
-                           dmsgm_process_host: DMSGM_KERNEL_AUTO (0),
-                           DMSGM_KERNEL_TILE (one CTA per tile) or
-                           DMSGM_KERNEL_PIPE (resident CTAs that stream the
-                           tiles, staging each tile's pixels and previous-
-                           state box in shared memory by TMA; frames in the
-                           general projective form, and sizes whose state
-                           rows are not 16-byte multiples, use the per-tile
-                           kernel).  Results are identical.                  */
+                           dmsgm_process_host: DMSGM_KERNEL_AUTO (0) or
+                           DMSGM_KERNEL_TILE (1), both the per-tile kernel
+                           (one CTA per tile); other values are refused.     */
     int mix_spread;     /* 1: Yi et al.'s mixture variance -- the compensated
                            variance also carries the spread of the mixed
                            means, sum_k w_k (var_k + (mu_k - mu~)^2) / sum w;
@@ -137,7 +132,7 @@ typedef struct {
                            (DMSGM_ERR_UNSUPPORTED).                          */
 } dmsgm_opts;
 
-enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1, DMSGM_KERNEL_PIPE = 2 };
+enum { DMSGM_KERNEL_AUTO = 0, DMSGM_KERNEL_TILE = 1 };
 
 /* Read-only description of a handle. */
 typedef struct {
@@ -152,8 +147,7 @@ typedef struct {
     int device;                  /* CUDA device of the handle                */
     int kernel;                  /* frame-step kernel setting (DMSGM_KERNEL_*) */
     int last_kernel;             /* kernel of the last dmsgm_process step:
-                                    DMSGM_KERNEL_TILE or DMSGM_KERNEL_PIPE;
-                                    0 before the first                        */
+                                    DMSGM_KERNEL_TILE; 0 before the first     */
     int mix_spread;              /* dmsgm_opts.mix_spread in use              */
     int pre_fused;               /* 1: the step kernel filters its own tile   */
     int checked;                 /* dmsgm_opts.checked in use                 */

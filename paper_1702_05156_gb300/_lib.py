@@ -26,7 +26,6 @@ DMSGM_STATE_FP32 = 0
 DMSGM_STATE_FP16 = 1
 DMSGM_KERNEL_AUTO = 0
 DMSGM_KERNEL_TILE = 1
-DMSGM_KERNEL_PIPE = 2
 DMSGM_MAX_BATCH = 256
 
 # every symbol include/dmsgm.h declares

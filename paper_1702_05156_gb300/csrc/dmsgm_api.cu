@@ -325,17 +325,10 @@ static int process_one(dmsgm_ctx* h, const uint8_t* frame_dev, const double* H3x
     if (rc) return rc;
     StreamArgs a;
     fill_args(h, affine, mask_dev, &a);
-    bool launched = false;
-    if (h->kernel != DMSGM_KERNEL_TILE && !h->pre_buf && !h->checked) {
-        rc = launch_pipe(h, *tm, a, c, s, h->kernel == DMSGM_KERNEL_AUTO, &launched);
-        if (rc) return rc;
-    }
-    if (!launched) {
-        cudaError_t e = launch_step(h, *tm, a, c, s, pdl);
-        if (e != cudaSuccess)
-            return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
-    }
-    h->last_kernel = launched ? DMSGM_KERNEL_PIPE : DMSGM_KERNEL_TILE;
+    cudaError_t e = launch_step(h, *tm, a, c, s, pdl);
+    if (e != cudaSuccess)
+        return fail(DMSGM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    h->last_kernel = DMSGM_KERNEL_TILE;
     advance(h);
     return DMSGM_OK;
 }
@@ -461,7 +454,7 @@ int dmsgm_create_ex(int W, int H, int B, float ts, float td, int age_max, const 
         return fail(DMSGM_ERR_INVALID_ARG, "seq_tile_rows %d invalid", opts.seq_tile_rows);
     }
     h->seq_tile_rows = opts.seq_tile_rows;
-    if (opts.kernel < DMSGM_KERNEL_AUTO || opts.kernel > DMSGM_KERNEL_PIPE) {
+    if (opts.kernel < DMSGM_KERNEL_AUTO || opts.kernel > DMSGM_KERNEL_TILE) {
         delete h;
         return fail(DMSGM_ERR_INVALID_ARG, "unknown kernel %d", opts.kernel);
     }

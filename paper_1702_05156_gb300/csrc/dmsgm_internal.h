@@ -77,8 +77,6 @@ struct dmsgm_ctx {
     int last_kernel;             // kernel of the last dmsgm_process step
     int step_rpt;                // strip rows per warp of the per-tile kernel at tile_rows = 8 B (0: not chosen yet)
     int step_narrow;             // block 4, 32-row tiles: 1 one block per lane, -1 two (0: not chosen yet)
-    int pipe_maps;               // state tensor maps of the pipelined kernel: 0 not yet, 1 ok, -1 unsupported
-    CUtensorMap smap[2][3];      // (mu, var, age) of each state buffer
     void* mem;                   // control block + two state buffers
     bool owns_mem;
     size_t state_bytes;
@@ -137,11 +135,6 @@ bool valid_dims_ex(int W, int H, int B);
 // T frames of one handle in persistent cooperative launches (dmsgm_seq.cu).
 int launch_seq(dmsgm_ctx* h, const uint8_t* frames_dev, int T, const double* H3x3s,
                uint32_t* masks_dev, cudaStream_t stream, int* flags);
-
-// Launch the pipelined frame step if it applies (dmsgm_pipe.cu); *launched
-// tells whether it did.  automatic: only where it is expected to be faster.
-int launch_pipe(dmsgm_ctx* h, const CUtensorMap& frame_map, const StreamArgs& a, const Coef& c,
-                cudaStream_t s, bool automatic, bool* launched);
 
 // Launch the per-tile frame-step kernel for block size B (dmsgm_step.cuh,
 // instantiated in dmsgm_step_b<B>.cu).

@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (DMSGM_KERNEL_AUTO, DMSGM_KERNEL_PIPE, DMSGM_KERNEL_TILE, DMSGM_STATE_FP16,
+from ._lib import (DMSGM_KERNEL_AUTO, DMSGM_KERNEL_TILE, DMSGM_STATE_FP16,
                    DMSGM_STATE_FP32)
 
 
@@ -60,8 +60,7 @@ class Dmsgm:
         opts.tile_rows = tile_rows
         opts.use_pdl = 1 if use_pdl else 0
         opts.seq_tile_rows = seq_tile_rows
-        opts.kernel = {"auto": DMSGM_KERNEL_AUTO, "tile": DMSGM_KERNEL_TILE,
-                       "pipe": DMSGM_KERNEL_PIPE}[kernel]
+        opts.kernel = {"auto": DMSGM_KERNEL_AUTO, "tile": DMSGM_KERNEL_TILE}[kernel]
         opts.mix_spread = 1 if mix_spread else 0
         opts.checked = 1 if checked else 0
         if prefilter is not None:   # (gauss_size, sigma, median): Sec. 2.1 preprocessing
