@@ -76,6 +76,37 @@ def test_seq_strong_motion_and_mixing_with_single_frames(lib):
         assert np.array_equal(st[k], ref_st[k]), k
 
 
+def test_seq_strong_perspective(lib):
+    """Strongly projective motion (Z from 0.7 to 1.5 across the frame, so
+    displacements grow far faster towards one side than a sample of block
+    centres would show): the dependency radius comes from a bound on every
+    block's displacement, and the multi-frame launch equals per-frame
+    launches bit for bit."""
+    rng = np.random.default_rng(17)
+    W, H, T = 640, 480, 10
+    frames, _ = make_stream(StreamSpec(W, H, T, seed=19), device="cuda")
+    Hs = [np.eye(3)]
+    for t in range(1, T):
+        th = np.radians(rng.uniform(-10, 10))
+        Hs.append(np.array([[np.cos(th), -np.sin(th), rng.uniform(-40, 40)],
+                            [np.sin(th), np.cos(th), rng.uniform(-40, 40)],
+                            [rng.choice([-1, 1]) * 8e-4, rng.choice([-1, 1]) * 6e-4, 1.0]]))
+        # keep Z > 0 over the frame: flip the sign pattern that would not
+        zs = [Hs[-1][2] @ [x, y, 1.0] for x in (0, W) for y in (0, H)]
+        if min(zs) < 0.25:
+            Hs[-1][2, :2] *= -1
+    Hs = np.stack(Hs)
+    ref_masks, ref_st = _per_frame(lib, frames, Hs, 4, "fp32")
+    m = lib.Dmsgm(W, H, 4)
+    out = m.process_seq(frames, Hs)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    assert torch.equal(out, ref_masks)
+    st = m.get_state()
+    for k in st:
+        assert np.array_equal(st[k], ref_st[k]), k
+
+
 def test_seq_teacher_forced_vs_oracle(lib):
     """The last frame of a multi-frame launch checked against the oracle."""
     W, H, T = 1920, 1080, 16
