@@ -352,9 +352,10 @@ def run_gpu(args):
 def run_batched(args, dev):
     """64 streams of mixed size (16 each of 320x240, 640x480, 1280x720,
     1920x1080), block 4 or 8 drawn per stream, seeds 1000 + k: all streams
-    advance one frame per step in ONE batched launch, steps captured as a
+    advance one frame per step in one batched launch (or one per lane when
+    the autotuner splits the streams over CUDA streams), steps captured as a
     CUDA graph, launch shape autotuned; against the plain path (one launch
-    per stream per step, also captured)."""
+    per stream per step, also captured, on one or 8 CUDA streams)."""
     import torch
     from paper_1702_05156_gb300.batch import BatchRunner, autotune, time_graph
     from paper_1702_05156_gb300.synth import make_stream, spec_for
@@ -385,7 +386,7 @@ def run_batched(args, dev):
                      "ms_per_step": round(per_step, 4),
                      "achieved_gbs": round(bytes_step / (per_step / 1e3) / 1e9, 1),
                      "frac": round(bytes_step / (per_step / 1e3) / 1e9 / peak, 4),
-                     "launches_per_step": 1 if mode == "batched" else len(specs)}
+                     "launches_per_step": len(r.lane_sets(shape.lanes)) if mode == "batched" else len(specs)}
         del g
     out["plain"]["note"] = "one CUDA stream, programmatic dependent launch"
     out["plain_multi"]["note"] = "stream i on CUDA stream i % 8, forked and joined in the graph"
@@ -394,9 +395,10 @@ def run_batched(args, dev):
     out["bytes_per_step"] = int(bytes_step)
     one_per_item = shape.ctas >= (1 << 30)
     out["launch_shape"] = {"ctas": "one per work item" if one_per_item else (shape.ctas or "all that fit"),
-                           "use_pdl": shape.use_pdl}
+                           "use_pdl": shape.use_pdl, "lanes": shape.lanes}
     out["autotune"] = [{"ctas": "one per work item" if t["ctas"] >= (1 << 30) else t["ctas"],
-                        "use_pdl": t["use_pdl"], "ms_per_step": round(t["ms_per_step"], 5)}
+                        "use_pdl": t["use_pdl"], "lanes": t["lanes"],
+                        "ms_per_step": round(t["ms_per_step"], 5)}
                        for t in tune]
     out["blocks"] = {"b4": sum(1 for s in specs if s[2] == 4), "b8": sum(1 for s in specs if s[2] == 8)}
     r.close()

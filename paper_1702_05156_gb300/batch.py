@@ -3,7 +3,8 @@ streams into one CUDA graph, and an autotuner for the batched kernel's
 launch shape.
 
 A "step" advances every stream of the batch by one frame in ONE launch of
-the persistent batched kernel (dmsgm_process_batch_ex); a captured graph
+the batched kernel (dmsgm_process_batch_ex), or in one launch per lane when
+the streams are split over several CUDA streams (lanes); a captured graph
 replays `steps` consecutive steps.  The plain path (one launch of the
 single-stream kernel per stream per step, also captured) is kept alongside
 for comparison.  All arithmetic happens in libdmsgm.so.
@@ -27,6 +28,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 class LaunchShape:
     ctas: int = 0          # persistent CTAs (0: all that fit)
     use_pdl: bool = True
+    lanes: int = 1         # CUDA streams the batch is split over, one launch each per step
 
     def opts(self) -> _lib.dmsgm_batch_opts:
         return _lib.dmsgm_batch_opts(0, self.ctas, 1 if self.use_pdl else 0)
@@ -62,13 +64,28 @@ class BatchRunner:
                          for t in range(self.T)]
 
     # -------------------------------------------------------------- launches
-    def step_batched(self, t: int, shape: LaunchShape, stream: int):
-        hs, fr, mk = _ptr_arrays(self.models, [f[t] for f in self.frames],
-                                 [k[t] for k in self.masks])
+    def lane_sets(self, lanes: int) -> list[list[int]]:
+        """The streams split over `lanes` launches with about equal pixels:
+        largest stream first, each onto the lane with the fewest pixels."""
+        load = [0] * lanes
+        sets = [[] for _ in range(lanes)]
+        for i in sorted(range(len(self.specs)), key=lambda i: -self.specs[i][0] * self.specs[i][1]):
+            j = load.index(min(load))
+            sets[j].append(i)
+            load[j] += self.specs[i][0] * self.specs[i][1]
+        return [sorted(s) for s in sets if s]
+
+    def step_batched(self, t: int, shape: LaunchShape, stream: int, idx: list[int] | None = None):
+        """One batched launch for streams `idx` (default: all) at frame t."""
+        idx = list(range(len(self.models))) if idx is None else idx
+        models = [self.models[i] for i in idx]
+        hs, fr, mk = _ptr_arrays(models, [self.frames[i][t] for i in idx],
+                                 [self.masks[i][t] for i in idx])
+        Hs = self._H_steps[t] if len(idx) == len(self.models) else \
+            np.ascontiguousarray(np.stack([self.Hs[i][t] for i in idx]).reshape(-1))
         opts = shape.opts()
         rc = _lib.load_library().dmsgm_process_batch_ex(
-            len(self.models), hs, fr, self._H_steps[t].ctypes.data, mk, _lib.ctypes.byref(opts),
-            stream)
+            len(models), hs, fr, Hs.ctypes.data, mk, _lib.ctypes.byref(opts), stream)
         _lib._check(rc)
 
     def step_plain(self, t: int, stream: int):
@@ -79,17 +96,21 @@ class BatchRunner:
     def capture(self, mode: str, shape: LaunchShape | None = None, steps: int | None = None,
                 stream: torch.cuda.Stream | None = None, lanes: int = 8) -> torch.cuda.CUDAGraph:
         """Capture `steps` (default T, even) consecutive steps into a graph.
-        mode "batched": one batched launch per step; "plain": one launch per
-        stream per step, all on the capturing stream; "plain_multi": the same
-        launches with stream i's on CUDA stream i % lanes (forked from and
-        joined back to the capturing stream), so independent streams' steps
-        can run side by side."""
+        mode "batched": one batched launch per step, or with shape.lanes > 1
+        one per lane, each lane's streams (lane_sets) on a CUDA stream of
+        their own; "plain": one launch per stream per step, all on the
+        capturing stream; "plain_multi": the same launches with stream i's on
+        CUDA stream i % lanes.  Side streams fork from and join back to the
+        capturing stream, so independent streams' steps run side by side."""
         steps = steps or self.T
         assert steps % 2 == 0, "an even number of steps keeps the handles' parity consistent"
         stream = stream or torch.cuda.Stream()
         sh = stream.cuda_stream
         g = torch.cuda.CUDAGraph()
-        side = [torch.cuda.Stream() for _ in range(lanes)] if mode == "plain_multi" else []
+        shape = shape or LaunchShape()
+        sets = self.lane_sets(shape.lanes) if mode == "batched" and shape.lanes > 1 else None
+        nside = lanes if mode == "plain_multi" else (len(sets) if sets else 0)
+        side = [torch.cuda.Stream() for _ in range(nside)]
         with torch.cuda.graph(g, stream=stream):
             if side:
                 fork = torch.cuda.Event()
@@ -98,8 +119,11 @@ class BatchRunner:
                     s.wait_event(fork)
             for k in range(steps):
                 t = k % self.T
-                if mode == "batched":
-                    self.step_batched(t, shape or LaunchShape(), sh)
+                if mode == "batched" and sets:
+                    for s, idx in zip(side, sets):
+                        self.step_batched(t, shape, s.cuda_stream, idx)
+                elif mode == "batched":
+                    self.step_batched(t, shape, sh)
                 elif mode == "plain":
                     self.step_plain(t, sh)
                 else:
@@ -148,7 +172,7 @@ def _key(specs, precision, sms):
 
 
 def autotune(runner: BatchRunner, candidates=None, steps: int = 8, use_cache: bool = True):
-    """Pick the launch shape (CTA count, PDL) of the batched kernel that gives
+    """Pick the launch shape (CTA count, PDL, lanes) of the batched kernel that gives
     the shortest step on this GPU for this stream mix; cached on disk by the
     mix, the precision and the SM count."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -162,24 +186,27 @@ def autotune(runner: BatchRunner, candidates=None, steps: int = 8, use_cache: bo
             cache = {}
     if use_cache and key in cache:
         d = cache[key]
-        return LaunchShape(d["ctas"], d["use_pdl"]), d.get("results", [])
+        return LaunchShape(d["ctas"], d["use_pdl"], d.get("lanes", 1)), d.get("results", [])
     if candidates is None:
         candidates = [LaunchShape(0, True), LaunchShape(0, False)]
         for per_sm in (1, 2, 3, 4):
             candidates.append(LaunchShape(per_sm * sms, True))
-        candidates.append(LaunchShape(1 << 30, True))   # one work item per CTA
+        for lanes in (1, 2, 4, 8):   # one work item per CTA, the streams over `lanes` launches
+            if lanes <= len(runner.specs):
+                candidates.append(LaunchShape(1 << 30, True, lanes))
     stream = torch.cuda.Stream()
     results = []
     for c in candidates:
         runner.warm("batched", c, stream)
         g = runner.capture("batched", c, steps=steps, stream=stream)
         ms = time_graph(g, stream, reps=3) / steps
-        results.append({"ctas": c.ctas, "use_pdl": c.use_pdl, "ms_per_step": ms})
+        results.append({"ctas": c.ctas, "use_pdl": c.use_pdl, "lanes": c.lanes, "ms_per_step": ms})
         del g
     best = min(results, key=lambda r: r["ms_per_step"])
-    shape = LaunchShape(best["ctas"], best["use_pdl"])
+    shape = LaunchShape(best["ctas"], best["use_pdl"], best["lanes"])
     if use_cache:
-        cache[key] = {"ctas": shape.ctas, "use_pdl": shape.use_pdl, "results": results}
+        cache[key] = {"ctas": shape.ctas, "use_pdl": shape.use_pdl, "lanes": shape.lanes,
+                      "results": results}
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
         with open(_CACHE, "w") as f:
             json.dump(cache, f, indent=1)

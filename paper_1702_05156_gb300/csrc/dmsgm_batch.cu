@@ -1,17 +1,23 @@
-// dmsgm_batch.cu -- many streams, one persistent launch per frame step.
+// dmsgm_batch.cu -- many streams, one launch per frame step.
 //
-// Every stream of the batch contributes its frame's 256 x TILE_H tiles to one
-// (stream, tile) work list.  A persistent grid of CTAs walks the list with a
-// static stride; each CTA double-buffers its tiles in shared memory: while
-// it runs the fused DMSGM step (Sec. 2.2-2.4) on tile k, the TMA engine
-// brings tile k+1 in by 1-D bulk copies (one per pixel row, so no tensor map
-// is needed for the streams' ever-changing frame pointers).  Streams may
+// Every stream of the batch contributes its frame's 256 x (4 B) tiles to one
+// (stream, tile) work list, grouped by kind (block size, state precision).
+// Two kernels run the fused DMSGM step (Sec. 2.2-2.4) over the list:
+//  - dmsgm_batch_single_kernel, one work item per CTA (the default: every
+//    item gets a CTA at once).  As in the per-frame kernel, the item's
+//    pixels, block statistics and back-projections are done before the wait
+//    on the previous step; only gathers, update and mask wait for it.
+//  - dmsgm_batch_kernel, a persistent grid (when the caller asks for fewer
+//    CTAs than items) that walks the list with a static stride and
+//    double-buffers its tiles in shared memory.
+// A batch of up to 64 streams carries one 2-D tensor map per stream's frame
+// in the kernel parameters, so a tile arrives in one TMA copy; a larger
+// batch stages a tile by 1-D bulk copies, one per pixel row.  Streams may
 // differ in size, block size (4 / 8) and state precision (FP32 / FP16).
 //
-// The per-stream descriptors travel in the kernel's parameter space (up to
-// 256 x 120 bytes), so a launch needs no device scratch and no host->device
-// copy, and a stream capture bakes each step's descriptors into its graph
-// node.
+// The per-stream descriptors travel in the kernel's parameter space, so a
+// launch needs no device scratch and no host->device copy, and a stream
+// capture bakes each step's descriptors into its graph node.
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -53,10 +59,9 @@ struct BatchParams<CAP, true> {
 static_assert(sizeof(BatchParams<DMSGM_MAX_BATCH>) <= 32764, "kernel parameter limit");
 static_assert(sizeof(BatchParams<kMapCap>) <= 32764, "kernel parameter limit");
 
-// Stage setup (one warp): locate the item's stream, describe it in shared
-// memory, and start the bulk copies of its pixel rows.
-// Work items are tiles of kTileW x (8 * B) pixels: 8 warps, one strip row
-// each.  The stage buffers are sized for B = 8.
+// Work items are tiles of kTileW x (kBatchWarps * B) pixels: one strip row
+// of blocks per warp.  The persistent kernel's stage buffers are sized for
+// B = 8.
 constexpr int kBatchWarps = 4;
 constexpr int kStageRows = kBatchWarps * 8;
 
@@ -161,12 +166,10 @@ __device__ __forceinline__ bool run_item(const BatchItem& it, int t, const Origi
 // statistics and projections run before the previous step's kernel ends;
 // only the gathers, update and mask wait for it.
 template <int B, typename T, bool SPREAD>
-__device__ __forceinline__ bool run_single(const BatchItem& it, int t, const Origin* orig,
-                                           const uint8_t* tile, uint64_t* bar) {
+__device__ __forceinline__ bool run_single(const BatchItem& it, const StreamArgs& a, int tx0,
+                                           int ty0, const Origin* orig, const uint8_t* tile,
+                                           uint64_t* bar) {
     constexpr int BPL = kLaneBlocks<B>;
-    const StreamArgs a = item_args(it);
-    int tx0, ty0;
-    item_origin(it, t, tx0, ty0);
     Proj pj[1][BPL];
     tile_project<B, kBatchWarps, 1>(a, it.coef, tx0, ty0, orig, pj);
     const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
@@ -175,7 +178,6 @@ __device__ __forceinline__ bool run_single(const BatchItem& it, int t, const Ori
     Stats st[1][BPL];
     tile_stats<B, kBatchWarps, 1>(a, tile, ty0, xin, st);
     pdl_wait();
-    pdl_launch_dependents();
     float muA[1][BPL], thr[1][BPL];
     tile_update<B, T, kBatchWarps, 1, false, SPREAD>(a, tx0, ty0, pj, st, muA, thr);
     tile_mask<B, kBatchWarps, 1>(a, tile, tx0, ty0, st, muA, thr);
@@ -193,22 +195,41 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 10)
     __shared__ __align__(8) uint64_t bar;
     __shared__ int meta[2];
     __shared__ Origin orig[2 * kBatchWarps];
+    __shared__ StreamArgs sa;   // the item's arguments, built once per CTA
+    __shared__ int sxy[2];      // the item's tile origin
     const int t = blockIdx.x;
+    // The next step's CTAs may launch once every CTA of this one has started:
+    // a step has far more items than the GPU holds, so they only take the
+    // slots that this step's finished CTAs free, and their pixel loads and
+    // statistics overlap this step's tail (measured 64 mixed streams: 39.0
+    // instead of 40.0 us per step).  The per-frame kernel triggers after its
+    // wait instead; there the next frame's CTAs would compete with the frame's
+    // own critical path.
+    pdl_launch_dependents();
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x < 32) stage_item<CAP>(p, t, meta, orig, stage, &bar);
-    __syncthreads();           // the item's stream and origins are visible
+    if (threadIdx.x < 32) {
+        stage_item<CAP>(p, t, meta, orig, stage, &bar);
+        if (threadIdx.x == 0) {
+            const BatchItem& i0 = p.item[meta[0]];
+            sa = item_args(i0);
+            item_origin(i0, t, sxy[0], sxy[1]);
+        }
+    }
+    __syncthreads();           // the item's stream, arguments and origins are visible
     const BatchItem& it = p.item[meta[0]];
+    const StreamArgs a = sa;
+    const int tx0 = sxy[0], ty0 = sxy[1];
     const int kind = (it.B == 8 ? 2 : 0) | (it.prec == DMSGM_STATE_FP16 ? 1 : 0);
     bool ok;
     switch (kind) {
-        case 0: ok = run_single<4, float, SPREAD>(it, t, orig, stage, &bar); break;
-        case 1: ok = run_single<4, __half, SPREAD>(it, t, orig, stage, &bar); break;
-        case 2: ok = run_single<8, float, SPREAD>(it, t, orig, stage, &bar); break;
-        default: ok = run_single<8, __half, SPREAD>(it, t, orig, stage, &bar); break;
+        case 0: ok = run_single<4, float, SPREAD>(it, a, tx0, ty0, orig, stage, &bar); break;
+        case 1: ok = run_single<4, __half, SPREAD>(it, a, tx0, ty0, orig, stage, &bar); break;
+        case 2: ok = run_single<8, float, SPREAD>(it, a, tx0, ty0, orig, stage, &bar); break;
+        default: ok = run_single<8, __half, SPREAD>(it, a, tx0, ty0, orig, stage, &bar); break;
     }
     if (!ok && threadIdx.x == 0) atomicOr(reinterpret_cast<int*>(it.mem), kStatusWaitTimeout);
 }

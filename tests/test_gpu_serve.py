@@ -62,7 +62,8 @@ def test_batch_runner_graph_equals_alone(lib):
     ref = _solo(lib, streams, T)
     r = BatchRunner(CFGS, [fr for fr, _ in streams], [h for _, h in streams])
     s = torch.cuda.Stream()
-    for mode_shape in (LaunchShape(0, True), LaunchShape(1 << 30, False), LaunchShape(3, True)):
+    for mode_shape in (LaunchShape(0, True), LaunchShape(1 << 30, False), LaunchShape(3, True),
+                       LaunchShape(1 << 30, True, 2)):
         for m in r.models:
             m.reset()
         g = r.capture("batched", mode_shape, steps=T, stream=s)
