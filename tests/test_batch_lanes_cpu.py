@@ -1,0 +1,43 @@
+"""CPU checks of the batched runner's split of streams over CUDA-stream lanes
+(BatchRunner.lane_sets): every stream lands in exactly one lane, lanes keep
+stream order inside, no lane is empty, and the pixel loads are balanced by
+the largest-first rule."""
+from types import SimpleNamespace
+
+import pytest
+
+from paper_1702_05156_gb300.batch import BatchRunner
+
+SIZES = [(320, 240)] * 16 + [(640, 480)] * 16 + [(1280, 720)] * 16 + [(1920, 1080)] * 16
+
+
+def _sets(specs, lanes):
+    return BatchRunner.lane_sets(SimpleNamespace(specs=specs), lanes)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 3, 4, 8])
+def test_every_stream_once_and_balanced(lanes):
+    specs = [(w, h, 4 if i % 3 else 8) for i, (w, h) in enumerate(SIZES)]
+    sets = _sets(specs, lanes)
+    assert len(sets) == lanes
+    flat = sorted(i for s in sets for i in s)
+    assert flat == list(range(len(specs)))
+    for s in sets:
+        assert s == sorted(s) and s
+    loads = [sum(specs[i][0] * specs[i][1] for i in s) for s in sets]
+    # largest first onto the lightest lane: no lane exceeds the mean by more
+    # than the largest stream
+    largest = max(w * h for (w, h, _) in specs)
+    assert max(loads) - sum(loads) / lanes <= largest
+
+
+def test_more_lanes_than_streams():
+    specs = [(320, 240, 4), (640, 480, 8)]
+    sets = _sets(specs, 8)
+    assert sorted(i for s in sets for i in s) == [0, 1]
+    assert all(s for s in sets) and len(sets) == 2
+
+
+def test_equal_streams_split_evenly():
+    specs = [(1920, 1080, 4)] * 8
+    assert [len(s) for s in _sets(specs, 4)] == [2, 2, 2, 2]
