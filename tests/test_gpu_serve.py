@@ -75,6 +75,51 @@ def test_batch_runner_graph_equals_alone(lib):
     r.close()
 
 
+def test_bench_batched_workload_equals_alone(lib):
+    """The bench's batched workload at full size -- 64 streams, 16 each of
+    320x240, 640x480, 1280x720 and 1920x1080, block 4 or 8 drawn per stream
+    from the same seeded generator -- in the launch configurations the
+    autotuner picks from (one work item per CTA on one, two and four lanes,
+    captured as a graph): every stream's masks and final state equal the
+    stream processed alone, bit for bit."""
+    from paper_1702_05156_gb300.batch import BatchRunner, LaunchShape
+    from paper_1702_05156_gb300.synth import spec_for
+    T = 4
+    rng = np.random.Generator(np.random.PCG64(1000))
+    sizes = [(320, 240)] * 16 + [(640, 480)] * 16 + [(1280, 720)] * 16 + [(1920, 1080)] * 16
+    specs, frames, Hs = [], [], []
+    for k, (w, h) in enumerate(sizes):
+        b = 4 if rng.random() < 0.5 else 8
+        fr, H = make_stream(spec_for(w, h, T, seed=1000 + k), device="cuda")
+        specs.append((w, h, b))
+        frames.append(fr)
+        Hs.append(H)
+    ref, ref_state = [], []
+    for (w, h, b), fr, H in zip(specs, frames, Hs):
+        m = lib.Dmsgm(w, h, b)
+        ref.append(torch.stack([m.process(fr[t], H[t]).clone() for t in range(T)]).cpu())
+        ref_state.append(m.get_state())
+        m.close()
+    r = BatchRunner(specs, frames, Hs)
+    s = torch.cuda.Stream()
+    for shape in (LaunchShape(1 << 30, True), LaunchShape(1 << 30, True, 2),
+                  LaunchShape(1 << 30, True, 4)):
+        for m in r.models:
+            m.reset()
+        g = r.capture("batched", shape, steps=T, stream=s)
+        with torch.cuda.stream(s):
+            g.replay()
+        s.synchronize()
+        for i in range(len(specs)):
+            assert torch.equal(r.masks[i].cpu(), ref[i]), (shape, i, specs[i])
+            st = r.models[i].get_state()
+            for key in st:
+                assert np.array_equal(st[key], ref_state[i][key]), (shape, i, key)
+            assert r.models[i].status() == 0
+        del g
+    r.close()
+
+
 def _serve(lib, engine, budget, T, waves=1):
     """Open every stream at once, submit its frames in `waves` bursts (the
     later ones while earlier frames are on the GPU), close it; returns the
