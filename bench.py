@@ -398,10 +398,11 @@ def run_batched(args, dev):
     out["bytes_per_step"] = int(bytes_step)
     one_per_item = shape.ctas >= (1 << 30)
     out["launch_shape"] = {"ctas": "one per work item" if one_per_item else (shape.ctas or "all that fit"),
-                           "use_pdl": shape.use_pdl, "lanes": shape.lanes}
+                           "use_pdl": shape.use_pdl, "lanes": shape.lanes,
+                           "item_warps": shape.item_warps or 4}
     out["autotune"] = [{"ctas": "one per work item" if t["ctas"] >= (1 << 30) else t["ctas"],
                         "use_pdl": t["use_pdl"], "lanes": t["lanes"],
-                        "ms_per_step": round(t["ms_per_step"], 5)}
+                        "item_warps": t["item_warps"], "ms_per_step": round(t["ms_per_step"], 5)}
                        for t in tune]
     out["blocks"] = {"b4": sum(1 for s in specs if s[2] == 4), "b8": sum(1 for s in specs if s[2] == 8)}
     r.close()

@@ -275,15 +275,20 @@ int dmsgm_prefilter(const uint8_t* in_dev, uint8_t* out_dev, int width, int heig
                     int gauss_size, double sigma, int median, void* cuda_stream);
 
 /* Launch shape of the batched kernel; zero-initialised = built-in choice.
- * A work item is a 256 x (8*block) pixel tile of one stream. */
+ * A work item is a 256 x (item_warps * block) pixel tile of one stream, one
+ * CTA of item_warps warps. */
 typedef struct {
     int reserved;    /* must be 0                                             */
     int ctas;        /* CTAs of the launch (each walks the work list with a
-                        stride of ctas); 0 = as many as fit on the GPU at once */
+                        stride of ctas); 0 = as many as fit on the GPU at
+                        once; at least the number of work items = one item
+                        per CTA (the single-item kernel)                      */
     int use_pdl;     /* 1: programmatic dependent launch (the first tile's
                         pixels load while the previous kernel drains; frames
                         must not be written by the immediately preceding
                         kernel on the stream); 0: plain stream order          */
+    int item_warps;  /* warps, i.e. strip rows of blocks, per work item: 4 or
+                        8; 0 = 4.  Other values: DMSGM_ERR_INVALID_ARG       */
 } dmsgm_batch_opts;
 
 int dmsgm_process_batch_ex(int n, const dmsgm_t* hs, const uint8_t* const* frames_dev,

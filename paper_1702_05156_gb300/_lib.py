@@ -53,7 +53,8 @@ class dmsgm_opts(ctypes.Structure):
 
 
 class dmsgm_batch_opts(ctypes.Structure):
-    _fields_ = [("reserved", ctypes.c_int), ("ctas", ctypes.c_int), ("use_pdl", ctypes.c_int)]
+    _fields_ = [("reserved", ctypes.c_int), ("ctas", ctypes.c_int), ("use_pdl", ctypes.c_int),
+                ("item_warps", ctypes.c_int)]
 
 
 class dmsgm_info(ctypes.Structure):

@@ -29,9 +29,10 @@ class LaunchShape:
     ctas: int = 0          # persistent CTAs (0: all that fit)
     use_pdl: bool = True
     lanes: int = 1         # CUDA streams the batch is split over, one launch each per step
+    item_warps: int = 0    # warps (strip rows) per work item: 4 or 8 (0: 4)
 
     def opts(self) -> _lib.dmsgm_batch_opts:
-        return _lib.dmsgm_batch_opts(0, self.ctas, 1 if self.use_pdl else 0)
+        return _lib.dmsgm_batch_opts(0, self.ctas, 1 if self.use_pdl else 0, self.item_warps)
 
 
 def _ptr_arrays(models, frames_t, masks_t):
@@ -172,7 +173,7 @@ def _key(specs, precision, sms):
 
 
 def autotune(runner: BatchRunner, candidates=None, steps: int = 8, use_cache: bool = True):
-    """Pick the launch shape (CTA count, PDL, lanes) of the batched kernel that gives
+    """Pick the launch shape (CTA count, PDL, lanes, work-item size) of the batched kernel that gives
     the shortest step on this GPU for this stream mix; cached on disk by the
     mix, the precision and the SM count."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -186,27 +187,30 @@ def autotune(runner: BatchRunner, candidates=None, steps: int = 8, use_cache: bo
             cache = {}
     if use_cache and key in cache:
         d = cache[key]
-        return LaunchShape(d["ctas"], d["use_pdl"], d.get("lanes", 1)), d.get("results", [])
+        return (LaunchShape(d["ctas"], d["use_pdl"], d.get("lanes", 1), d.get("item_warps", 0)),
+                d.get("results", []))
     if candidates is None:
         candidates = [LaunchShape(0, True), LaunchShape(0, False)]
         for per_sm in (1, 2, 3, 4):
             candidates.append(LaunchShape(per_sm * sms, True))
-        for lanes in (1, 2, 4, 8):   # one work item per CTA, the streams over `lanes` launches
-            if lanes <= len(runner.specs):
-                candidates.append(LaunchShape(1 << 30, True, lanes))
+        for item_warps in (4, 8):    # one work item per CTA, the streams over `lanes` launches
+            for lanes in (1, 2, 4, 8):
+                if lanes <= len(runner.specs):
+                    candidates.append(LaunchShape(1 << 30, True, lanes, item_warps))
     stream = torch.cuda.Stream()
     results = []
     for c in candidates:
         runner.warm("batched", c, stream)
         g = runner.capture("batched", c, steps=steps, stream=stream)
         ms = time_graph(g, stream, reps=3) / steps
-        results.append({"ctas": c.ctas, "use_pdl": c.use_pdl, "lanes": c.lanes, "ms_per_step": ms})
+        results.append({"ctas": c.ctas, "use_pdl": c.use_pdl, "lanes": c.lanes,
+                        "item_warps": c.item_warps or 4, "ms_per_step": ms})
         del g
     best = min(results, key=lambda r: r["ms_per_step"])
-    shape = LaunchShape(best["ctas"], best["use_pdl"], best["lanes"])
+    shape = LaunchShape(best["ctas"], best["use_pdl"], best["lanes"], best["item_warps"])
     if use_cache:
         cache[key] = {"ctas": shape.ctas, "use_pdl": shape.use_pdl, "lanes": shape.lanes,
-                      "results": results}
+                      "item_warps": shape.item_warps, "results": results}
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
         with open(_CACHE, "w") as f:
             json.dump(cache, f, indent=1)

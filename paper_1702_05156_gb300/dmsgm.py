@@ -191,9 +191,11 @@ def prefilter(frame: torch.Tensor, gauss_size: int = 5, sigma: float = 1.0, medi
     return out
 
 
-def process_batch(models, frames, Hs, masks, stream=None, ctas: int = 0, use_pdl: bool = False):
-    """One frame for each of several handles in one persistent launch."""
-    opts = _lib.dmsgm_batch_opts(0, ctas, 1 if use_pdl else 0)
+def process_batch(models, frames, Hs, masks, stream=None, ctas: int = 0, use_pdl: bool = False,
+                  item_warps: int = 0):
+    """One frame for each of several handles in one batched launch
+    (dmsgm_batch_opts: ctas, use_pdl, item_warps)."""
+    opts = _lib.dmsgm_batch_opts(0, ctas, 1 if use_pdl else 0, item_warps)
     _lib.dmsgm_process_batch([m.handle for m in models], [f.data_ptr() for f in frames],
                              np.asarray(Hs), [k.data_ptr() for k in masks],
                              _stream_handle(stream), opts)

@@ -277,11 +277,15 @@ def test_caller_owned_state_memory(lib):
     a.close()
 
 
-@pytest.mark.parametrize("ctas,pdl", [(0, False), (0, True), (1, False), (3, True), (7, True)])
-def test_batch_launch_shapes(lib, ctas, pdl):
-    """The persistent batched kernel with every launch shape (a single CTA
-    walks the whole work list through its two-stage ring) matches the
-    single-stream kernel bit for bit, over several steps."""
+@pytest.mark.parametrize("ctas,pdl,item_warps", [(0, False, 0), (0, True, 0), (1, False, 0),
+                                                 (3, True, 0), (7, True, 0), (0, True, 8),
+                                                 (5, False, 8), (1 << 30, True, 8),
+                                                 (1 << 30, False, 4)])
+def test_batch_launch_shapes(lib, ctas, pdl, item_warps):
+    """The batched kernels with every launch shape (a single CTA walks the
+    whole work list through its two-stage ring; one item per CTA; items of 4
+    or 8 warps) match the single-stream kernel bit for bit, over several
+    steps."""
     cfgs = [(1920, 1080, 4, "fp32"), (320, 240, 8, "fp32"), (640, 480, 4, "fp16"),
             (272, 40, 8, "fp16")]
     streams = [make_stream(StreamSpec(w, h, 4, seed=200 + i), device="cuda")
@@ -293,7 +297,7 @@ def test_batch_launch_shapes(lib, ctas, pdl):
         outs = [lib.new_mask(h, w) for (w, h, b, p) in cfgs]
         lib.process_batch(bat, [fr[t] for fr, _ in streams],
                           np.stack([Hs[t] for _, Hs in streams]), outs,
-                          ctas=ctas, use_pdl=pdl)
+                          ctas=ctas, use_pdl=pdl, item_warps=item_warps)
         for r, o in zip(ref, outs):
             assert torch.equal(r, o)
     for a, b in zip(solo, bat):
@@ -302,6 +306,14 @@ def test_batch_launch_shapes(lib, ctas, pdl):
             assert np.array_equal(sa[k], sb[k]), k
     for m in bat:
         assert m.status() == 0
+
+
+def test_batch_rejects_bad_item_warps(lib):
+    from paper_1702_05156_gb300 import _lib
+    m = lib.Dmsgm(64, 32, 4)
+    fr = torch.zeros((32, 64), dtype=torch.uint8, device="cuda")
+    with pytest.raises(_lib.DmsgmError, match="item_warps"):
+        lib.process_batch([m], [fr], np.eye(3).reshape(1, 9), [lib.new_mask(32, 64)], item_warps=6)
 
 
 def test_batch_teacher_forced_vs_oracle(lib):

@@ -63,7 +63,8 @@ def test_batch_runner_graph_equals_alone(lib):
     r = BatchRunner(CFGS, [fr for fr, _ in streams], [h for _, h in streams])
     s = torch.cuda.Stream()
     for mode_shape in (LaunchShape(0, True), LaunchShape(1 << 30, False), LaunchShape(3, True),
-                       LaunchShape(1 << 30, True, 2)):
+                       LaunchShape(1 << 30, True, 2), LaunchShape(1 << 30, True, 2, 8),
+                       LaunchShape(0, True, 1, 8)):
         for m in r.models:
             m.reset()
         g = r.capture("batched", mode_shape, steps=T, stream=s)
@@ -80,8 +81,8 @@ def test_bench_batched_workload_equals_alone(lib):
     320x240, 640x480, 1280x720 and 1920x1080, block 4 or 8 drawn per stream
     from the same seeded generator -- in the launch configurations the
     autotuner picks from (one work item per CTA on one, two and four lanes,
-    captured as a graph): every stream's masks and final state equal the
-    stream processed alone, bit for bit."""
+    items of 4 or 8 warps, captured as a graph): every stream's masks and
+    final state equal the stream processed alone, bit for bit."""
     from paper_1702_05156_gb300.batch import BatchRunner, LaunchShape
     from paper_1702_05156_gb300.synth import spec_for
     T = 4
@@ -103,7 +104,7 @@ def test_bench_batched_workload_equals_alone(lib):
     r = BatchRunner(specs, frames, Hs)
     s = torch.cuda.Stream()
     for shape in (LaunchShape(1 << 30, True), LaunchShape(1 << 30, True, 2),
-                  LaunchShape(1 << 30, True, 4)):
+                  LaunchShape(1 << 30, True, 4), LaunchShape(1 << 30, True, 2, 8)):
         for m in r.models:
             m.reset()
         g = r.capture("batched", shape, steps=T, stream=s)
