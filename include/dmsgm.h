@@ -247,11 +247,13 @@ int dmsgm_process_seq_noalloc(int width, int height, int block, int precision, f
 int dmsgm_process_host(dmsgm_t h, const uint8_t* frames_host, int n,
                        const double* H3x3s, uint32_t* masks_host, void* cuda_stream);
 
-/* n handles, one frame each, in ONE persistent kernel launch over a
- * (stream, tile) work list (handles may differ in size, block and
+/* n handles, one frame each, in ONE kernel launch over a (stream, tile)
+ * work list -- by default one work item per CTA, or a persistent grid that
+ * walks the list when dmsgm_batch_opts.ctas asks for fewer CTAs than items
+ * (Sec. 2.2-2.4 per item, as dmsgm_process).  Handles may differ in size, block and
  * precision; all on one device; no handle twice; width and height at most
  * 65535; block 4 or 8 with the height a multiple of it, else
- * DMSGM_ERR_UNSUPPORTED).  frames_dev[i], masks_dev[i] and H3x3s[9*i..] are handle i's
+ * DMSGM_ERR_UNSUPPORTED.  frames_dev[i], masks_dev[i] and H3x3s[9*i..] are handle i's
  * arguments as in dmsgm_process.  1 <= n <= DMSGM_MAX_BATCH (n == 0 is a
  * no-op).  The per-stream descriptors travel in the launch's parameters:
  * the call allocates nothing and copies nothing to the device, and a stream

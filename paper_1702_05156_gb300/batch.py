@@ -26,7 +26,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 
 @dataclass(frozen=True)
 class LaunchShape:
-    ctas: int = 0          # persistent CTAs (0: all that fit)
+    ctas: int = 0          # CTAs (0: all that fit; >= work items: one item per CTA)
     use_pdl: bool = True
     lanes: int = 1         # CUDA streams the batch is split over, one launch each per step
     item_warps: int = 0    # warps (strip rows) per work item: 4 or 8 (0: 4)
