@@ -396,11 +396,11 @@ def run_batched(args, dev):
     best_plain = max(out["plain"]["mpix_s"], out["plain_multi"]["mpix_s"])
     out["speedup_batched_vs_plain"] = round(out["batched"]["mpix_s"] / best_plain, 3)
     out["bytes_per_step"] = int(bytes_step)
-    one_per_item = shape.ctas >= (1 << 30)
-    out["launch_shape"] = {"ctas": "one per work item" if one_per_item else (shape.ctas or "all that fit"),
+    one_per_item = shape.ctas == 0 or shape.ctas >= (1 << 30)
+    out["launch_shape"] = {"ctas": "one per work item" if one_per_item else shape.ctas,
                            "use_pdl": shape.use_pdl, "lanes": shape.lanes,
                            "item_warps": shape.item_warps or 4}
-    out["autotune"] = [{"ctas": "one per work item" if t["ctas"] >= (1 << 30) else t["ctas"],
+    out["autotune"] = [{"ctas": "one per work item" if t["ctas"] == 0 or t["ctas"] >= (1 << 30) else t["ctas"],
                         "use_pdl": t["use_pdl"], "lanes": t["lanes"],
                         "item_warps": t["item_warps"], "ms_per_step": round(t["ms_per_step"], 5)}
                        for t in tune]

@@ -281,10 +281,11 @@ int dmsgm_prefilter(const uint8_t* in_dev, uint8_t* out_dev, int width, int heig
  * CTA of item_warps warps. */
 typedef struct {
     int reserved;    /* must be 0                                             */
-    int ctas;        /* CTAs of the launch (each walks the work list with a
-                        stride of ctas); 0 = as many as fit on the GPU at
-                        once; at least the number of work items = one item
-                        per CTA (the single-item kernel)                      */
+    int ctas;        /* CTAs of the launch: 0, or at least the number of
+                        work items = one item per CTA (the single-item
+                        kernel, the built-in choice); fewer = a persistent
+                        grid, each CTA walking the work list with a stride
+                        of ctas                                              */
     int use_pdl;     /* 1: programmatic dependent launch (the first tile's
                         pixels load while the previous kernel drains; frames
                         must not be written by the immediately preceding

@@ -26,7 +26,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 
 @dataclass(frozen=True)
 class LaunchShape:
-    ctas: int = 0          # CTAs (0: all that fit; >= work items: one item per CTA)
+    ctas: int = 0          # CTAs (0 or >= work items: one item per CTA; fewer: persistent)
     use_pdl: bool = True
     lanes: int = 1         # CUDA streams the batch is split over, one launch each per step
     item_warps: int = 0    # warps (strip rows) per work item: 4 or 8 (0: 4)
@@ -190,8 +190,8 @@ def autotune(runner: BatchRunner, candidates=None, steps: int = 8, use_cache: bo
         return (LaunchShape(d["ctas"], d["use_pdl"], d.get("lanes", 1), d.get("item_warps", 0)),
                 d.get("results", []))
     if candidates is None:
-        candidates = [LaunchShape(0, True), LaunchShape(0, False)]
-        for per_sm in (1, 2, 3, 4):
+        candidates = [LaunchShape(0, False)]   # one work item per CTA, no PDL
+        for per_sm in (1, 2, 4, 8):            # persistent grids
             candidates.append(LaunchShape(per_sm * sms, True))
         for item_warps in (4, 8):    # one work item per CTA, the streams over `lanes` launches
             for lanes in (1, 2, 4, 8):

@@ -90,11 +90,10 @@ static int run_cap(int n, const dmsgm_t* hs, const uint8_t* const* frames, const
     }
     p.n = n;
     p.total = total;
-    // 0: every CTA that fits at once; otherwise as asked (CTAs never wait on
-    // one another, so more than fit at once is fine: one item each at most)
-    int ctas = o.ctas > 0 ? o.ctas
-                          : (nwb == 8 ? batch_resident_w8(CAP, hs[0]->device)
-                                      : resident_ctas<CAP, 4>(hs[0]->device));
+    // 0: one work item per CTA (the single-item kernel); otherwise as asked,
+    // a persistent grid when fewer than the items (CTAs never wait on one
+    // another, so more CTAs than fit at once is fine)
+    int ctas = o.ctas > 0 ? o.ctas : total;
     ctas = std::max(1, std::min(ctas, total));
     const bool pdl = o.use_pdl > 0;
     cudaError_t e;

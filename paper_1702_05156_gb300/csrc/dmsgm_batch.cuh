@@ -286,28 +286,11 @@ cudaError_t launch_t(const BatchParams<CAP>& p, int ctas, cudaStream_t s, bool p
     return cudaLaunchKernelEx(&cfg, dmsgm_batch_kernel<CAP, SPREAD, NWB>, p);
 }
 
-template <int CAP, int NWB>
-int resident_ctas(int device) {
-    static std::mutex mu;
-    static int cache[64] = {0};
-    std::lock_guard<std::mutex> g(mu);
-    if (device < 0 || device >= 64) return 1;
-    if (!cache[device]) {
-        int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmsgm_batch_kernel<CAP, false, NWB>,
-                                                          NWB * 32, 0) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
-            return 1;
-        cache[device] = std::max(1, per_sm) * std::max(1, sms);
-    }
-    return cache[device];
-}
 
 
-// Launch and capacity for work items of 8 warps (dmsgm_batch_w8.cu); p points
-// to a BatchParams<cap>, cap 16, 64 or DMSGM_MAX_BATCH.
+// Launch for work items of 8 warps (dmsgm_batch_w8.cu); p points to a
+// BatchParams<cap>, cap 16, 64 or DMSGM_MAX_BATCH.
 cudaError_t batch_launch_w8(int cap, bool spread, const void* p, int ctas, cudaStream_t s,
                             bool pdl, int max_block);
-int batch_resident_w8(int cap, int device);
 
 }  // namespace dmsgm

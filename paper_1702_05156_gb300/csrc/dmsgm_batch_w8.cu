@@ -23,13 +23,4 @@ cudaError_t batch_launch_w8(int cap, bool spread, const void* p, int ctas, cudaS
     }
 }
 
-int batch_resident_w8(int cap, int device) {
-    switch (cap) {
-        case 16: return resident_ctas<16, 8>(device);
-        case 64: return resident_ctas<64, 8>(device);
-        case DMSGM_MAX_BATCH: return resident_ctas<DMSGM_MAX_BATCH, 8>(device);
-        default: return 1;
-    }
-}
-
 }  // namespace dmsgm
