@@ -5,7 +5,6 @@
 #pragma once
 
 #include <algorithm>
-#include <mutex>
 
 #include "dmsgm_internal.h"
 
