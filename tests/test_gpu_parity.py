@@ -308,6 +308,37 @@ def test_batch_launch_shapes(lib, ctas, pdl, item_warps):
         assert m.status() == 0
 
 
+@pytest.mark.parametrize("item_warps,ctas", [(4, 0), (8, 0), (8, 40)])
+def test_batch_beyond_64_streams(lib, item_warps, ctas):
+    """More than 64 streams (the kernel stages each tile by 1-D row copies
+    instead of tensor maps, with 256 descriptors in its parameters): 70 small
+    streams of mixed size, block and precision, one item per CTA and a
+    persistent grid, equal each stream alone, bit for bit, over 3 steps."""
+    rng = np.random.default_rng(5)
+    sizes = [(48, 24), (64, 32), (320, 240), (96, 64)]
+    cfgs = [(*sizes[i % 4], 4 if rng.random() < 0.5 else 8, "fp16" if i % 5 == 0 else "fp32")
+            for i in range(70)]
+    cfgs = [(w, h, b, p) for (w, h, b, p) in cfgs if h % b == 0]
+    streams = [make_stream(StreamSpec(w, h, 3, seed=500 + i), device="cuda")
+               for i, (w, h, b, p) in enumerate(cfgs)]
+    solo = [lib.Dmsgm(w, h, b, precision=p) for (w, h, b, p) in cfgs]
+    bat = [lib.Dmsgm(w, h, b, precision=p) for (w, h, b, p) in cfgs]
+    assert len(cfgs) > 64
+    for t in range(3):
+        ref = [m.process(fr[t], Hs[t]).clone() for m, (fr, Hs) in zip(solo, streams)]
+        outs = [lib.new_mask(h, w) for (w, h, b, p) in cfgs]
+        lib.process_batch(bat, [fr[t] for fr, _ in streams],
+                          np.stack([Hs[t] for _, Hs in streams]), outs, ctas=ctas,
+                          use_pdl=True, item_warps=item_warps)
+        for i, (r, o) in enumerate(zip(ref, outs)):
+            assert torch.equal(r, o), (i, cfgs[i])
+    for a, b in zip(solo, bat):
+        sa, sb = a.get_state(), b.get_state()
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), k
+        assert b.status() == 0
+
+
 def test_batch_rejects_bad_item_warps(lib):
     from paper_1702_05156_gb300 import _lib
     m = lib.Dmsgm(64, 32, 4)
