@@ -41,3 +41,27 @@ def test_more_lanes_than_streams():
 def test_equal_streams_split_evenly():
     specs = [(1920, 1080, 4)] * 8
     assert [len(s) for s in _sets(specs, 4)] == [2, 2, 2, 2]
+
+
+def test_launch_shape_fills_the_abi_options():
+    """LaunchShape.opts() fills dmsgm_batch_opts field by field (reserved 0,
+    ctas, use_pdl, item_warps), in the header's order."""
+    import ctypes
+
+    from paper_1702_05156_gb300 import _lib
+    from paper_1702_05156_gb300.batch import LaunchShape
+    o = LaunchShape(1 << 30, True, 2, 8).opts()
+    assert (o.reserved, o.ctas, o.use_pdl, o.item_warps) == (0, 1 << 30, 1, 8)
+    o = LaunchShape().opts()
+    assert (o.reserved, o.ctas, o.use_pdl, o.item_warps) == (0, 0, 1, 0)
+    # the binding's fields are the header's, in its order
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "dmsgm.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} dmsgm_batch_opts;", hdr, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"int\s+(\w+)\s*;", body)
+    assert [f for f, _ in _lib.dmsgm_batch_opts._fields_] == names == [
+        "reserved", "ctas", "use_pdl", "item_warps"]
+    assert ctypes.sizeof(_lib.dmsgm_batch_opts) == 4 * len(names)
