@@ -59,7 +59,8 @@ def test_launch_shape_fills_the_abi_options():
     import re
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                             "include", "dmsgm.h")).read()
-    body = re.search(r"typedef struct \{(.*?)\} dmsgm_batch_opts;", hdr, re.S).group(1)
+    end = hdr.index("} dmsgm_batch_opts;")
+    body = hdr[hdr.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     names = re.findall(r"int\s+(\w+)\s*;", body)
     assert [f for f, _ in _lib.dmsgm_batch_opts._fields_] == names == [
