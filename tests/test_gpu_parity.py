@@ -347,21 +347,27 @@ def test_batch_rejects_bad_item_warps(lib):
         lib.process_batch([m], [fr], np.eye(3).reshape(1, 9), [lib.new_mask(32, 64)], item_warps=6)
 
 
-def test_batch_teacher_forced_vs_oracle(lib):
-    """A 64-stream-like mix (fewer frames) checked against the oracle."""
-    cfgs = [(320, 240, 4), (640, 480, 8), (1280, 720, 4)]
+@pytest.mark.parametrize("item_warps", [4, 8])
+def test_batch_teacher_forced_vs_oracle(lib, item_warps):
+    """A 64-stream-like mix (fewer frames; FP32 and FP16 state, blocks 4 and
+    8, up to 1920x1080) through the batched kernel with either item size,
+    checked against the oracle, teacher-forced, in the parity bands (FP16
+    state: relative 6e-4)."""
+    cfgs = [(320, 240, 4, "fp32"), (640, 480, 8, "fp32"), (1280, 720, 4, "fp32"),
+            (1920, 1080, 8, "fp16"), (640, 480, 4, "fp16")]
     streams = [make_stream(spec_for(w, h, 3, seed=1000 + i), device="cuda")
-               for i, (w, h, b) in enumerate(cfgs)]
-    ms = [lib.Dmsgm(w, h, b) for (w, h, b) in cfgs]
+               for i, (w, h, b, p) in enumerate(cfgs)]
+    ms = [lib.Dmsgm(w, h, b, precision=p) for (w, h, b, p) in cfgs]
     rep = StepReport()
     for t in range(3):
         prev = [m.get_state() for m in ms] if t else [None] * len(ms)
-        outs = [lib.new_mask(h, w) for (w, h, b) in cfgs]
+        outs = [lib.new_mask(h, w) for (w, h, b, p) in cfgs]
         lib.process_batch(ms, [fr[t] for fr, _ in streams],
-                          np.stack([Hs[t] for _, Hs in streams]), outs)
-        for m, (w, h, b), (fr, Hs), o, p in zip(ms, cfgs, streams, outs, prev):
+                          np.stack([Hs[t] for _, Hs in streams]), outs, use_pdl=True,
+                          item_warps=item_warps)
+        for m, (w, h, b, pr), (fr, Hs), o, p in zip(ms, cfgs, streams, outs, prev):
             rep.add(compare_step(p, m.get_state(), lib.unpack_mask(o, w), fr[t].cpu().numpy(),
-                                 Hs[t], block=b))
+                                 Hs[t], block=b, rel=6e-4 if pr == "fp16" else 1e-5))
     rep.assert_ok()
 
 
